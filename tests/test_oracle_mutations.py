@@ -1,0 +1,87 @@
+"""Pins are strong enough: each planted mistake in a copy of the oracle's C source is caught.
+
+The mistake is planted in a temporary copy of oracle/mg_oracle.c compiled on the CPU;
+the pins of test_oracle_operator / test_oracle_solver then run against that copy and
+at least one of them must fail.  The real oracle is restored afterwards.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle as O
+import test_oracle_operator as T1
+import test_oracle_solver as T2
+
+SRC = os.path.join(os.path.dirname(O.__file__), "mg_oracle.c")
+
+# (name, original text, mutated text, pins that must catch it)
+MUTANTS = [
+    ("face harmonic mean -> arithmetic", "return 2.0 / (rhoL + rhoR);", "return 0.5 * (1.0 / rhoL + 1.0 / rhoR);",
+     [T1.test_face_coeffs_golden_pairs, T1.test_face_coeffs_is_harmonic_mean_of_inverse_density]),
+    ("density model lam <-> 1-lam", "double rhoL = lam + (1.0 - lam) * phiL;", "double rhoL = (1.0 - lam) + lam * phiL;",
+     [T1.test_face_coeffs_golden_pairs]),
+    ("operator drops the z+ term", "if (k < nz - 1) s += bz[IX(i, j, k + 1)] * (p[IX(i, j, k + 1)] - p[c]);", "",
+     [T1.test_stencil_golden_3x3x3, T1.test_constant_coefficient_operator_is_neumann_laplacian]),
+    ("operator uses the low y face twice", "if (j < ny - 1) s += by[IX(i, j + 1, k)] * (p[IX(i, j + 1, k)] - p[c]);",
+     "if (j < ny - 1) s += by[c] * (p[IX(i, j + 1, k)] - p[c]);",
+     [lambda: T1.test_operator_invariants("ellipsoid"), T1.test_dense_operator_matches_independent_assembly]),
+    ("smoother sign of the source", "p[c] = dinv[c] * (s - h2 * b[c]);", "p[c] = dinv[c] * (s + h2 * b[c]);",
+     [lambda: T1.test_colour_sweep_zeroes_that_colours_residual(0)]),
+    ("smoother reads the wrong x neighbour", "if (i < nx - 1) s += bx[IX(i + 1, j, k)] * p[IX(i + 1, j, k)];",
+     "if (i < nx - 1) s += bx[IX(i + 1, j, k)] * p[IX(i, j, k)];",
+     [lambda: T1.test_colour_sweep_zeroes_that_colours_residual(1)]),
+    ("coefficient restriction scale", "cbx[C] = 0.25 * (", "cbx[C] = 0.5 * (",
+     [T1.test_coefficient_restriction_invariants]),
+    ("coefficient restriction takes the odd fine plane", "cbz[C] = 0.25 * (bz[IX(2 * I, 2 * J, 2 * K)] + bz[IX(2 * I + 1, 2 * J, 2 * K)] +",
+     "cbz[C] = 0.25 * (bz[IX(2 * I, 2 * J, 2 * K + 1)] + bz[IX(2 * I + 1, 2 * J, 2 * K)] +",
+     [T1.test_coefficient_restriction_invariants]),
+    ("restriction weight", "rc[((size_t)K * NY + J) * NX + I] = 0.125 * s;", "rc[((size_t)K * NY + J) * NX + I] = 0.25 * s;",
+     [T1.test_restriction_is_child_average]),
+    ("prolongation weights swapped", "double w[2] = {0.75, 0.25};", "double w[2] = {0.25, 0.75};",
+     [T1.test_prolongation_reproduces_linear_fields_and_constants]),
+    ("prolongation neighbour on the wrong side", "int I1 = (i & 1) ? I0 + 1 : I0 - 1;", "int I1 = (i & 1) ? I0 - 1 : I0 + 1;",
+     [T1.test_prolongation_reproduces_linear_fields_and_constants]),
+    ("divergence sign of the z flux", "if (bz[c] > 0.0) d -= uz[c];", "if (bz[c] > 0.0) d += uz[c];",
+     [T2.test_projection_is_divergence_free_and_idempotent]),
+    ("correction uses the wrong neighbour", "if (by[c] > 0.0) uy[c] = uy0[c] - dt * by[c] * (p[c] - p[IX(i, j - 1, k)]) / h;",
+     "if (by[c] > 0.0) uy[c] = uy0[c] - dt * by[c] * (p[c] - p[IX(i - 1, j, k)]) / h;",
+     [T2.test_projection_is_divergence_free_and_idempotent]),
+    ("phi gradient sign", "gphi[c] = -0.5 * (1.0 - lam) * s;", "gphi[c] = 0.5 * (1.0 - lam) * s;",
+     [T2.test_adjoint_phi_gradient_central_differences]),
+    ("phi gradient drops the high x face", "if (i < nx - 1) s += bx[IX(i + 1, j, k)] * bx[IX(i + 1, j, k)] * gbx[IX(i + 1, j, k)];", "",
+     [T2.test_adjoint_phi_gradient_central_differences]),
+    ("pseudo-inverse keeps the null space", "if (fabs(lam) <= 1e-9 * lmax) continue;", "if (fabs(lam) == 0.0) continue;",
+     [T1.test_pinv_matches_numpy_and_penrose_conditions]),
+    ("component search ignores upper z faces", "if (k < nz - 1) { nb[m] = IX(i, j, k + 1); fb[m++] = bz[IX(i, j, k + 1)]; }", "",
+     [T1.test_components_counts]),
+]
+
+
+def _compile(src_text, out):
+    c = out + ".c"
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", out, c, "-lm"],
+                   check=True)
+
+
+@pytest.mark.parametrize("name,orig,mut,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(name, orig, mut, pins, tmp_path):
+    src = open(SRC).read()
+    assert src.count(orig) >= 1, f"mutation anchor not found: {orig}"
+    lib = str(tmp_path / "mutant.so")
+    _compile(src.replace(orig, mut, 1), lib)
+    O.use_library(lib)
+    try:
+        caught = []
+        for pin in pins:
+            try:
+                pin()
+                caught.append(False)
+            except (AssertionError, RuntimeError, ValueError, ZeroDivisionError, FloatingPointError):
+                caught.append(True)
+        assert any(caught), f"no pin caught the mutant '{name}'"
+    finally:
+        O.use_library(None)
