@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 variable-density pressure projection.
+
+Metric: Poisson solves/s to relative residual 1e-10 at 256^3 (mixed FP32-in-FP64
+refinement), with the plain FP64 solve and the V-cycle HBM GB/s of both reported
+beside it.  One timed step is one pass of the whole hot path over the 256^3 case
+(unit cube, 4-mode free surface of amplitude 0.08, a piercing ellipsoid, density
+ratio 1e-3, u* ~ N(0, 0.1), loss weights w ~ N(0, 1)):
+
+    face coefficients from phi -> multigrid hierarchy (mg_update) ->
+    projection (divergence, solve to 1e-10, correction) ->
+    adjoint projection (second solve) -> chain rule to phi
+
+i.e. two Poisson solves per step.  Inputs are resident in HBM when the timed region
+starts; the ``e2e`` leg repeats the step through the public API with pinned host
+buffers, host<->device copies included.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run, one rank per GPU) every rank runs an
+independent replica of the workload (the projection is a single-GPU problem here):
+"scaling": "weak", value = all ranks' solves / max-over-ranks time.
+``--impl reference`` times the CPU FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s to 1e-10 resid at 256^3; V-cycle HBM GB/s, FP64 vs mixed"
+TOL = 1e-10
+# algorithmic bytes per fine cell (each array read or written once per pass)
+B_SWEEP32 = 28.0      # one fused red-black sweep, FP32: p, b, bx, by, bz, dinv read + p written
+B_SWEEP64 = 56.0
+B_VCYCLE32 = 161.0    # V(2,2), all levels, FP32
+B_VCYCLE64 = 322.0    # V(2,2), all levels, FP64
+B_RESID64 = 48.0      # FP64 residual + norm (p, b, bx, by, bz read; dinv mask)
+B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="grid size per axis (256 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return (f"{n}^3 unit cube, 4-mode free surface (amp 0.08, seed 2) + piercing ellipsoid (0.3,0.06,0.05), "
+            f"rho_air/rho_water 1e-3, u*~N(0,0.1) seed 3, w~N(0,1); step = face coeffs + hierarchy + projection "
+            f"+ adjoint projection + phi chain rule (2 solves to rel. resid {TOL:g})")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.dev = device_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.dev:
+            cmd += ["-i", self.dev]
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """Largest x over the ranks (the job's time is its slowest replica's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(local_ms, solves_per_rank, world):
+    """Whole-job solves/s of N independent replicas: all ranks' solves / max-over-ranks time."""
+    ms = max_over_ranks(local_ms, world)
+    return solves_per_rank * world / (ms / 1e3), ms
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+class Step:
+    """All device buffers of one projection step; run() launches it on the current stream."""
+
+    def __init__(self, case, prec, profile):
+        import torch
+        from paper_1410_2240_gb300 import mgproj
+        self.mg = mgproj
+        self.case = case
+        dev = lambda a, dt=torch.float64: torch.from_numpy(a).to(device="cuda", dtype=dt)
+        self.phi = dev(case.phi)
+        self.solid = dev(case.solid, torch.uint8)
+        self.u_star = tuple(dev(x) for x in case.u_star)
+        self.w = tuple(dev(x) for x in case.w)
+        self.beta = mgproj.face_coeffs(self.phi, case.h, self.solid, rho_air=case.lam)
+        self.ctx = mgproj.Context(self.beta, case.h, prec=prec, profile=profile)
+        self.u = tuple(torch.empty_like(x) for x in self.u_star)
+        self.p = torch.zeros_like(self.phi)
+        self.q = torch.zeros_like(self.phi)
+        self.gu = tuple(torch.empty_like(x) for x in self.u_star)
+        self.gb = tuple(torch.empty_like(x) for x in self.u_star)
+        self.gphi = torch.empty_like(self.phi)
+        self.cycles = []
+        self.solve_ms = []
+
+    def run(self):
+        mg, c = self.mg, self.case
+        mg.face_coeffs(self.phi, c.h, self.solid, rho_air=c.lam, out=self.beta)
+        self.ctx.update(self.beta)
+        self.p.zero_()
+        _, _, st = self.ctx.project(self.u_star, p=self.p, tol=TOL, out=self.u)
+        c1, t1 = st.cycles, st.ms_solve
+        self.q.zero_()
+        _, _, st = self.ctx.project_adjoint(self.w, self.p, tol=TOL, grad_u=self.gu, grad_beta=self.gb, q=self.q)
+        mg.phi_grad(self.beta, self.gb, c.h, rho_air=c.lam, out=self.gphi)
+        self.cycles.append((c1, st.cycles))
+        self.solve_ms.append(t1 + st.ms_solve)
+
+
+def time_steps(step, K, W, world):
+    import torch
+    for _ in range(W):
+        step.run()
+    torch.cuda.synchronize()
+    step.ctx.profile_reset()
+    step.cycles.clear()
+    step.solve_ms.clear()
+    launches0 = step.mg.kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        step.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    return ms, step.mg.kernel_launches() - launches0
+
+
+def e2e_leg(case, K, W):
+    """The same step through the public autograd API with pinned host buffers."""
+    import torch
+    from paper_1410_2240_gb300.autograd import project
+    pin = lambda a, dt=torch.float64: torch.from_numpy(a).to(dtype=dt).pin_memory()
+    h_phi = pin(case.phi)
+    h_solid = pin(case.solid, torch.uint8)
+    h_u = tuple(pin(x) for x in case.u_star)
+    h_w = tuple(pin(x) for x in case.w)
+    o_u = tuple(torch.empty_like(x).pin_memory() for x in h_u)
+    o_gu = tuple(torch.empty_like(x).pin_memory() for x in h_u)
+    o_gphi = torch.empty_like(h_phi).pin_memory()
+
+    def one():
+        phi = h_phi.to("cuda", non_blocking=True).requires_grad_(True)
+        solid = h_solid.to("cuda", non_blocking=True)
+        u = tuple(x.to("cuda", non_blocking=True).requires_grad_(True) for x in h_u)
+        w = tuple(x.to("cuda", non_blocking=True) for x in h_w)
+        (ux, uy, uz), p = project(u, phi, case.h, solid=solid, rho_air=case.lam, tol=TOL, precision="mixed")
+        torch.autograd.backward((ux, uy, uz), w)
+        for o, x in zip(o_u, (ux, uy, uz)):
+            o.copy_(x.detach(), non_blocking=True)
+        for o, x in zip(o_gu, u):
+            o.copy_(x.grad, non_blocking=True)
+        o_gphi.copy_(phi.grad, non_blocking=True)
+
+    for _ in range(W):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        one()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    n = case.ncell
+    h2d = (7 * 8 + 1) * n
+    d2h = 7 * 8 * n
+    return {"value": 2 * K / sec, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": 1e3 * sec / K, "api": "paper_1410_2240_gb300.autograd.project (mixed) + backward"}
+
+
+def cpu_baseline(case, fp64_cycles):
+    """The CPU FP64 oracle, as it stands, on this host's cores: a full forward solve of the
+    same 256^3 problem to 1e-10 (setup included)."""
+    import oracle as O
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    beta = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = O.divergence(beta, case.u_star, case.h)
+    mg = O.MG(beta, case.h)
+    t1 = time.perf_counter()
+    p, cyc, _ = mg.solve(rhs, tol=TOL, max_cycles=200)
+    t2 = time.perf_counter()
+    return {"value": 1.0 / (t2 - t0), "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"one full FP64 oracle solve of the {case.nx}^3 workload to {TOL:g} "
+                      f"(face coeffs + rhs + hierarchy {t1 - t0:.1f} s, {abs(cyc)} V-cycles {t2 - t1:.1f} s); "
+                      f"GPU FP64 solve took {fp64_cycles} cycles"}, p
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_1410_2240_gb300 import synth
+
+    world, rank, local = dist_setup(args)
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    from paper_1410_2240_gb300 import mgproj
+    case = synth.case_c3(args.n)
+    n = case.ncell
+    K, W = args.steps, max(args.warmup, 3)
+
+    # ---- mixed (headline) ----
+    step = Step(case, "mixed", profile=1)
+    dev_uuid = None
+    try:
+        dev_uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        dev_uuid = dev_uuid if dev_uuid.startswith("GPU-") else "GPU-" + dev_uuid
+    except Exception:
+        dev_uuid = None
+    clocks = ClockSampler(dev_uuid)
+    clocks.start()
+    ms, launches = time_steps(step, K, W, world)
+    clk = clocks.stop()
+    value, ms = replica_throughput(ms, 2 * K, world)
+    cyc_mixed = step.cycles[-1]
+    # dominant kernel: finest-grid FP32 smoother, one launch per colour; a sweep = 2 launches
+    cnt, sm_ms = step.ctx.profile_read(mgproj.PROF_SMOOTH)
+    sweep_ms = 2.0 * sm_ms / max(cnt, 1)
+    achieved = B_SWEEP32 * n / (sweep_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    rcnt, r_ms = step.ctx.profile_read(mgproj.PROF_RESID64)
+    steps_total = sum(a + b for a, b in step.cycles)
+    solve_ms_total = sum(step.solve_ms)  # the solves alone (CUDA events inside the library)
+    mixed_vcycle_gbs = (B_VCYCLE32 + B_REFINE) * n * steps_total / (solve_ms_total / 1e3) / 1e9
+    prof = {g: step.ctx.profile_read(i) for g, i in (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3))}
+    p_mixed = step.p.detach().cpu().numpy() if rank == 0 else None
+    del step
+    torch.cuda.empty_cache()
+
+    # ---- plain FP64 on the same step ----
+    fp64 = None
+    if not args.no_fp64:
+        s64 = Step(case, "fp64", profile=1)
+        K64 = max(2, K // 2)
+        ms64, _ = time_steps(s64, K64, 3, world)
+        sps64, ms64 = replica_throughput(ms64, 2 * K64, world)
+        cyc64 = s64.cycles[-1]
+        c64, sm64 = s64.ctx.profile_read(mgproj.PROF_SMOOTH)
+        sweep64 = 2.0 * sm64 / max(c64, 1)
+        tot64 = sum(a + b for a, b in s64.cycles)
+        fp64 = {"solves_per_s": sps64, "ms_per_step": ms64 / K64,
+                "cycles_fwd_bwd": list(cyc64),
+                "vcycle_hbm_gbs": (B_VCYCLE64 + B_RESID64) * n * tot64 / (sum(s64.solve_ms) / 1e3) / 1e9,
+                "fine_sweep_ms": sweep64, "fine_sweep_gbs": B_SWEEP64 * n / (sweep64 / 1e3) / 1e9}
+        p64 = s64.p.detach().cpu().numpy() if rank == 0 else None
+        del s64
+        torch.cuda.empty_cache()
+    else:
+        p64 = None
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.n), "cells": n, "precision": "mixed (FP32 V-cycles, FP64 "
+                   "residual/accumulation/coarsest solve)", "tol": TOL, "solves_per_step": 2,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: each FP64 fine array is %.0f MB, ~1.5 GB touched per step" % (8 * n / 1e6)},
+        "cycles_fwd_bwd": list(cyc_mixed),
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "k_smooth<float> finest grid (2 launches = 1 red-black sweep)",
+                     "algorithmic_bytes_per_sweep": B_SWEEP32 * n, "sweep_ms": sweep_ms,
+                     "peak_source": f"{peak_src} hbm_gbs (burst copy)"},
+        "vcycle_hbm_gbs": {"mixed": mixed_vcycle_gbs, "fp64": fp64["vcycle_hbm_gbs"] if fp64 else None},
+        "fp64": fp64,
+        "kernel_ms": {g: {"launches": c, "ms": t} for g, (c, t) in prof.items()},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_leg(case, max(2, K // 4), 2)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, p_or = cpu_baseline(case, fp64["cycles_fwd_bwd"][0] if fp64 else None)
+        out["cpu_baseline"] = cb
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        out["error_vs_oracle"] = {"p_mixed": rel(p_mixed, p_or), "p_fp64": rel(p64, p_or) if p64 is not None else None,
+                                  "note": "p of the last timed step's forward solve vs the oracle's forward solve"}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1410_2240_gb300 import synth
+    case = synth.case_c3(args.n)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    beta = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = O.divergence(beta, case.u_star, case.h)
+    t0 = time.perf_counter()
+    mg = O.MG(beta, case.h)
+    t_setup = time.perf_counter() - t0
+    lab, nc = O.components(beta)
+    b = O.remove_mean(rhs, lab, nc)
+    # warm-up: one full solve counts the cycles a solve needs
+    _, cycles, _ = mg.solve(rhs, tol=TOL, max_cycles=200)
+    cycles = abs(cycles)
+    p = None
+    import numpy as np
+    p = np.zeros_like(b)
+    for _ in range(max(0, args.warmup - 1)):
+        p = mg.vcycle(b, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p = mg.vcycle(b, p)
+        O.residual(beta, b, p, case.h)
+    sec = time.perf_counter() - t0
+    t_cycle = sec / args.steps
+    value = 1.0 / (t_setup + cycles * t_cycle)
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_cycle, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": workload_name(args.n), "cells": case.ncell, "tol": TOL},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                            "sample": f"each step = one FP64 oracle V-cycle + residual on the {args.n}^3 workload "
+                                      f"({t_cycle:.2f} s); solves/s = 1/(setup {t_setup:.2f} s + {cycles} cycles "
+                                      f"x step time), cycles counted by a full oracle solve during warm-up"},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * mgproj.h -- C ABI of the GB300 (sm_103a) variable-density pressure projection.
+ *
+ * The library solves, on one GPU, the pressure Poisson problem of the paper's
+ * time integrator (Eq. poisson1 / Eq. poisson2) in the finite-volume form of
+ * Eq. integral2 on a uniform Cartesian MAC grid,
+ *
+ *     (A p)_c = h^-2 * sum_{open faces f of c} beta_f (p_nb - p_c) = b_c ,
+ *
+ * with face coefficients beta_f = area_f / rho_f (the product of one over the
+ * density and the cut-surface area that the Poisson-solver section moves to
+ * the coarse grids as one unit), and applies the velocity correction of
+ * Eq. runge1, u = u* - dt beta grad p.  The solver is geometric multigrid
+ * (red-black Gauss-Seidel, face-coefficient restriction, cell-centred
+ * restriction and trilinear prolongation, exact coarsest-grid solve) in FP64,
+ * or FP32 V-cycles inside FP64 iterative refinement.
+ *
+ * Layout of every field: C order [k][j][i], x fastest, nx*ny*nz entries.
+ * Face arrays use the low-face convention: bx[k][j][i] / ux[k][j][i] belong to
+ * the x-face between cells (i-1,j,k) and (i,j,k); entries with i = 0 are the
+ * low wall; the high wall face is not stored.  Likewise for y (index j) and z
+ * (index k).  Walls are closed (homogeneous Neumann, Eq. neumann with a wall
+ * velocity of 0); a face that touches a solid cell is closed (binary cut
+ * cells, area 0, static body).
+ *
+ * Pointers: every array argument is a DEVICE pointer (cudaMalloc'd or from a
+ * caching allocator) unless marked "host".  The caller owns every buffer it
+ * passes; the library never frees or retains them beyond the call, except as
+ * stated for mg_setup.  All work is ordered on the CUDA stream given to
+ * mg_setup (or to the stand-alone calls); pass NULL for the legacy default
+ * stream.  Calls that return a convergence result synchronise with that
+ * stream once per residual check (a 16-byte device-to-host read).
+ *
+ * Errors: every function returns an mg_status; on failure mg_last_error()
+ * gives a message (thread-local, valid until the next call on that thread).
+ * No function aborts, traps or prints.
+ */
+#ifndef MGPROJ_H
+#define MGPROJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_ARG = 1,            /* bad argument (null pointer, size, option) */
+    MG_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    MG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; p and stats hold the last iterate */
+    MG_ERR_NAN = 4,            /* a residual norm was not finite */
+    MG_ERR_OOM = 6             /* device allocation failed */
+} mg_status;
+
+/* Grid: cells per axis and the isotropic spacing h. */
+typedef struct {
+    int nx, ny, nz;
+    double h;
+} mg_grid;
+
+/* Wall conditions.  Only homogeneous Neumann (closed walls, the no-flux
+ * condition of Eq. neumann with zero wall velocity) is implemented. */
+typedef enum { MG_BC_NEUMANN = 0 } mg_bc_kind;
+typedef struct {
+    mg_bc_kind wall[6]; /* -x, +x, -y, +y, -z, +z */
+} mg_bc;
+
+typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
+
+/* Solver options; mg_default_opts fills the defaults given in brackets. */
+typedef struct {
+    int nu1;              /* pre-smoothing red-black sweeps per level [2] */
+    int nu2;              /* post-smoothing sweeps, colours reversed [2] */
+    int max_cycles;       /* cycle (or refinement-step) limit [100] */
+    int check_every;      /* residual check every this many cycles [1] */
+    int coarse_max_cells; /* largest coarsest grid solved densely [512] */
+    mg_precision prec;    /* MG_FP64 or MG_MIXED [MG_FP64] */
+    int inner_cycles;     /* MG_MIXED: FP32 V-cycles per FP64 refinement step [1] */
+    int profile;          /* nonzero: time finest-grid kernels with CUDA events (mg_profile_read) [0] */
+} mg_opts;
+
+/* Solve statistics (host struct, filled when non-NULL). */
+typedef struct {
+    int cycles;              /* V-cycles (FP64) or refinement steps (mixed) run */
+    double rel_resid;        /* final ||b - A p||_2 / ||b||_2 over fluid cells, FP64 */
+    double rhs_norm;         /* ||b||_2 after compatibility projection */
+    double rhs_mean_removed; /* mean of the rhs over fluid cells that was subtracted */
+    double resid_hist[256];  /* relative residual after each checked cycle */
+    float ms_setup;          /* mg_setup wall time of this context (ms, host clock) */
+    float ms_solve;          /* last solve's time (ms, CUDA events on the stream) */
+} mg_stats;
+
+typedef struct mg_ctx mg_ctx; /* opaque, owned by the library */
+
+/* Fill *o with the defaults listed in mg_opts. */
+void mg_default_opts(mg_opts *o);
+
+/*
+ * Face coefficients from the volume fraction (Eq. density with H(phi) = phi;
+ * Poisson-solver section, face product (1/rho)*area on the finest grid):
+ *   rho_c = rho_air + (rho_water - rho_air) * phi_c
+ *   beta_f = 2 / (rho_L + rho_R)   (harmonic mean of 1/rho)   on open faces
+ *   beta_f = 0 on walls and on faces touching a solid cell.
+ * phi: device, nx*ny*nz doubles.  solid_mask: device, nx*ny*nz bytes, 1 =
+ * solid, or NULL (no body).  beta_out[0..2]: device, nx*ny*nz doubles each
+ * (x, y, z low-face layout), written.  Stream-ordered on `stream`.
+ */
+int mg_face_coeffs(const mg_grid *g, const double *phi, const uint8_t *solid_mask, double rho_air,
+                   double rho_water, double *const beta_out[3], void *stream);
+
+/*
+ * Build the multigrid hierarchy (Poisson-solver section): copy the fine face
+ * coefficients, restrict them face-wise to every coarser grid (mean of the 2x2
+ * coplanar fine faces), form the inverse diagonals, the FP32 copies when
+ * opt->prec == MG_MIXED, and the dense minimum-norm inverse of the coarsest
+ * grid's operator (computed on the host in FP64).  Levels halve every axis
+ * while all three are even and >= 8; the coarsest grid must then have at most
+ * opt->coarse_max_cells cells (MG_ERR_ARG otherwise).
+ * face_coeffs[0..2]: device, nx*ny*nz doubles each, copied (a later change of
+ * phi needs a new mg_setup).  bc: host, NULL = all Neumann.  solid_mask: device
+ * or NULL; it is implied by the zero faces and used only for validation.
+ * opt: host or NULL (defaults).  stream: cudaStream_t or NULL.  The context
+ * owns all its device memory (about 5.3 x the fine face arrays in FP64 plus,
+ * when mixed, 2.4 x in FP32) until mg_destroy.  The fluid cells with at least
+ * one open face must form one connected component (isolated cells, e.g. solid
+ * ones, are allowed and hold p = 0).
+ */
+int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3], const mg_bc *bc,
+             const uint8_t *solid_mask, const mg_opts *opt, void *stream);
+
+/*
+ * Rebuild the hierarchy of an existing context for new fine face coefficients
+ * on the same grid (same work as mg_setup, no allocation): restriction,
+ * inverse diagonals, FP32 copies and the coarsest dense inverse.  face_coeffs:
+ * device, copied.  Synchronises with the context's stream once (the coarsest
+ * operator, at most coarse_max_cells cells, is inverted on the host).
+ */
+int mg_update(mg_ctx *c, const double *const face_coeffs[3]);
+
+/*
+ * Solve A p = b to ||b - A p|| / ||b|| <= tol (multigrid of the Poisson-solver
+ * section).  rhs: device, read only; its mean over the fluid cells is removed
+ * first (compatibility of the Neumann problem) and isolated cells are ignored.
+ * p: device, in = initial guess, out = solution with zero mean over the fluid
+ * cells (isolated cells 0).  stats: host or NULL.  Returns MG_OK,
+ * MG_ERR_NOT_CONVERGED (p holds the last iterate), MG_ERR_NAN, or an error.
+ * rhs and p must not alias.
+ */
+int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stats);
+
+/*
+ * One FP64 V(nu1,nu2)-cycle on the finest grid, p updated in place, with no
+ * mean removal and no residual check: red-black Gauss-Seidel (red = (i+j+k)
+ * even first on the way down, colours reversed on the way up), residual and
+ * cell-centred full weighting (mean of the 8 children), recursion, exact
+ * coarsest solve, trilinear prolongation.  rhs, p: device; rhs is used as
+ * given (the caller makes it compatible).
+ */
+int mg_vcycle(mg_ctx *c, const double *rhs, double *p);
+
+/*
+ * Right-hand side of Eq. poisson1 for a static body: rhs_c = (D u)_c / dt with
+ *   (D u)_c = h^-1 * sum_axis ( u_high - u_low ) over the OPEN faces of c
+ * (closed faces carry the wall/body velocity, zero).  u[0..2]: device face
+ * arrays; rhs: device, written.
+ */
+int mg_divergence(mg_ctx *c, const double *const u[3], double dt, double *rhs);
+
+/*
+ * Velocity correction of Eq. runge1: on open faces u_f = u*_f - dt beta_f
+ * (p_R - p_L) / h; closed faces copy u*.  u_star, u: device face arrays (u
+ * may alias u_star); p: device.
+ */
+int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double dt, double *const u[3]);
+
+/*
+ * Projection: rhs = D u* / dt (mg_divergence), solve (mg_solve, p's incoming
+ * value is the initial guess), correct (mg_correct).  u_star: device, read;
+ * u: device, written (may alias u_star); p: device, in/out.  The divergence
+ * of u over the fluid cells is then at the solve's tolerance.
+ */
+int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], double *p, double dt, double tol,
+               mg_stats *stats);
+
+/*
+ * Adjoint of the projection (derived from u = u* - B G A^+ D u*, B = diag(beta),
+ * G the face gradient on open faces, G = -D^T): for the upstream gradient
+ * w = dL/du,
+ *   c = D (beta w),  A q = c (same hierarchy: A is self-adjoint),
+ *   grad_u*_f    = w_f - (G q)_f                    (closed faces: w_f)
+ *   grad_beta_f  = dt (G p)_f ((G q)_f - w_f)       (closed faces: 0)
+ * w: device face arrays; p: device, the forward solution; grad_u: device,
+ * written; grad_beta: device or NULL; q_out: device scratch of nx*ny*nz
+ * doubles that receives q (also the initial guess; pass zeros), may be NULL
+ * to use the context's buffer.  stats: host or NULL.
+ */
+int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, double dt, double tol,
+                       double *const grad_u[3], double *const grad_beta[3], double *q_out, mg_stats *stats);
+
+/*
+ * Chain rule from face coefficients to phi (Eq. density):
+ *   d beta_f / d rho_c = -beta_f^2 / 2,  d rho / d phi = rho_water - rho_air,
+ *   grad_phi_c = -(rho_water - rho_air)/2 * sum_{open faces f of c} beta_f^2 grad_beta_f.
+ * beta, grad_beta: device face arrays; grad_phi: device, written.
+ */
+int mg_phi_grad(const mg_grid *g, const double *const beta[3], const double *const grad_beta[3], double rho_air,
+                double rho_water, double *grad_phi, void *stream);
+
+/* Hierarchy introspection (tests): number of levels, dimensions of level l
+ * (host int[3] = nx, ny, nz), and a copy of one of its FP64 arrays
+ * (which: 0,1,2 = beta x,y,z; 3 = inverse diagonal 1/sum(beta)) into a device
+ * buffer of that level's size. */
+int mg_num_levels(const mg_ctx *c);
+int mg_level_dims(const mg_ctx *c, int level, int dims[3]);
+int mg_level_array(mg_ctx *c, int level, int which, double *out);
+
+/* Instrumentation.  mg_kernel_launches: number of CUDA kernels this library has
+ * launched in this process (all contexts).  mg_profile_read: for a context made
+ * with opts.profile != 0, the number of timed launches and their summed device
+ * time (ms, CUDA events on the context's stream) of one kernel group since the
+ * last mg_profile_reset; the stream must be idle (any solve returns so).
+ * Groups: 0 = finest-grid smoothing sweep of one colour (the precision the
+ * cycles run in), 1 = finest-grid residual + restriction, 2 = finest-grid
+ * prolongation, 3 = FP64 finest-grid residual (norm or mixed cast). */
+enum { MG_PROF_SMOOTH = 0, MG_PROF_RESTRICT = 1, MG_PROF_PROLONG = 2, MG_PROF_RESID64 = 3, MG_PROF_GROUPS = 4 };
+uint64_t mg_kernel_launches(void);
+int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total);
+void mg_profile_reset(mg_ctx *c);
+
+void mg_destroy(mg_ctx *c);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGPROJ_H */

@@ -6,8 +6,11 @@
  * CPU-baseline leg of the benchmark.  It shares no code with the CUDA path.
  *
  * It is written for a reader who checks it against the paper by eye: plain
- * loops over cells and faces, no blocking, no fusion, fixed summation order,
- * compiled with -ffp-contract=off so that no fused multiply-add appears.
+ * loops over cells and faces, no blocking, no fusion, fixed summation order.
+ * Rounding is specified, not left to the compiler (-ffp-contract=off): the
+ * stencil sums of the smoother, the residual and the prolongation accumulate
+ * their products with C99 fma() in the stated order; everything else is
+ * separately rounded IEEE arithmetic.
  *
  * Grid: nx*ny*nz cells, isotropic spacing h, C order [k][j][i], x fastest.
  * Faces: bx[k][j][i] is the x-face between cells (i-1,j,k) and (i,j,k); i = 0 is
@@ -172,7 +175,7 @@ void orc_remove_mean(size_t n, const int *label, int ncomp, double *v)
 /* Red-black Gauss-Seidel: one colour (colour = (i+j+k) mod 2).  Each cell    */
 /* of that colour solves its own row of A p = b with its neighbours fixed:     */
 /*   p_c = dinv_c * (sum_f beta_f p_nb - h^2 b_c)                            */
-/* Sum order: x-, x+, y-, y+, z-, z+.  No two cells of one colour neighbour   */
+/* Sum order: x-, x+, y-, y+, z-, z+ (fma).  No two cells of one colour touch */
 /* each other, so the update order inside a colour does not matter.           */
 /* ------------------------------------------------------------------------- */
 void orc_smooth_colour(int nx, int ny, int nz, double h, const double *bx, const double *by,
@@ -186,13 +189,13 @@ void orc_smooth_colour(int nx, int ny, int nz, double h, const double *bx, const
                 if (((i + j + k) & 1) != colour) continue;
                 size_t c = IX(i, j, k);
                 double s = 0.0;
-                if (i > 0) s += bx[c] * p[IX(i - 1, j, k)];
-                if (i < nx - 1) s += bx[IX(i + 1, j, k)] * p[IX(i + 1, j, k)];
-                if (j > 0) s += by[c] * p[IX(i, j - 1, k)];
-                if (j < ny - 1) s += by[IX(i, j + 1, k)] * p[IX(i, j + 1, k)];
-                if (k > 0) s += bz[c] * p[IX(i, j, k - 1)];
-                if (k < nz - 1) s += bz[IX(i, j, k + 1)] * p[IX(i, j, k + 1)];
-                p[c] = dinv[c] * (s - h2 * b[c]);
+                if (i > 0) s = fma(bx[c], p[IX(i - 1, j, k)], s);
+                if (i < nx - 1) s = fma(bx[IX(i + 1, j, k)], p[IX(i + 1, j, k)], s);
+                if (j > 0) s = fma(by[c], p[IX(i, j - 1, k)], s);
+                if (j < ny - 1) s = fma(by[IX(i, j + 1, k)], p[IX(i, j + 1, k)], s);
+                if (k > 0) s = fma(bz[c], p[IX(i, j, k - 1)], s);
+                if (k < nz - 1) s = fma(bz[IX(i, j, k + 1)], p[IX(i, j, k + 1)], s);
+                p[c] = dinv[c] * fma(-h2, b[c], s); /* dinv * (s - h^2 b) */
             }
 }
 
@@ -221,13 +224,26 @@ void orc_restrict_coeffs(int nx, int ny, int nz, const double *bx, const double 
             }
 }
 
-/* residual r = b - A p */
+/* residual r = b - A p: the flux sum s = sum_f beta_f (p_nb - p_c) (fma, order  */
+/* x-, x+, y-, y+, z-, z+), then r = b - h^-2 s (fma)                          */
 void orc_residual(int nx, int ny, int nz, double h, const double *bx, const double *by,
                   const double *bz, const double *b, const double *p, double *r)
 {
-    size_t n = (size_t)nx * ny * nz;
-    orc_apply_A(nx, ny, nz, h, bx, by, bz, p, r);
-    for (size_t c = 0; c < n; c++) r[c] = b[c] - r[c];
+    double ih2 = 1.0 / (h * h);
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t c = IX(i, j, k);
+                double s = 0.0;
+                if (i > 0) s = fma(bx[c], p[IX(i - 1, j, k)] - p[c], s);
+                if (i < nx - 1) s = fma(bx[IX(i + 1, j, k)], p[IX(i + 1, j, k)] - p[c], s);
+                if (j > 0) s = fma(by[c], p[IX(i, j - 1, k)] - p[c], s);
+                if (j < ny - 1) s = fma(by[IX(i, j + 1, k)], p[IX(i, j + 1, k)] - p[c], s);
+                if (k > 0) s = fma(bz[c], p[IX(i, j, k - 1)] - p[c], s);
+                if (k < nz - 1) s = fma(bz[IX(i, j, k + 1)], p[IX(i, j, k + 1)] - p[c], s);
+                r[c] = fma(-s, ih2, b[c]);
+            }
 }
 
 /* cell-centred full weighting: coarse value = mean of the 8 children */
@@ -250,6 +266,7 @@ void orc_restrict(int nx, int ny, int nz, const double *r, double *rc)
 /* centre lies a quarter coarse cell from its parent's centre: weight 3/4 on  */
 /* the parent and 1/4 on the next coarse cell on the same side; that index    */
 /* is clamped to the domain at walls.  Cells with dinv = 0 are not updated.   */
+/* The 8 weighted values are accumulated with fma (K outer, then J, then I).  */
 void orc_prolong_add(int nx, int ny, int nz, const double *ec, const double *dinv, double *p)
 {
     int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
@@ -275,7 +292,7 @@ void orc_prolong_add(int nx, int ny, int nz, const double *ec, const double *din
                 for (int a = 0; a < 2; a++)
                     for (int bb = 0; bb < 2; bb++)
                         for (int d = 0; d < 2; d++)
-                            s += w[a] * w[bb] * w[d] * ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]];
+                            s = fma(w[a] * w[bb] * w[d], ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]], s);
                 p[c] += s;
             }
 }

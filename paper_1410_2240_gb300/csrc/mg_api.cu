@@ -1,0 +1,713 @@
+// mg_api.cu -- C ABI of the GB300 variable-density pressure projection (host side).
+//
+// Owns the multigrid hierarchy (one mg_ctx per set of face coefficients), drives
+// the V-cycles on the caller's stream, and computes the dense minimum-norm inverse
+// of the coarsest grid's operator on the host in FP64 (one Cholesky
+// factorisation per connected component of a rank-one-shifted operator).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mg_internal.cuh"
+
+using mg::Dims;
+using mg::LevelArrays;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+    } while (0)
+
+#define CKS(expr)              \
+    do {                       \
+        int s_ = (expr);       \
+        if (s_ != MG_OK) return s_; \
+    } while (0)
+
+}  // namespace
+
+struct mg_ctx {
+    mg_grid g{};
+    mg_opts o{};
+    cudaStream_t s = nullptr;
+    int nlev = 0;
+    std::vector<Dims> dims;
+    std::vector<double> hs;
+    std::vector<LevelArrays<double>> L64;
+    std::vector<LevelArrays<float>> L32;
+    double *b0 = nullptr;       // compatible fine rhs of the current solve
+    double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
+    double *qbuf = nullptr;     // adjoint solution when the caller passes none
+    double *M = nullptr;        // coarsest dense inverse (device, ncoarse^2)
+    int ncoarse = 0;
+    double *partials = nullptr; // reduction partials
+    double *dscal = nullptr;    // device scalars (mg::Scal)
+    double *hscal = nullptr;    // pinned host mirror of dscal
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    float ms_setup = 0.f;
+    double nlive = 0.0;
+    std::vector<void *> allocs;
+    // profiling (opts.profile): event pairs recorded around finest-grid kernels
+    std::vector<cudaEvent_t> pev;
+    std::vector<int> pgroup;
+    size_t pused = 0;
+
+    template <typename T>
+    int alloc(T **p, size_t n)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MG_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        *p = (T *)q;
+        return MG_OK;
+    }
+    ~mg_ctx()
+    {
+        for (void *q : allocs) cudaFree(q);
+        if (hscal) cudaFreeHost(hscal);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : pev) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+bool grid_ok(const mg_grid *g)
+{
+    return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->h > 0.0 && std::isfinite(g->h) &&
+           (double)g->nx * g->ny * g->nz < 2147483647.0;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest-grid dense inverse (host, FP64).  A is assembled face by face; for
+// each connected component of >= 2 cells the Moore-Penrose inverse is formed
+// from one Cholesky factorisation of the shifted matrix -A + (a/m) 1 1^T (see
+// below); isolated cells get zero rows and columns.
+// ---------------------------------------------------------------------------
+int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &bx, const std::vector<double> &by,
+                   const std::vector<double> &bz, std::vector<double> &M)
+{
+    const int n = nx * ny * nz;
+    const double ih2 = 1.0 / (h * h);
+    std::vector<double> A((size_t)n * n, 0.0);
+    auto couple = [&](int a, int c, double beta) {
+        if (beta <= 0.0) return;
+        const double v = beta * ih2;
+        A[(size_t)a * n + a] -= v;
+        A[(size_t)c * n + c] -= v;
+        A[(size_t)a * n + c] += v;
+        A[(size_t)c * n + a] += v;
+    };
+    auto id = [&](int i, int j, int k) { return (k * ny + j) * nx + i; };
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                const int c = id(i, j, k);
+                if (i > 0) couple(id(i - 1, j, k), c, bx[c]);
+                if (j > 0) couple(id(i, j - 1, k), c, by[c]);
+                if (k > 0) couple(id(i, j, k - 1), c, bz[c]);
+            }
+    // components (union of cells joined by a nonzero off-diagonal)
+    std::vector<int> comp(n, -1);
+    std::vector<std::vector<int>> members;
+    for (int s0 = 0; s0 < n; s0++) {
+        if (comp[s0] >= 0) continue;
+        const int cid = (int)members.size();
+        members.emplace_back();
+        std::vector<int> stack{s0};
+        comp[s0] = cid;
+        while (!stack.empty()) {
+            const int a = stack.back();
+            stack.pop_back();
+            members[cid].push_back(a);
+            for (int b = 0; b < n; b++)
+                if (b != a && A[(size_t)a * n + b] != 0.0 && comp[b] < 0) {
+                    comp[b] = cid;
+                    stack.push_back(b);
+                }
+        }
+    }
+    M.assign((size_t)n * n, 0.0);
+    for (auto &mem : members) {
+        const int m = (int)mem.size();
+        if (m < 2) continue;
+        // L = -A on the component (positive semi-definite, null vector 1).  With
+        // J = 1 1^T and a = trace(L)/m (inside L's spectrum), L + (a/m) J is
+        // positive definite and its inverse is L^+ + J/(a m): no cancellation.
+        std::vector<double> S((size_t)m * m);
+        double tr = 0.0;
+        for (int q = 0; q < m; q++) tr += -A[(size_t)mem[q] * n + mem[q]];
+        const double a = tr / m, shift = a / m;
+        for (int x = 0; x < m; x++)
+            for (int y = 0; y < m; y++) S[(size_t)x * m + y] = -A[(size_t)mem[x] * n + mem[y]] + shift;
+        // Cholesky S = L L^T (lower triangle, in place)
+        for (int j = 0; j < m; j++) {
+            double d = S[(size_t)j * m + j];
+            for (int q = 0; q < j; q++) d -= S[(size_t)j * m + q] * S[(size_t)j * m + q];
+            if (!(d > 0.0)) return fail(MG_ERR_ARG, "coarsest-grid operator is not semi-definite");
+            const double ljj = std::sqrt(d);
+            S[(size_t)j * m + j] = ljj;
+            for (int i = j + 1; i < m; i++) {
+                double v = S[(size_t)i * m + j];
+                for (int q = 0; q < j; q++) v -= S[(size_t)i * m + q] * S[(size_t)j * m + q];
+                S[(size_t)i * m + j] = v / ljj;
+            }
+        }
+        // X = S^-1 column by column (forward then backward substitution)
+        std::vector<double> X((size_t)m * m), y(m);
+        for (int col = 0; col < m; col++) {
+            for (int i = 0; i < m; i++) {
+                double v = (i == col) ? 1.0 : 0.0;
+                for (int q = 0; q < i; q++) v -= S[(size_t)i * m + q] * y[q];
+                y[i] = v / S[(size_t)i * m + i];
+            }
+            for (int i = m - 1; i >= 0; i--) {
+                double v = y[i];
+                for (int q = i + 1; q < m; q++) v -= S[(size_t)q * m + i] * X[(size_t)q * m + col];
+                X[(size_t)i * m + col] = v / S[(size_t)i * m + i];
+            }
+        }
+        // A^+ = -L^+ = -(X - J/(a m))
+        const double jc = 1.0 / (a * m);
+        for (int x = 0; x < m; x++)
+            for (int y2 = 0; y2 < m; y2++) M[(size_t)mem[x] * n + mem[y2]] = -(X[(size_t)x * m + y2] - jc);
+    }
+    return MG_OK;
+}
+
+template <typename T>
+int level_alloc(mg_ctx *c, LevelArrays<T> &L, size_t n, bool with_bp)
+{
+    CKS(c->alloc(&L.bx, n));
+    CKS(c->alloc(&L.by, n));
+    CKS(c->alloc(&L.bz, n));
+    CKS(c->alloc(&L.dinv, n));
+    if (with_bp) {
+        CKS(c->alloc(&L.b, n));
+        CKS(c->alloc(&L.p, n));
+    }
+    return MG_OK;
+}
+
+// Profiling: an event pair around one finest-grid kernel launch (no-op unless enabled).
+struct ProfScope {
+    mg_ctx *c;
+    int slot = -1;
+    ProfScope(mg_ctx *c_, int group, bool on) : c(c_)
+    {
+        if (!on || !c->o.profile || c->pused + 2 > c->pev.size()) return;
+        slot = (int)c->pused;
+        c->pused += 2;
+        c->pgroup[slot / 2] = group;
+        cudaEventRecord(c->pev[slot], c->s);
+    }
+    ~ProfScope()
+    {
+        if (slot >= 0) cudaEventRecord(c->pev[slot + 1], c->s);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// V-cycle on level l (p updated in place): pre-smooth nu1 x (red, black),
+// residual + restriction, coarse correction (recursion or exact solve),
+// prolongation, post-smooth nu2 x (black, red).
+// ---------------------------------------------------------------------------
+template <typename T>
+int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T *p)
+{
+    cudaStream_t s = c->s;
+    const Dims d = c->dims[l];
+    if (l == c->nlev - 1) {
+        CK(mg::launch_coarse_solve<T>(c->ncoarse, c->M, b, p, s));
+        return MG_OK;
+    }
+    const T h = (T)c->hs[l];
+    const T h2 = (T)(c->hs[l] * c->hs[l]);
+    const T ih2 = (T)(1.0 / (c->hs[l] * c->hs[l]));
+    const bool fine = (l == 0);
+    auto smooth = [&](int colour) -> int {
+        ProfScope ps(c, MG_PROF_SMOOTH, fine);
+        CK(mg::launch_smooth<T>(d, h2, L[l], b, p, colour, s));
+        return MG_OK;
+    };
+    for (int it = 0; it < c->o.nu1; it++) {
+        CKS(smooth(0));
+        CKS(smooth(1));
+    }
+    (void)h;
+    const LevelArrays<T> &C = L[l + 1];
+    {
+        ProfScope ps(c, MG_PROF_RESTRICT, fine);
+        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, p, C.b, s));
+    }
+    CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
+    CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
+    {
+        ProfScope ps(c, MG_PROF_PROLONG, fine);
+        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, p, s));
+    }
+    for (int it = 0; it < c->o.nu2; it++) {
+        CKS(smooth(1));
+        CKS(smooth(0));
+    }
+    return MG_OK;
+}
+
+// read the device scalars into the pinned mirror (one stream sync)
+int read_scalars(mg_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->hscal, c->dscal, mg::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return MG_OK;
+}
+
+void stats_begin(mg_stats *st)
+{
+    if (!st) return;
+    st->cycles = 0;
+    st->rel_resid = 0.0;
+    st->rhs_norm = 0.0;
+    st->rhs_mean_removed = 0.0;
+    for (double &v : st->resid_hist) v = 0.0;
+}
+
+int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
+{
+    cudaStream_t s = c->s;
+    const Dims d = c->dims[0];
+    const double ih2 = 1.0 / (c->hs[0] * c->hs[0]);
+    const bool mixed = c->o.prec == MG_MIXED;
+    stats_begin(st);
+    if (st) st->ms_setup = c->ms_setup;
+    CK(cudaEventRecord(c->ev0, s));
+    CK(mg::launch_rhs_prepare(d, rhs, c->L64[0].dinv, c->b0, c->partials, c->dscal, s));
+    int scale_slot = mg::S_SCALE0, next_slot = mg::S_SCALE1;
+    if (mixed) {
+        ProfScope ps(c, MG_PROF_RESID64, true);
+        CK(mg::launch_resid_cast(d, ih2, c->L64[0], c->b0, p, c->L32[0].b, c->partials, c->dscal, -1, next_slot, s));
+    } else {
+        ProfScope ps(c, MG_PROF_RESID64, true);
+        CK(mg::launch_resid_norm(d, ih2, c->L64[0], c->b0, p, c->partials, c->dscal, s));
+    }
+    CKS(read_scalars(c));
+    const double nb2 = c->hscal[mg::S_NB2];
+    if (st) {
+        st->rhs_norm = std::sqrt(nb2);
+        st->rhs_mean_removed = c->nlive > 0 ? c->hscal[mg::S_SUM_B] / c->nlive : 0.0;
+    }
+    if (!std::isfinite(nb2)) return fail(MG_ERR_NAN, "right-hand side is not finite");
+    if (nb2 == 0.0 || c->nlive == 0.0) {
+        CK(cudaMemsetAsync(p, 0, d.n() * sizeof(double), s));
+        CK(cudaEventRecord(c->ev1, s));
+        CK(cudaEventSynchronize(c->ev1));
+        if (st) cudaEventElapsedTime(&st->ms_solve, c->ev0, c->ev1);
+        return MG_OK;
+    }
+    double rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
+    int cyc = 0, status = MG_OK;
+    int nhist = 0;
+    while (!(rel <= tol)) {
+        if (!std::isfinite(rel)) {
+            status = fail(MG_ERR_NAN, "residual norm is not finite after %d cycles", cyc);
+            break;
+        }
+        if (cyc >= c->o.max_cycles) {
+            status = fail(MG_ERR_NOT_CONVERGED, "not converged: relative residual %.3e after %d cycles (tol %.1e)",
+                          rel, cyc, tol);
+            break;
+        }
+        cyc++;
+        if (mixed) {
+            CK(cudaMemsetAsync(c->L32[0].p, 0, d.n() * sizeof(float), s));
+            for (int ic = 0; ic < c->o.inner_cycles; ic++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, c->L32[0].p));
+            CK(mg::launch_accumulate(d, c->L64[0].dinv, c->L32[0].p, p, c->dscal, scale_slot, s));
+            std::swap(scale_slot, next_slot);
+            ProfScope ps(c, MG_PROF_RESID64, true);
+            CK(mg::launch_resid_cast(d, ih2, c->L64[0], c->b0, p, c->L32[0].b, c->partials, c->dscal, scale_slot,
+                                     next_slot, s));
+        } else {
+            CKS(vcycle<double>(c, c->L64, 0, c->b0, p));
+            if (cyc % c->o.check_every != 0 && cyc < c->o.max_cycles) continue;
+            ProfScope ps(c, MG_PROF_RESID64, true);
+            CK(mg::launch_resid_norm(d, ih2, c->L64[0], c->b0, p, c->partials, c->dscal, s));
+        }
+        CKS(read_scalars(c));
+        rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
+        if (st && nhist < 256) st->resid_hist[nhist++] = rel;
+    }
+    // zero mean over live cells (the cycle commutes with constant shifts, so once suffices)
+    CK(mg::launch_sub_mean_p(d, c->L64[0].dinv, p, c->dscal, s));
+    CK(cudaEventRecord(c->ev1, s));
+    CK(cudaEventSynchronize(c->ev1));
+    if (st) {
+        st->cycles = cyc;
+        st->rel_resid = rel;
+        cudaEventElapsedTime(&st->ms_solve, c->ev0, c->ev1);
+    }
+    return status;
+}
+
+int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
+{
+    cudaStream_t s = c->s;
+    const Dims dc = c->dims.back();
+    const size_t n0 = c->dims[0].n();
+    CK(cudaMemsetAsync(c->dscal, 0, mg::S_COUNT * sizeof(double), s));
+    CK(cudaMemcpyAsync(c->L64[0].bx, face_coeffs[0], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->L64[0].by, face_coeffs[1], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->L64[0].bz, face_coeffs[2], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int l = 0; l < c->nlev; l++) {
+        if (l > 0)
+            CK(mg::launch_restrict_coeffs(c->dims[l - 1], c->L64[l - 1].bx, c->L64[l - 1].by, c->L64[l - 1].bz,
+                                          c->L64[l].bx, c->L64[l].by, c->L64[l].bz, s));
+        CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv, s));
+    }
+    CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
+    // coarsest operator to the host
+    const int nc = c->ncoarse;
+    std::vector<double> cb[3];
+    double *src[3] = {c->L64.back().bx, c->L64.back().by, c->L64.back().bz};
+    for (int a = 0; a < 3; a++) {
+        cb[a].resize(nc);
+        CK(cudaMemcpyAsync(cb[a].data(), src[a], nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CKS(read_scalars(c));
+    c->nlive = c->hscal[mg::S_NLIVE];
+    std::vector<double> M;
+    CKS(coarse_inverse(dc.nx, dc.ny, dc.nz, c->hs.back(), cb[0], cb[1], cb[2], M));
+    CK(cudaMemcpyAsync(c->M, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (c->o.prec == MG_MIXED) {
+        for (int l = 0; l < c->nlev; l++) {
+            const size_t n = c->dims[l].n();
+            CK(mg::launch_cast_f32(n, c->L64[l].bx, c->L32[l].bx, s));
+            CK(mg::launch_cast_f32(n, c->L64[l].by, c->L32[l].by, s));
+            CK(mg::launch_cast_f32(n, c->L64[l].bz, c->L32[l].bz, s));
+            CK(mg::launch_cast_f32(n, c->L64[l].dinv, c->L32[l].dinv, s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));  // M's host staging buffer must outlive the copy
+    return MG_OK;
+}
+
+int ensure(mg_ctx *c, double **p, size_t n)
+{
+    if (*p) return MG_OK;
+    return c->alloc(p, n);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_default_opts(mg_opts *o)
+{
+    if (!o) return;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->max_cycles = 100;
+    o->check_every = 1;
+    o->coarse_max_cells = 512;
+    o->prec = MG_FP64;
+    o->inner_cycles = 1;
+    o->profile = 0;
+}
+
+const char *mg_last_error(void) { return g_err.c_str(); }
+
+int mg_face_coeffs(const mg_grid *g, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water,
+                   double *const beta_out[3], void *stream)
+{
+    g_err.clear();
+    if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_face_coeffs: bad grid");
+    if (!phi || !beta_out || !beta_out[0] || !beta_out[1] || !beta_out[2])
+        return fail(MG_ERR_ARG, "mg_face_coeffs: null pointer");
+    if (!(rho_air > 0.0) || !(rho_water > 0.0)) return fail(MG_ERR_ARG, "mg_face_coeffs: densities must be > 0");
+    const Dims d{g->nx, g->ny, g->nz};
+    CK(mg::launch_face_coeffs(d, phi, solid_mask, rho_air, rho_water - rho_air, beta_out[0], beta_out[1], beta_out[2],
+                              (cudaStream_t)stream));
+    return MG_OK;
+}
+
+int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3], const mg_bc *bc,
+             const uint8_t *solid_mask, const mg_opts *opt, void *stream)
+{
+    g_err.clear();
+    (void)solid_mask;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) return fail(MG_ERR_ARG, "mg_setup: out is null");
+    *out = nullptr;
+    if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_setup: bad grid");
+    if (!face_coeffs || !face_coeffs[0] || !face_coeffs[1] || !face_coeffs[2])
+        return fail(MG_ERR_ARG, "mg_setup: null face coefficient pointer");
+    if (bc)
+        for (int w = 0; w < 6; w++)
+            if (bc->wall[w] != MG_BC_NEUMANN) return fail(MG_ERR_ARG, "mg_setup: only Neumann walls are supported");
+    mg_opts o;
+    mg_default_opts(&o);
+    if (opt) o = *opt;
+    if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
+        o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
+        o.inner_cycles < 1 || o.profile < 0)
+        return fail(MG_ERR_ARG, "mg_setup: invalid options");
+
+    mg_ctx *c = new mg_ctx();
+    c->g = *g;
+    c->o = o;
+    c->s = (cudaStream_t)stream;
+    auto bail = [&](int code) {
+        delete c;
+        return code;
+    };
+    // levels: halve while every axis is even and >= 8
+    Dims d{g->nx, g->ny, g->nz};
+    double h = g->h;
+    for (;;) {
+        c->dims.push_back(d);
+        c->hs.push_back(h);
+        if (!(d.nx % 2 == 0 && d.ny % 2 == 0 && d.nz % 2 == 0 && d.nx >= 8 && d.ny >= 8 && d.nz >= 8)) break;
+        d = Dims{d.nx / 2, d.ny / 2, d.nz / 2};
+        h *= 2.0;
+    }
+    c->nlev = (int)c->dims.size();
+    const Dims dc = c->dims.back();
+    if ((long long)dc.n() > o.coarse_max_cells)
+        return bail(fail(MG_ERR_ARG, "mg_setup: coarsest grid %dx%dx%d has %zu cells > coarse_max_cells=%d", dc.nx,
+                         dc.ny, dc.nz, dc.n(), o.coarse_max_cells));
+    c->ncoarse = (int)dc.n();
+    cudaStream_t s = c->s;
+    int st = MG_OK;
+    c->L64.resize(c->nlev);
+    for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<double>(c, c->L64[l], c->dims[l].n(), l > 0);
+    if (st == MG_OK) st = c->alloc(&c->b0, c->dims[0].n());
+    if (st == MG_OK) st = c->alloc(&c->partials, 2 * mg::kRedBlocks);
+    if (st == MG_OK) st = c->alloc(&c->dscal, mg::S_COUNT);
+    if (st == MG_OK) st = c->alloc(&c->M, (size_t)c->ncoarse * c->ncoarse);
+    if (st != MG_OK) return bail(st);
+    if (cudaMallocHost(&c->hscal, mg::S_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(MG_ERR_CUDA, "mg_setup: pinned buffer / event creation failed"));
+    }
+    if (c->o.prec == MG_MIXED) {
+        c->L32.resize(c->nlev);
+        for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<float>(c, c->L32[l], c->dims[l].n(), true);
+        if (st != MG_OK) return bail(st);
+    }
+    if (c->o.profile) {
+        c->pev.resize(2 * 32768);
+        c->pgroup.resize(32768);
+        for (auto &e : c->pev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return bail(fail(MG_ERR_CUDA, "mg_setup: event creation failed"));
+            }
+    }
+    st = compute_hierarchy(c, face_coeffs);
+    if (st != MG_OK) return bail(st);
+    c->ms_setup = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = c;
+    return MG_OK;
+}
+
+int mg_update(mg_ctx *c, const double *const face_coeffs[3])
+{
+    g_err.clear();
+    if (!c || !face_coeffs || !face_coeffs[0] || !face_coeffs[1] || !face_coeffs[2])
+        return fail(MG_ERR_ARG, "mg_update: null argument");
+    const auto t0 = std::chrono::steady_clock::now();
+    CKS(compute_hierarchy(c, face_coeffs));
+    c->ms_setup = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return MG_OK;
+}
+
+int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stats)
+{
+    g_err.clear();
+    if (!c || !rhs || !p) return fail(MG_ERR_ARG, "mg_solve: null argument");
+    if (rhs == p) return fail(MG_ERR_ARG, "mg_solve: rhs and p must not alias");
+    if (!(tol > 0.0)) return fail(MG_ERR_ARG, "mg_solve: tol must be > 0");
+    return solve_impl(c, rhs, p, tol, stats);
+}
+
+int mg_vcycle(mg_ctx *c, const double *rhs, double *p)
+{
+    g_err.clear();
+    if (!c || !rhs || !p) return fail(MG_ERR_ARG, "mg_vcycle: null argument");
+    return vcycle<double>(c, c->L64, 0, rhs, p);
+}
+
+int mg_divergence(mg_ctx *c, const double *const u[3], double dt, double *rhs)
+{
+    g_err.clear();
+    if (!c || !u || !u[0] || !u[1] || !u[2] || !rhs) return fail(MG_ERR_ARG, "mg_divergence: null argument");
+    if (!(dt > 0.0)) return fail(MG_ERR_ARG, "mg_divergence: dt must be > 0");
+    const LevelArrays<double> &L = c->L64[0];
+    CK(mg::launch_divergence(c->dims[0], 1.0 / (dt * c->g.h), L.bx, L.by, L.bz, u[0], u[1], u[2], rhs, c->s));
+    return MG_OK;
+}
+
+int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double dt, double *const u[3])
+{
+    g_err.clear();
+    if (!c || !u_star || !u || !p) return fail(MG_ERR_ARG, "mg_correct: null argument");
+    for (int a = 0; a < 3; a++)
+        if (!u_star[a] || !u[a]) return fail(MG_ERR_ARG, "mg_correct: null face array");
+    const LevelArrays<double> &L = c->L64[0];
+    CK(mg::launch_correct(c->dims[0], dt, c->g.h, L.bx, L.by, L.bz, p, u_star[0], u_star[1], u_star[2], u[0], u[1],
+                          u[2], c->s));
+    return MG_OK;
+}
+
+int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], double *p, double dt, double tol,
+               mg_stats *stats)
+{
+    g_err.clear();
+    if (!c || !u_star || !u || !p) return fail(MG_ERR_ARG, "mg_project: null argument");
+    for (int a = 0; a < 3; a++)
+        if (!u_star[a] || !u[a]) return fail(MG_ERR_ARG, "mg_project: null face array");
+    if (!(dt > 0.0) || !(tol > 0.0)) return fail(MG_ERR_ARG, "mg_project: dt and tol must be > 0");
+    CKS(ensure(c, &c->rhs_tmp, c->dims[0].n()));
+    CKS(mg_divergence(c, u_star, dt, c->rhs_tmp));
+    const int st = solve_impl(c, c->rhs_tmp, p, tol, stats);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    const std::string keep = g_err;
+    CKS(mg_correct(c, u_star, p, dt, u));
+    g_err = keep;
+    return st;
+}
+
+int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, double dt, double tol,
+                       double *const grad_u[3], double *const grad_beta[3], double *q_out, mg_stats *stats)
+{
+    g_err.clear();
+    if (!c || !w || !p || !grad_u) return fail(MG_ERR_ARG, "mg_project_adjoint: null argument");
+    for (int a = 0; a < 3; a++) {
+        if (!w[a] || !grad_u[a]) return fail(MG_ERR_ARG, "mg_project_adjoint: null face array");
+        for (int b = 0; b < 3; b++)
+            if ((const double *)grad_u[a] == w[b]) return fail(MG_ERR_ARG, "mg_project_adjoint: grad_u aliases w");
+    }
+    if (!(dt > 0.0) || !(tol > 0.0)) return fail(MG_ERR_ARG, "mg_project_adjoint: dt and tol must be > 0");
+    const size_t n = c->dims[0].n();
+    CKS(ensure(c, &c->rhs_tmp, n));
+    double *q = q_out;
+    if (!q) {
+        CKS(ensure(c, &c->qbuf, n));
+        q = c->qbuf;
+        CK(cudaMemsetAsync(q, 0, n * sizeof(double), c->s));
+    }
+    const LevelArrays<double> &L = c->L64[0];
+    // beta * w into grad_u (used as scratch), then c = D(beta w)
+    CK(mg::launch_face_mul(n, L.bx, L.by, L.bz, w[0], w[1], w[2], grad_u[0], grad_u[1], grad_u[2], c->s));
+    CK(mg::launch_divergence(c->dims[0], 1.0 / c->g.h, L.bx, L.by, L.bz, grad_u[0], grad_u[1], grad_u[2], c->rhs_tmp,
+                             c->s));
+    const int st = solve_impl(c, c->rhs_tmp, q, tol, stats);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    const std::string keep = g_err;
+    double *gb[3] = {nullptr, nullptr, nullptr};
+    if (grad_beta)
+        for (int a = 0; a < 3; a++) gb[a] = grad_beta[a];
+    CK(mg::launch_adjoint_faces(c->dims[0], c->g.h, dt, L.bx, L.by, L.bz, p, q, w[0], w[1], w[2], grad_u[0],
+                                grad_u[1], grad_u[2], gb[0], gb[1], gb[2], c->s));
+    g_err = keep;
+    return st;
+}
+
+int mg_phi_grad(const mg_grid *g, const double *const beta[3], const double *const grad_beta[3], double rho_air,
+                double rho_water, double *grad_phi, void *stream)
+{
+    g_err.clear();
+    if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_phi_grad: bad grid");
+    if (!beta || !grad_beta || !grad_phi) return fail(MG_ERR_ARG, "mg_phi_grad: null argument");
+    for (int a = 0; a < 3; a++)
+        if (!beta[a] || !grad_beta[a]) return fail(MG_ERR_ARG, "mg_phi_grad: null face array");
+    const Dims d{g->nx, g->ny, g->nz};
+    CK(mg::launch_phi_grad(d, -0.5 * (rho_water - rho_air), beta[0], beta[1], beta[2], grad_beta[0], grad_beta[1],
+                           grad_beta[2], grad_phi, (cudaStream_t)stream));
+    return MG_OK;
+}
+
+int mg_num_levels(const mg_ctx *c) { return c ? c->nlev : 0; }
+
+int mg_level_dims(const mg_ctx *c, int level, int dims[3])
+{
+    if (!c || !dims || level < 0 || level >= c->nlev) return fail(MG_ERR_ARG, "mg_level_dims: bad level");
+    dims[0] = c->dims[level].nx;
+    dims[1] = c->dims[level].ny;
+    dims[2] = c->dims[level].nz;
+    return MG_OK;
+}
+
+int mg_level_array(mg_ctx *c, int level, int which, double *out)
+{
+    g_err.clear();
+    if (!c || !out || level < 0 || level >= c->nlev || which < 0 || which > 3)
+        return fail(MG_ERR_ARG, "mg_level_array: bad argument");
+    const LevelArrays<double> &L = c->L64[level];
+    const double *src = which == 0 ? L.bx : which == 1 ? L.by : which == 2 ? L.bz : L.dinv;
+    CK(cudaMemcpyAsync(out, src, c->dims[level].n() * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    return MG_OK;
+}
+
+uint64_t mg_kernel_launches(void) { return (uint64_t)mg::launch_count(); }
+
+int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total)
+{
+    g_err.clear();
+    if (!c || group < 0 || group >= MG_PROF_GROUPS) return fail(MG_ERR_ARG, "mg_profile_read: bad argument");
+    int n = 0;
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < c->pused; i += 2) {
+        if (c->pgroup[i / 2] != group) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->pev[i], c->pev[i + 1]));
+        tot += ms;
+        n++;
+    }
+    if (count) *count = n;
+    if (ms_total) *ms_total = tot;
+    return MG_OK;
+}
+
+void mg_profile_reset(mg_ctx *c)
+{
+    if (c) c->pused = 0;
+}
+
+void mg_destroy(mg_ctx *c)
+{
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    else cudaDeviceSynchronize();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// mg_internal.cuh -- internal declarations shared by the CUDA kernels and the C ABI host code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mgproj.h"
+
+namespace mg {
+
+// Geometry of one grid level.  Cell (i,j,k) is at linear index (k*ny + j)*nx + i.
+struct Dims {
+    int nx, ny, nz;
+    size_t n() const { return (size_t)nx * ny * nz; }
+};
+
+// Arrays of one multigrid level in one precision.
+template <typename T>
+struct LevelArrays {
+    T *bx = nullptr, *by = nullptr, *bz = nullptr;  // low-face coefficients
+    T *dinv = nullptr;                               // 1 / sum of the six face coefficients (0 if none open)
+    T *b = nullptr;                                  // right-hand side (levels >= 1; level 0 owned elsewhere)
+    T *p = nullptr;                                  // correction (levels >= 1)
+};
+
+// Number of CTAs of the grid-stride reduction kernels (a multiple of the 152 SMs).
+constexpr int kRedBlocks = 608;
+constexpr int kRedThreads = 256;
+
+// Device scalar slots (FP64) in ctx->dscal.
+enum Scal {
+    S_SUM_B = 0,   // sum of the rhs over live cells
+    S_NB2 = 1,     // ||b0||^2 after mean removal
+    S_RR = 2,      // ||b0 - A p||^2 of the last residual pass
+    S_SUM_P = 3,   // sum of p over live cells (same pass)
+    S_SCALE0 = 4,  // mixed refinement: scale of the FP32 residual (ping)
+    S_SCALE1 = 5,  // (pong)
+    S_NLIVE = 6,   // number of live fine cells (as double)
+    S_COUNT = 16
+};
+
+// total kernels launched by this library in this process
+unsigned long long launch_count();
+
+// ---- kernel launchers (mg_kernels.cu); all stream-ordered, return cudaError_t of the launch ----
+cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
+                               double *bx, double *by, double *bz, cudaStream_t s);
+template <typename T>
+cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s);
+cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
+                                   double *cby, double *cbz, cudaStream_t s);
+cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s);
+template <typename T>
+cudaError_t launch_resid_restrict(Dims fine, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
+                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s);
+
+// reductions and fine-level helpers (FP64)
+cudaError_t launch_count_live(Dims d, const double *dinv, double *partials, double *dscal, cudaStream_t s);
+cudaError_t launch_rhs_prepare(Dims d, const double *rhs, const double *dinv, double *b0, double *partials,
+                               double *dscal, cudaStream_t s);
+cudaError_t launch_resid_norm(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
+                              double *partials, double *dscal, cudaStream_t s);
+cudaError_t launch_sub_mean_p(Dims d, const double *dinv, double *p, const double *dscal, cudaStream_t s);
+cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
+                              float *r32, double *partials, double *dscal, int scale_in, int scale_out,
+                              cudaStream_t s);
+cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, double *p, const double *dscal,
+                              int scale_slot, cudaStream_t s);
+
+// projection and adjoint
+cudaError_t launch_divergence(Dims d, double scale, const double *bx, const double *by, const double *bz,
+                              const double *ux, const double *uy, const double *uz, double *rhs, cudaStream_t s);
+cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const double *by, const double *bz,
+                           const double *p, const double *ux0, const double *uy0, const double *uz0, double *ux,
+                           double *uy, double *uz, cudaStream_t s);
+cudaError_t launch_face_mul(size_t n, const double *bx, const double *by, const double *bz, const double *wx,
+                            const double *wy, const double *wz, double *ox, double *oy, double *oz,
+                            cudaStream_t s);
+cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, const double *by,
+                                 const double *bz, const double *p, const double *q, const double *wx,
+                                 const double *wy, const double *wz, double *gux, double *guy, double *guz,
+                                 double *gbx, double *gby, double *gbz, cudaStream_t s);
+cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, const double *by, const double *bz,
+                            const double *gbx, const double *gby, const double *gbz, double *gphi,
+                            cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,707 @@
+// mg_kernels.cu -- CUDA kernels (sm_103a) of the variable-density pressure projection.
+//
+// Every kernel works on one grid level stored in C order [k][j][i] (x fastest).
+// Face arrays hold the LOW face of each cell: bx[c] couples cells c-1 and c in x;
+// bx[.][.][0] is the wall (0).  The high wall face is not stored (closed).
+// A "live" cell has at least one open face (dinv > 0); other cells (solid or
+// isolated) hold p = 0 and are excluded from means and norms.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "mg_internal.cuh"
+
+namespace mg {
+
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+constexpr int kRowThreads = 128;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  NT = blockDim.x.
+template <int NT>
+__device__ double block_sum(double v)
+{
+    __shared__ double sh[NT / 32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < NT / 32) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Sums the per-block partial pairs in a fixed order (deterministic) into dscal.
+__global__ void k_finish2(const double *__restrict__ partials, int nblocks, double *__restrict__ dscal, int slot0,
+                          int slot1)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        a += partials[2 * i];
+        b += partials[2 * i + 1];
+    }
+    a = block_sum<kRedThreads>(a);
+    b = block_sum<kRedThreads>(b);
+    if (threadIdx.x == 0) {
+        if (slot0 >= 0) dscal[slot0] = a;
+        if (slot1 >= 0) dscal[slot1] = b;
+    }
+}
+
+__device__ __forceinline__ void cell_of(unsigned idx, int nx, int ny, int &i, int &j, int &k)
+{
+    const unsigned t = idx / (unsigned)nx;
+    i = (int)(idx - t * (unsigned)nx);
+    k = (int)(t / (unsigned)ny);
+    j = (int)(t - (unsigned)k * (unsigned)ny);
+}
+
+// ---------------------------------------------------------------------------
+// Face coefficients (Eq. density, H(phi) = phi; face product (1/rho)*area):
+// rho = rho_a + drho*phi, beta = 2/(rho_L + rho_R) on open faces.  Rounded as
+// separate IEEE operations (no contraction) so that it is reproducible.
+// ---------------------------------------------------------------------------
+__global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__ phi,
+                              const uint8_t *__restrict__ solid, double rho_a, double drho, double *__restrict__ bx,
+                              double *__restrict__ by, double *__restrict__ bz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    const bool sc = solid && solid[c];
+    const double rc = __dadd_rn(rho_a, __dmul_rn(drho, phi[c]));
+    double v = 0.0;
+    if (i > 0 && !sc && !(solid && solid[c - 1])) v = 2.0 / __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - 1])), rc);
+    bx[c] = v;
+    v = 0.0;
+    if (j > 0 && !sc && !(solid && solid[c - nx])) v = 2.0 / __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - nx])), rc);
+    by[c] = v;
+    v = 0.0;
+    if (k > 0 && !sc && !(solid && solid[c - sxy])) v = 2.0 / __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - sxy])), rc);
+    bz[c] = v;
+}
+
+// dinv = 1 / (sum of the six face coefficients), summed x-, x+, y-, y+, z-, z+; 0 if none is open.
+template <typename T>
+__global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, const T *__restrict__ by,
+                           const T *__restrict__ bz, T *__restrict__ dinv)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    T s = bx[c];
+    s += (i < nx - 1) ? bx[c + 1] : T(0);
+    s += by[c];
+    s += (j < ny - 1) ? by[c + nx] : T(0);
+    s += bz[c];
+    s += (k < nz - 1) ? bz[c + sxy] : T(0);
+    dinv[c] = (s > T(0)) ? T(1) / s : T(0);
+}
+
+// Coarse face coefficient = mean of the 2x2 coplanar fine faces it covers.
+__global__ void k_restrict_coeffs(int nx, int ny, int nz, const double *__restrict__ bx,
+                                  const double *__restrict__ by, const double *__restrict__ bz,
+                                  double *__restrict__ cbx, double *__restrict__ cby, double *__restrict__ cbz)
+{
+    const int NX = nx / 2, NY = ny / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= NX) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t f = (size_t)(2 * K) * sxy + (size_t)(2 * J) * nx + 2 * I;  // fine cell (2I, 2J, 2K)
+    const size_t C = ((size_t)K * NY + J) * NX + I;
+    cbx[C] = 0.25 * (((bx[f] + bx[f + nx]) + bx[f + sxy]) + bx[f + sxy + nx]);
+    cby[C] = 0.25 * (((by[f] + by[f + 1]) + by[f + sxy]) + by[f + sxy + 1]);
+    cbz[C] = 0.25 * (((bz[f] + bz[f + 1]) + bz[f + nx]) + bz[f + nx + 1]);
+}
+
+__global__ void k_cast_f32(size_t n, const double *__restrict__ src, float *__restrict__ dst)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Red-black Gauss-Seidel, one colour ((i+j+k) mod 2 == colour).  Each thread
+// owns the one cell of that colour in an x-pair of a row:
+//     p_c = dinv_c * (sum_f beta_f p_nb - h^2 b_c),  sum order x-,x+,y-,y+,z-,z+,
+// products accumulated with fused multiply-adds in that order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T *__restrict__ b,
+                         T *__restrict__ p, int colour)
+{
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    T s = T(0);
+    if (i > 0) s = fma(L.bx[c], p[c - 1], s);
+    if (i < nx - 1) s = fma(L.bx[c + 1], p[c + 1], s);
+    if (j > 0) s = fma(L.by[c], p[c - nx], s);
+    if (j < ny - 1) s = fma(L.by[c + nx], p[c + nx], s);
+    if (k > 0) s = fma(L.bz[c], p[c - sxy], s);
+    if (k < nz - 1) s = fma(L.bz[c + sxy], p[c + sxy], s);
+    p[c] = L.dinv[c] * fma(-h2, b[c], s);
+}
+
+// r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
+template <typename T>
+__device__ __forceinline__ T residual_at(int i, int j, int k, size_t c, int nx, int ny, int nz, size_t sxy, T ih2,
+                                         const LevelArrays<T> &L, const T *__restrict__ b,
+                                         const T *__restrict__ p)
+{
+    const T pc = p[c];
+    T s = T(0);
+    if (i > 0) s = fma(L.bx[c], p[c - 1] - pc, s);
+    if (i < nx - 1) s = fma(L.bx[c + 1], p[c + 1] - pc, s);
+    if (j > 0) s = fma(L.by[c], p[c - nx] - pc, s);
+    if (j < ny - 1) s = fma(L.by[c + nx], p[c + nx] - pc, s);
+    if (k > 0) s = fma(L.bz[c], p[c - sxy] - pc, s);
+    if (k < nz - 1) s = fma(L.bz[c + sxy], p[c + sxy] - pc, s);
+    return fma(-s, ih2, b[c]);
+}
+
+// Residual and cell-centred full weighting: coarse b = mean of the 8 children's residuals.
+template <typename T>
+__global__ void k_resid_restrict(int nx, int ny, int nz, T ih2, LevelArrays<T> L, const T *__restrict__ b,
+                                 const T *__restrict__ p, T *__restrict__ bc)
+{
+    const int NX = nx / 2, NY = ny / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= NX) return;
+    const size_t sxy = (size_t)nx * ny;
+    T s = T(0);
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++)
+#pragma unroll
+            for (int di = 0; di < 2; di++) {
+                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+                s += residual_at<T>(i, j, k, c, nx, ny, nz, sxy, ih2, L, b, p);
+            }
+    bc[((size_t)K * NY + J) * NX + I] = T(0.125) * s;
+}
+
+// Trilinear cell-centred prolongation added to p: weights 3/4 (parent) and 1/4 (next
+// coarse cell on the fine cell's side) per axis; that index clamps at walls.
+template <typename T>
+__global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, const T *__restrict__ dinv,
+                          T *__restrict__ p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t c = ((size_t)k * ny + j) * nx + i;
+    if (dinv[c] == T(0)) return;
+    const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int I1 = min(max((i & 1) ? I0 + 1 : I0 - 1, 0), NX - 1);
+    const int J1 = min(max((j & 1) ? J0 + 1 : J0 - 1, 0), NY - 1);
+    const int K1 = min(max((k & 1) ? K0 + 1 : K0 - 1, 0), NZ - 1);
+    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
+    const T w[2] = {T(0.75), T(0.25)};
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int bb = 0; bb < 2; bb++)
+#pragma unroll
+            for (int d = 0; d < 2; d++)
+                s = fma(w[a] * w[bb] * w[d], ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]], s);
+    p[c] += s;
+}
+
+// Exact coarsest-grid solve e = M b with the dense minimum-norm inverse M (FP64 always).
+template <typename T>
+__global__ void k_coarse_solve(int n, const double *__restrict__ M, const T *__restrict__ b, T *__restrict__ e)
+{
+    extern __shared__ double sb[];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)b[i];
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const double *row = M + (size_t)r * n;
+        double s = 0.0;
+        for (int q = 0; q < n; q++) s += row[q] * sb[q];
+        e[r] = (T)s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fine-level reductions (FP64, grid-stride, per-block partial pairs)
+// ---------------------------------------------------------------------------
+__global__ void k_count_live(unsigned n, const double *__restrict__ dinv, double *__restrict__ partials)
+{
+    double a = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        a += (dinv[idx] > 0.0) ? 1.0 : 0.0;
+    a = block_sum<kRedThreads>(a);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// pass 1 of the rhs preparation: sum of rhs over live cells
+__global__ void k_sum_live(unsigned n, const double *__restrict__ v, const double *__restrict__ dinv,
+                           double *__restrict__ partials)
+{
+    double a = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        if (dinv[idx] > 0.0) a += v[idx];
+    a = block_sum<kRedThreads>(a);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// pass 2: b0 = rhs - mean on live cells, 0 elsewhere; partial ||b0||^2
+__global__ void k_rhs_center(unsigned n, const double *__restrict__ rhs, const double *__restrict__ dinv,
+                             double *__restrict__ b0, const double *__restrict__ dscal, double *__restrict__ partials)
+{
+    const double mean = dscal[S_SUM_B] / dscal[S_NLIVE];
+    double a = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const double v = (dinv[idx] > 0.0) ? rhs[idx] - mean : 0.0;
+        b0[idx] = v;
+        a += v * v;
+    }
+    a = block_sum<kRedThreads>(a);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// ||b - A p||^2 and sum of p over live cells
+__global__ void k_resid_norm(int nx, int ny, int nz, double ih2, LevelArrays<double> L,
+                             const double *__restrict__ b, const double *__restrict__ p, double *__restrict__ partials)
+{
+    const unsigned n = (unsigned)nx * ny * nz;
+    const size_t sxy = (size_t)nx * ny;
+    double rr = 0.0, sp = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(idx, nx, ny, i, j, k);
+        const double r = residual_at<double>(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        rr += r * r;
+        if (L.dinv[idx] > 0.0) sp += p[idx];
+    }
+    rr = block_sum<kRedThreads>(rr);
+    sp = block_sum<kRedThreads>(sp);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = rr;
+        partials[2 * blockIdx.x + 1] = sp;
+    }
+}
+
+// p -= mean of p over live cells (mean = dscal[S_SUM_P] / dscal[S_NLIVE]); dead cells 0
+__global__ void k_sub_mean_p(unsigned n, const double *__restrict__ dinv, double *__restrict__ p,
+                             const double *__restrict__ dscal)
+{
+    const double mean = dscal[S_SUM_P] / dscal[S_NLIVE];
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        p[idx] = (dinv[idx] > 0.0) ? p[idx] - mean : 0.0;
+}
+
+// Mixed refinement: r = b - A p in FP64, stored as FP32 r / scale_in; partial ||r||^2.
+__global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<double> L,
+                             const double *__restrict__ b, const double *__restrict__ p, float *__restrict__ r32,
+                             const double *__restrict__ dscal, int scale_in, double *__restrict__ partials)
+{
+    const unsigned n = (unsigned)nx * ny * nz;
+    const size_t sxy = (size_t)nx * ny;
+    const double inv_scale = 1.0 / dscal[scale_in];
+    double rr = 0.0, sp = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(idx, nx, ny, i, j, k);
+        const double r = residual_at<double>(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        rr += r * r;
+        if (L.dinv[idx] > 0.0) sp += p[idx];
+        r32[idx] = (float)(r * inv_scale);
+    }
+    rr = block_sum<kRedThreads>(rr);
+    sp = block_sum<kRedThreads>(sp);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = rr;
+        partials[2 * blockIdx.x + 1] = sp;
+    }
+}
+
+// next scale = RMS of the residual over live cells (1 if zero)
+__global__ void k_set_scale(double *dscal, int slot)
+{
+    const double rms = sqrt(dscal[S_RR] / dscal[S_NLIVE]);
+    dscal[slot] = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
+}
+
+__global__ void k_scale_from_nb2(double *dscal, int slot)
+{
+    const double rms = sqrt(dscal[S_NB2] / dscal[S_NLIVE]);
+    dscal[slot] = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
+}
+
+// p += scale * e32 (the FP32 cycle leaves e32 = 0 on dead cells, so no mask is read)
+__global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *__restrict__ p,
+                             const double *__restrict__ dscal, int scale_slot)
+{
+    const double s = dscal[scale_slot];
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        p[idx] = fma(s, (double)e32[idx], p[idx]);
+}
+
+// ---------------------------------------------------------------------------
+// Projection (Eq. poisson1 right-hand side; Eq. runge1 correction) and adjoint
+// ---------------------------------------------------------------------------
+__global__ void k_divergence(int nx, int ny, int nz, double scale, const double *__restrict__ bx,
+                             const double *__restrict__ by, const double *__restrict__ bz,
+                             const double *__restrict__ ux, const double *__restrict__ uy,
+                             const double *__restrict__ uz, double *__restrict__ rhs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    double d = 0.0;
+    if (i < nx - 1 && bx[c + 1] > 0.0) d += ux[c + 1];
+    if (bx[c] > 0.0) d -= ux[c];
+    if (j < ny - 1 && by[c + nx] > 0.0) d += uy[c + nx];
+    if (by[c] > 0.0) d -= uy[c];
+    if (k < nz - 1 && bz[c + sxy] > 0.0) d += uz[c + sxy];
+    if (bz[c] > 0.0) d -= uz[c];
+    rhs[c] = scale * d;
+}
+
+// u_f = u*_f - dt beta_f (p_c - p_nb) / h on open low faces; closed faces copy u*.
+__global__ void k_correct(int nx, int ny, int nz, double dt, double h, const double *__restrict__ bx,
+                          const double *__restrict__ by, const double *__restrict__ bz, const double *__restrict__ p,
+                          const double *ux0, const double *uy0, const double *uz0, double *ux, double *uy, double *uz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    const double pc = p[c];
+    double b = bx[c], u = ux0[c];
+    if (i > 0 && b > 0.0) u = __dsub_rn(u, __dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - 1])) / h);
+    ux[c] = u;
+    b = by[c];
+    u = uy0[c];
+    if (j > 0 && b > 0.0) u = __dsub_rn(u, __dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - nx])) / h);
+    uy[c] = u;
+    b = bz[c];
+    u = uz0[c];
+    if (k > 0 && b > 0.0) u = __dsub_rn(u, __dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - sxy])) / h);
+    uz[c] = u;
+}
+
+__global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double *__restrict__ by,
+                           const double *__restrict__ bz, const double *__restrict__ wx, const double *__restrict__ wy,
+                           const double *__restrict__ wz, double *__restrict__ ox, double *__restrict__ oy,
+                           double *__restrict__ oz)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        ox[i] = __dmul_rn(bx[i], wx[i]);
+        oy[i] = __dmul_rn(by[i], wy[i]);
+        oz[i] = __dmul_rn(bz[i], wz[i]);
+    }
+}
+
+// grad_u = w - G q (open faces) / w (closed);  grad_beta = dt (G p)((G q) - w) (open) / 0 (closed)
+__device__ __forceinline__ void adj_face(double b, double pc, double pn, double qc, double qn, double w, double h,
+                                         double dt, double &gu, double &gb)
+{
+    if (b > 0.0) {
+        const double gq = __dsub_rn(qc, qn) / h;
+        const double gp = __dsub_rn(pc, pn) / h;
+        gu = __dsub_rn(w, gq);
+        gb = __dmul_rn(__dmul_rn(dt, gp), __dsub_rn(gq, w));
+    } else {
+        gu = w;
+        gb = 0.0;
+    }
+}
+
+__global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double dt, const double *__restrict__ bx,
+                                const double *__restrict__ by, const double *__restrict__ bz,
+                                const double *__restrict__ p, const double *__restrict__ q,
+                                const double *__restrict__ wx, const double *__restrict__ wy,
+                                const double *__restrict__ wz, double *gux, double *guy, double *guz, double *gbx,
+                                double *gby, double *gbz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    const double pc = p[c], qc = q[c];
+    double gu, gb;
+    adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, dt, gu, gb);
+    gux[c] = gu;
+    if (gbx) gbx[c] = gb;
+    adj_face(by[c], pc, j > 0 ? p[c - nx] : 0.0, qc, j > 0 ? q[c - nx] : 0.0, wy[c], h, dt, gu, gb);
+    guy[c] = gu;
+    if (gby) gby[c] = gb;
+    adj_face(bz[c], pc, k > 0 ? p[c - sxy] : 0.0, qc, k > 0 ? q[c - sxy] : 0.0, wz[c], h, dt, gu, gb);
+    guz[c] = gu;
+    if (gbz) gbz[c] = gb;
+}
+
+// grad_phi_c = -(drho/2) sum over the six faces of beta_f^2 grad_beta_f (order x-,x+,y-,y+,z-,z+)
+__global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const double *__restrict__ bx,
+                           const double *__restrict__ by, const double *__restrict__ bz,
+                           const double *__restrict__ gbx, const double *__restrict__ gby,
+                           const double *__restrict__ gbz, double *__restrict__ gphi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    double s = 0.0;
+    s = __dadd_rn(s, __dmul_rn(__dmul_rn(bx[c], bx[c]), gbx[c]));
+    if (i < nx - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(bx[c + 1], bx[c + 1]), gbx[c + 1]));
+    s = __dadd_rn(s, __dmul_rn(__dmul_rn(by[c], by[c]), gby[c]));
+    if (j < ny - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(by[c + nx], by[c + nx]), gby[c + nx]));
+    s = __dadd_rn(s, __dmul_rn(__dmul_rn(bz[c], bz[c]), gbz[c]));
+    if (k < nz - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(bz[c + sxy], bz[c + sxy]), gbz[c + sxy]));
+    gphi[c] = __dmul_rn(neg_half_drho, s);
+}
+
+inline dim3 row_grid(int threads_x, int ny, int nz)
+{
+    return dim3((unsigned)((threads_x + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)nz);
+}
+
+inline unsigned red_grid(size_t n)
+{
+    size_t b = (n + kRedThreads - 1) / kRedThreads;
+    return (unsigned)(b < (size_t)kRedBlocks ? (b ? b : 1) : kRedBlocks);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
+                               double *bx, double *by, double *bz, cudaStream_t s)
+{
+    note_launch();
+    k_face_coeffs<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, phi, solid, rho_a, drho, bx, by,
+                                                                      bz);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s)
+{
+    note_launch();
+    k_diag_inv<T><<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv);
+    return cudaGetLastError();
+}
+template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *,
+                                             cudaStream_t);
+template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, cudaStream_t);
+
+cudaError_t launch_restrict_coeffs(Dims f, const double *bx, const double *by, const double *bz, double *cbx,
+                                   double *cby, double *cbz, cudaStream_t s)
+{
+    note_launch();
+    k_restrict_coeffs<<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, bx, by, bz, cbx,
+                                                                                      cby, cbz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s)
+{
+    note_launch();
+    k_cast_f32<<<red_grid(n), kRedThreads, 0, s>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s)
+{
+    note_launch();
+    k_smooth<T><<<row_grid((d.nx + 1) / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour);
+    return cudaGetLastError();
+}
+template cudaError_t launch_smooth<double>(Dims, double, const LevelArrays<double> &, const double *, double *, int,
+                                           cudaStream_t);
+template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> &, const float *, float *, int,
+                                          cudaStream_t);
+
+template <typename T>
+cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
+                                  cudaStream_t s)
+{
+    note_launch();
+    k_resid_restrict<T><<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p,
+                                                                                        bc);
+    return cudaGetLastError();
+}
+template cudaError_t launch_resid_restrict<double>(Dims, double, const LevelArrays<double> &, const double *,
+                                                   const double *, double *, cudaStream_t);
+template cudaError_t launch_resid_restrict<float>(Dims, float, const LevelArrays<float> &, const float *,
+                                                  const float *, float *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s)
+{
+    note_launch();
+    k_prolong<T><<<row_grid(f.nx, f.ny, f.nz), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p);
+    return cudaGetLastError();
+}
+template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t);
+template cudaError_t launch_prolong<float>(Dims, const float *, const float *, float *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s)
+{
+    note_launch();
+    k_coarse_solve<T><<<1, 256, (size_t)n * sizeof(double), s>>>(n, M, b, e);
+    return cudaGetLastError();
+}
+template cudaError_t launch_coarse_solve<double>(int, const double *, const double *, double *, cudaStream_t);
+template cudaError_t launch_coarse_solve<float>(int, const double *, const float *, float *, cudaStream_t);
+
+cudaError_t launch_count_live(Dims d, const double *dinv, double *partials, double *dscal, cudaStream_t s)
+{
+    const unsigned g = red_grid(d.n());
+    note_launch();
+    k_count_live<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), dinv, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_NLIVE, -1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_prepare(Dims d, const double *rhs, const double *dinv, double *b0, double *partials,
+                               double *dscal, cudaStream_t s)
+{
+    const unsigned g = red_grid(d.n());
+    note_launch();
+    k_sum_live<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), rhs, dinv, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_SUM_B, -1);
+    note_launch();
+    k_rhs_center<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), rhs, dinv, b0, dscal, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_NB2, -1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_norm(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
+                              double *partials, double *dscal, cudaStream_t s)
+{
+    const unsigned g = red_grid(d.n());
+    note_launch();
+    k_resid_norm<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_mean_p(Dims d, const double *dinv, double *p, const double *dscal, cudaStream_t s)
+{
+    note_launch();
+    k_sub_mean_p<<<red_grid(d.n()), kRedThreads, 0, s>>>((unsigned)d.n(), dinv, p, dscal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
+                              float *r32, double *partials, double *dscal, int scale_in, int scale_out,
+                              cudaStream_t s)
+{
+    const unsigned g = red_grid(d.n());
+    if (scale_in < 0) {  // first pass: scale from ||b0||
+        scale_in = S_SCALE0;
+        note_launch();
+        k_scale_from_nb2<<<1, 1, 0, s>>>(dscal, scale_in);
+    }
+    note_launch();
+    k_resid_cast<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r32, dscal, scale_in, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
+    note_launch();
+    k_set_scale<<<1, 1, 0, s>>>(dscal, scale_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, double *p, const double *dscal,
+                              int scale_slot, cudaStream_t s)
+{
+    note_launch();
+    (void)dinv;
+    k_accumulate<<<red_grid(d.n()), kRedThreads, 0, s>>>((unsigned)d.n(), e32, p, dscal, scale_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divergence(Dims d, double scale, const double *bx, const double *by, const double *bz,
+                              const double *ux, const double *uy, const double *uz, double *rhs, cudaStream_t s)
+{
+    note_launch();
+    k_divergence<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, scale, bx, by, bz, ux, uy, uz,
+                                                                     rhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const double *by, const double *bz,
+                           const double *p, const double *ux0, const double *uy0, const double *uz0, double *ux,
+                           double *uy, double *uz, cudaStream_t s)
+{
+    note_launch();
+    k_correct<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, dt, h, bx, by, bz, p, ux0, uy0, uz0,
+                                                                  ux, uy, uz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_mul(size_t n, const double *bx, const double *by, const double *bz, const double *wx,
+                            const double *wy, const double *wz, double *ox, double *oy, double *oz, cudaStream_t s)
+{
+    note_launch();
+    k_face_mul<<<red_grid(n), kRedThreads, 0, s>>>(n, bx, by, bz, wx, wy, wz, ox, oy, oz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, const double *by, const double *bz,
+                                 const double *p, const double *q, const double *wx, const double *wy,
+                                 const double *wz, double *gux, double *guy, double *guz, double *gbx, double *gby,
+                                 double *gbz, cudaStream_t s)
+{
+    note_launch();
+    k_adjoint_faces<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h, dt, bx, by, bz, p, q, wx,
+                                                                        wy, wz, gux, guy, guz, gbx, gby, gbz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, const double *by, const double *bz,
+                            const double *gbx, const double *gby, const double *gbz, double *gphi, cudaStream_t s)
+{
+    note_launch();
+    k_phi_grad<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, neg_half_drho, bx, by, bz, gbx,
+                                                                   gby, gbz, gphi);
+    return cudaGetLastError();
+}
+
+}  // namespace mg

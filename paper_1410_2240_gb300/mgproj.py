@@ -1,0 +1,279 @@
+"""ctypes binding of libmgproj.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in ``include/mgproj.h`` with
+the same name; all arithmetic runs in the library's CUDA kernels.  Tensors are
+torch CUDA tensors (device memory and streams come from PyTorch): float64,
+contiguous, shape (nz, ny, nx); face fields are 3-tuples of such tensors in the
+low-face layout.  Importing this module loads the library and raises if it has
+not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from .build import LIB
+
+MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, MG_ERR_NAN, MG_ERR_OOM = 0, 1, 2, 3, 4, 6
+MG_FP64, MG_MIXED = 0, 1
+
+if not os.path.exists(LIB):
+    raise ImportError(f"{LIB} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "or `python -m paper_1410_2240_gb300.build`")
+_lib = ctypes.CDLL(LIB)
+
+_vp = ctypes.c_void_p
+_P3 = _vp * 3
+_PP = ctypes.POINTER(_vp)  # double *const x[3]; an _P3 instance or None
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double)]
+
+
+class Bc(ctypes.Structure):
+    _fields_ = [("wall", ctypes.c_int * 6)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("coarse_max_cells", ctypes.c_int), ("prec", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("rel_resid", ctypes.c_double), ("rhs_norm", ctypes.c_double),
+                ("rhs_mean_removed", ctypes.c_double), ("resid_hist", ctypes.c_double * 256),
+                ("ms_setup", ctypes.c_float), ("ms_solve", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"cycles": self.cycles, "rel_resid": self.rel_resid, "rhs_norm": self.rhs_norm,
+                "rhs_mean_removed": self.rhs_mean_removed,
+                "resid_hist": list(self.resid_hist[: max(0, min(self.cycles, 256))]),
+                "ms_setup": self.ms_setup, "ms_solve": self.ms_solve}
+
+
+_lib.mg_default_opts.argtypes = [ctypes.POINTER(Opts)]
+_lib.mg_last_error.restype = ctypes.c_char_p
+_lib.mg_face_coeffs.argtypes = [ctypes.POINTER(Grid), _vp, _vp, ctypes.c_double, ctypes.c_double, _PP, _vp]
+_lib.mg_setup.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Grid), _PP, ctypes.POINTER(Bc), _vp,
+                          ctypes.POINTER(Opts), _vp]
+_lib.mg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(Stats)]
+_lib.mg_vcycle.argtypes = [_vp, _vp, _vp]
+_lib.mg_divergence.argtypes = [_vp, _PP, ctypes.c_double, _vp]
+_lib.mg_correct.argtypes = [_vp, _PP, _vp, ctypes.c_double, _PP]
+_lib.mg_project.argtypes = [_vp, _PP, _PP, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Stats)]
+_lib.mg_project_adjoint.argtypes = [_vp, _PP, _vp, ctypes.c_double, ctypes.c_double, _PP, _PP, _vp,
+                                    ctypes.POINTER(Stats)]
+_lib.mg_phi_grad.argtypes = [ctypes.POINTER(Grid), _PP, _PP, ctypes.c_double, ctypes.c_double, _vp, _vp]
+_lib.mg_num_levels.argtypes = [_vp]
+_lib.mg_level_dims.argtypes = [_vp, ctypes.c_int, ctypes.c_int * 3]
+_lib.mg_level_array.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp]
+_lib.mg_update.argtypes = [_vp, _PP]
+_lib.mg_kernel_launches.restype = ctypes.c_uint64
+_lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+_lib.mg_profile_reset.argtypes = [_vp]
+_lib.mg_destroy.argtypes = [_vp]
+
+PROF_SMOOTH, PROF_RESTRICT, PROF_PROLONG, PROF_RESID64 = 0, 1, 2, 3
+
+
+def kernel_launches() -> int:
+    """mg_kernel_launches: kernels launched by the library so far in this process."""
+    return int(_lib.mg_kernel_launches())
+
+#: every symbol declared in include/mgproj.h
+EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_solve", "mg_vcycle", "mg_divergence",
+           "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
+           "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset", "mg_destroy",
+           "mg_last_error"]
+
+
+class MGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[mgproj status {code}] {msg}")
+        self.code = code
+
+
+class NotConverged(MGError):
+    pass
+
+
+def _check(code, allow_not_converged=False):
+    if code == MG_OK:
+        return code
+    msg = _lib.mg_last_error().decode(errors="replace")
+    if code == MG_ERR_NOT_CONVERGED:
+        if allow_not_converged:
+            return code
+        raise NotConverged(code, msg)
+    raise MGError(code, msg)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, shape, dtype=torch.float64, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}, got {tuple(t.shape)}")
+    return _vp(t.data_ptr())
+
+
+def _faces(fs, shape, name):
+    if len(fs) != 3:
+        raise ValueError(f"{name} must be 3 face arrays")
+    return _P3(*[_dev(f, shape, name=f"{name}[{a}]") for a, f in enumerate(fs)])
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib.mg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = {"fp64": MG_FP64, "mixed": MG_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+def face_coeffs(phi: torch.Tensor, h: float, solid: Optional[torch.Tensor] = None, rho_air: float = 1e-3,
+                rho_water: float = 1.0, out=None, stream=None):
+    """mg_face_coeffs: (bx, by, bz) from phi (and an optional uint8 solid mask)."""
+    nz, ny, nx = phi.shape
+    g = Grid(nx, ny, nz, h)
+    if out is None:
+        out = tuple(torch.empty_like(phi) for _ in range(3))
+    sp = _vp(0) if solid is None else _dev(solid, phi.shape, torch.uint8, "solid")
+    _check(_lib.mg_face_coeffs(ctypes.byref(g), _dev(phi, phi.shape, name="phi"), sp, rho_air, rho_water,
+                               _faces(out, phi.shape, "beta_out"), _stream(stream)))
+    return out
+
+
+def phi_grad(beta: Sequence[torch.Tensor], grad_beta: Sequence[torch.Tensor], h: float, rho_air=1e-3,
+             rho_water=1.0, out=None, stream=None):
+    """mg_phi_grad: chain rule from face coefficients to phi."""
+    shape = beta[0].shape
+    nz, ny, nx = shape
+    g = Grid(nx, ny, nz, h)
+    if out is None:
+        out = torch.empty_like(beta[0])
+    _check(_lib.mg_phi_grad(ctypes.byref(g), _faces(beta, shape, "beta"), _faces(grad_beta, shape, "grad_beta"),
+                            rho_air, rho_water, _dev(out, shape, name="grad_phi"), _stream(stream)))
+    return out
+
+
+class Context:
+    """An mg_ctx: the multigrid hierarchy for one set of face coefficients."""
+
+    def __init__(self, beta: Sequence[torch.Tensor], h: float, solid: Optional[torch.Tensor] = None,
+                 opts: Optional[Opts] = None, stream=None, **kw):
+        self.shape = tuple(beta[0].shape)
+        nz, ny, nx = self.shape
+        self.h = h
+        self.grid = Grid(nx, ny, nz, h)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.opts = opts if opts is not None else default_opts(**kw)
+        self._c = _vp()
+        sp = _vp(0) if solid is None else _dev(solid, self.shape, torch.uint8, "solid")
+        _check(_lib.mg_setup(ctypes.byref(self._c), ctypes.byref(self.grid), _faces(beta, self.shape, "beta"), None,
+                             sp, ctypes.byref(self.opts), _stream(self.stream)))
+        self.last_stats = Stats()
+
+    def close(self):
+        if self._c:
+            _lib.mg_destroy(self._c)
+            self._c = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, beta):
+        """mg_update: rebuild the hierarchy for new face coefficients (same grid, no allocation)."""
+        _check(_lib.mg_update(self._c, _faces(beta, self.shape, "beta")))
+
+    def profile_read(self, group):
+        n = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(_lib.mg_profile_read(self._c, group, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def profile_reset(self):
+        _lib.mg_profile_reset(self._c)
+
+    @property
+    def num_levels(self):
+        return _lib.mg_num_levels(self._c)
+
+    def level_dims(self, level):
+        d = (ctypes.c_int * 3)()
+        _check(_lib.mg_level_dims(self._c, level, d))
+        return tuple(d)
+
+    def level_array(self, level, which):
+        nx, ny, nz = self.level_dims(level)
+        out = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+        _check(_lib.mg_level_array(self._c, level, which, _vp(out.data_ptr())))
+        return out
+
+    def solve(self, rhs, p=None, tol=1e-10, allow_not_converged=False):
+        if p is None:
+            p = torch.zeros_like(rhs)
+        st = Stats()
+        code = _check(_lib.mg_solve(self._c, _dev(rhs, self.shape, name="rhs"), _dev(p, self.shape, name="p"), tol,
+                                    ctypes.byref(st)), allow_not_converged)
+        self.last_stats = st
+        return p, st
+
+    def vcycle(self, rhs, p):
+        _check(_lib.mg_vcycle(self._c, _dev(rhs, self.shape, name="rhs"), _dev(p, self.shape, name="p")))
+        return p
+
+    def divergence(self, u, dt=1.0, out=None):
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        _check(_lib.mg_divergence(self._c, _faces(u, self.shape, "u"), dt, _dev(out, self.shape, name="rhs")))
+        return out
+
+    def correct(self, u_star, p, dt=1.0, out=None):
+        if out is None:
+            out = tuple(torch.empty_like(x) for x in u_star)
+        _check(_lib.mg_correct(self._c, _faces(u_star, self.shape, "u_star"), _dev(p, self.shape, name="p"), dt,
+                               _faces(out, self.shape, "u")))
+        return out
+
+    def project(self, u_star, p=None, dt=1.0, tol=1e-10, out=None, allow_not_converged=False):
+        if p is None:
+            p = torch.zeros(self.shape, dtype=torch.float64, device="cuda")
+        if out is None:
+            out = tuple(torch.empty_like(x) for x in u_star)
+        st = Stats()
+        _check(_lib.mg_project(self._c, _faces(u_star, self.shape, "u_star"), _faces(out, self.shape, "u"),
+                               _dev(p, self.shape, name="p"), dt, tol, ctypes.byref(st)), allow_not_converged)
+        self.last_stats = st
+        return out, p, st
+
+    def project_adjoint(self, w, p, dt=1.0, tol=1e-10, grad_u=None, grad_beta=None, want_grad_beta=True, q=None,
+                        allow_not_converged=False):
+        if grad_u is None:
+            grad_u = tuple(torch.empty_like(x) for x in w)
+        if want_grad_beta and grad_beta is None:
+            grad_beta = tuple(torch.empty_like(x) for x in w)
+        gb = _faces(grad_beta, self.shape, "grad_beta") if grad_beta is not None else None
+        qp = _dev(q, self.shape, name="q") if q is not None else _vp(0)
+        st = Stats()
+        _check(_lib.mg_project_adjoint(self._c, _faces(w, self.shape, "w"), _dev(p, self.shape, name="p"), dt, tol,
+                                       _faces(grad_u, self.shape, "grad_u"), gb, qp, ctypes.byref(st)),
+               allow_not_converged)
+        self.last_stats = st
+        return grad_u, grad_beta, st

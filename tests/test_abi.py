@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/mgproj.h declares.
+
+CPU only: no compute call is made (there may be no GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mgproj.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("mg_setup", "mg_solve", "mg_project", "mg_project_adjoint", "mg_face_coeffs", "mg_phi_grad",
+                 "mg_destroy", "mg_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1410_2240_gb300.build import build
+    lib_path = build()
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mg_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_binding_lists_every_declared_symbol():
+    src = open(os.path.join(ROOT, "paper_1410_2240_gb300", "mgproj.py")).read()
+    m = re.search(r"EXPORTS = \[(.*?)\]", src, re.S)
+    listed = set(re.findall(r'"(mg_\w+)"', m.group(1)))
+    assert listed == set(_declared())
+
+
+def test_library_is_built_for_sm_103a_only():
+    from paper_1410_2240_gb300 import build as B
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_no_cpu_fallback_in_product_package():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_1410_2240_gb300")
+    for fn in os.listdir(pkg):
+        if fn.endswith(".py"):
+            src = open(os.path.join(pkg, fn)).read()
+            assert "import oracle" not in src and "from oracle" not in src, fn

@@ -1,0 +1,179 @@
+"""GPU <-> oracle parity through the C ABI (libmgproj.so via its ctypes binding).
+
+Tolerances: integer/structural results and the operations the library performs as
+separately rounded IEEE operations in the oracle's order (face coefficients, the
+coefficient hierarchy, inverse diagonals, divergence, correction, adjoint faces,
+phi chain rule) are compared bit for bit.  The V-cycle uses fused multiply-adds and
+an independently computed coarsest inverse, so one V-cycle must match the oracle's to
+1e-12 relative (FP64).  Solves must reach relative residual 1e-10 (checked with the
+oracle's operator) and match the oracle's solution to 1e-9 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1410_2240_gb300 import synth
+
+from _gpu_util import case_rhs, cases_small, dev, faces_dev, faces_host, host, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mgp():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_2240_gb300 import mgproj
+    return mgproj
+
+
+SMALL = cases_small()
+
+
+def _ctx(mgp, case, **kw):
+    beta = mgp.face_coeffs(dev(case.phi), case.h, None if case.solid is None else dev(case.solid, dtype=torch.uint8),
+                           rho_air=case.lam, rho_water=1.0)
+    kw.setdefault("coarse_max_cells", 2048)
+    return beta, mgp.Context(beta, case.h, **kw)
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_face_coeffs_and_hierarchy_bit_exact(mgp, name):
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    for a, b in zip(faces_host(beta_g), beta_o):
+        assert np.array_equal(a, b)
+    mg = O.MG(beta_o, case.h, max_coarse=4096)
+    assert ctx.num_levels == mg.nlev
+    for l in range(mg.nlev):
+        assert ctx.level_dims(l) == mg.level_dims(l)
+        for which in range(4):
+            assert np.array_equal(host(ctx.level_array(l, which)), mg.level_array(l, which)), (l, which)
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_vcycle_matches_oracle(mgp, name):
+    """The solver's own iterates: from p = 0, three V-cycles, each restarted from the oracle's
+    iterate.  One GPU V-cycle matches the oracle's to 1e-12 relative."""
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    lab, nc = O.components(beta_o)
+    b = O.remove_mean(case_rhs(case, beta_o), lab, nc)
+    mg = O.MG(beta_o, case.h, max_coarse=4096)
+    p = np.zeros(case.shape)
+    bd = dev(b)
+    for it in range(3):
+        pd = dev(p)
+        p = mg.vcycle(b, p)
+        ctx.vcycle(bd, pd)
+        assert rel(host(pd), p) <= 1e-12, (it, rel(host(pd), p))
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_vcycle_from_rough_start(mgp, name):
+    """From white noise the first cycle's coarse correction excites the coarsest grid's
+    near-null mode, so the map amplifies the (independent, both correct) coarsest inverses'
+    rounding by its condition number (~1e4): the bound is 1e-10 here."""
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    lab, nc = O.components(beta_o)
+    b = O.remove_mean(case_rhs(case, beta_o), lab, nc)
+    mg = O.MG(beta_o, case.h, max_coarse=4096)
+    rng = np.random.default_rng(7)
+    p = np.where(O.diag_inv(beta_o) > 0, rng.standard_normal(case.shape), 0.0)
+    pd = dev(p)
+    ctx.vcycle(dev(b), pd)
+    assert rel(host(pd), mg.vcycle(b, p)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_64", "ell16", "odd_coarse_24", "aniso_64x32x16"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_matches_oracle(mgp, name, prec):
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case, prec=prec)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = case_rhs(case, beta_o)
+    p_o, cyc_o, _ = O.MG(beta_o, case.h, max_coarse=4096).solve(rhs, tol=1e-12, max_cycles=300)
+    assert cyc_o > 0
+    p_g, st = ctx.solve(dev(rhs), tol=1e-10)
+    pg = host(p_g)
+    assert st.rel_resid <= 1e-10
+    lab, nc = O.components(beta_o)
+    b = O.remove_mean(rhs, lab, nc)
+    r = O.residual(beta_o, b, pg, case.h)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.0001e-10
+    assert rel(pg, p_o) <= 1e-9
+    live = O.diag_inv(beta_o) > 0
+    assert abs(pg[live].mean()) <= 1e-12 * np.abs(pg).max()
+    assert np.all(pg[~live] == 0)
+    if prec == "fp64":
+        _, cyc10, _ = O.MG(beta_o, case.h, max_coarse=4096).solve(rhs, tol=1e-10, max_cycles=300)
+        assert abs(st.cycles - cyc10) <= 1
+
+
+def test_solve_c2_128_fp64_and_mixed(mgp):
+    case = synth.case_c2(128)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = O.divergence(beta_o, case.u_star, case.h)
+    p_o, cyc_o, _ = O.MG(beta_o, case.h).solve(rhs, tol=1e-12)
+    lab, nc = O.components(beta_o)
+    b = O.remove_mean(rhs, lab, nc)
+    for prec in ("fp64", "mixed"):
+        _, ctx = _ctx(mgp, case, prec=prec)
+        p_g, st = ctx.solve(dev(rhs), tol=1e-10)
+        pg = host(p_g)
+        r = O.residual(beta_o, b, pg, case.h)
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.0001e-10, prec
+        assert rel(pg, p_o) <= 1e-9, prec
+
+
+@pytest.mark.parametrize("name", ["c2_64", "ell16", "aniso_64x32x16"])
+def test_divergence_and_correction_bit_exact(mgp, name):
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    u = case.u_star
+    for dt in (1.0, 2.5e-4):
+        rg = host(ctx.divergence(faces_dev(u), dt=dt))
+        assert np.array_equal(rg, O.divergence(beta_o, u, case.h, dt))
+    p = np.random.default_rng(3).standard_normal(case.shape)
+    ug = faces_host(ctx.correct(faces_dev(u), dev(p), dt=2.5e-4))
+    uo = O.correct(beta_o, p, u, case.h, 2.5e-4)
+    for a, b in zip(ug, uo):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["c2_64", "ell16"])
+def test_projection_matches_oracle(mgp, name):
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    uo, po, beta_o, rhs = O.project(case.phi, case.solid, case.u_star, case.h, lam=case.lam, tol=1e-12)
+    ug, pg, st = ctx.project(faces_dev(case.u_star), tol=1e-10)
+    ug = faces_host(ug)
+    scale = max(np.abs(x).max() for x in uo)
+    for a, b in zip(ug, uo):
+        assert np.abs(a - b).max() <= 1e-8 * scale
+    du = O.divergence(beta_o, ug, case.h)
+    assert np.linalg.norm(du) <= 1.0001e-10 * np.linalg.norm(O.remove_mean(rhs, *O.components(beta_o)))
+
+
+@pytest.mark.parametrize("name", ["c2_64", "ell16"])
+def test_adjoint_faces_and_phi_grad_bit_exact_given_p_q(mgp, name):
+    """Given the same p and w, the adjoint's face gradients and the phi chain rule are bit-exact;
+    the adjoint solve itself matches the oracle to the solve tolerance."""
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    uo, po, beta_o, _ = O.project(case.phi, case.solid, case.u_star, case.h, lam=case.lam, tol=1e-12)
+    gu_o, gb_o, gphi_o = O.project_adjoint(beta_o, po, case.w, case.h, lam=case.lam, tol=1e-12)
+    gu_g, gb_g, st = ctx.project_adjoint(faces_dev(case.w), dev(po), tol=1e-12)
+    for a, b in zip(faces_host(gu_g), gu_o):
+        assert np.abs(a - b).max() <= 1e-8 * max(np.abs(b).max(), 1.0)
+    for a, b in zip(faces_host(gb_g), gb_o):
+        assert np.abs(a - b).max() <= 1e-8 * max(np.abs(b).max(), 1e-300)
+    # phi chain rule bit-exact on the oracle's grad_beta
+    gphi_g = host(mgp.phi_grad(beta_g, faces_dev(gb_o), case.h, rho_air=case.lam))
+    assert np.array_equal(gphi_g, O.phi_grad(beta_o, gb_o, case.lam))

@@ -27,11 +27,13 @@ MUTANTS = [
     ("operator uses the low y face twice", "if (j < ny - 1) s += by[IX(i, j + 1, k)] * (p[IX(i, j + 1, k)] - p[c]);",
      "if (j < ny - 1) s += by[c] * (p[IX(i, j + 1, k)] - p[c]);",
      [lambda: T1.test_operator_invariants("ellipsoid"), T1.test_dense_operator_matches_independent_assembly]),
-    ("smoother sign of the source", "p[c] = dinv[c] * (s - h2 * b[c]);", "p[c] = dinv[c] * (s + h2 * b[c]);",
+    ("smoother sign of the source", "p[c] = dinv[c] * fma(-h2, b[c], s);", "p[c] = dinv[c] * fma(h2, b[c], s);",
      [lambda: T1.test_colour_sweep_zeroes_that_colours_residual(0)]),
-    ("smoother reads the wrong x neighbour", "if (i < nx - 1) s += bx[IX(i + 1, j, k)] * p[IX(i + 1, j, k)];",
-     "if (i < nx - 1) s += bx[IX(i + 1, j, k)] * p[IX(i, j, k)];",
+    ("smoother reads the wrong x neighbour", "if (i < nx - 1) s = fma(bx[IX(i + 1, j, k)], p[IX(i + 1, j, k)], s);",
+     "if (i < nx - 1) s = fma(bx[IX(i + 1, j, k)], p[IX(i, j, k)], s);",
      [lambda: T1.test_colour_sweep_zeroes_that_colours_residual(1)]),
+    ("residual drops the y- flux", "if (j > 0) s = fma(by[c], p[IX(i, j - 1, k)] - p[c], s);", "",
+     [lambda: T1.test_colour_sweep_zeroes_that_colours_residual(0)]),
     ("coefficient restriction scale", "cbx[C] = 0.25 * (", "cbx[C] = 0.5 * (",
      [T1.test_coefficient_restriction_invariants]),
     ("coefficient restriction takes the odd fine plane", "cbz[C] = 0.25 * (bz[IX(2 * I, 2 * J, 2 * K)] + bz[IX(2 * I + 1, 2 * J, 2 * K)] +",
