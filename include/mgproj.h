@@ -229,6 +229,34 @@ uint64_t mg_kernel_launches(void);
 int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total);
 void mg_profile_reset(mg_ctx *c);
 
+/*
+ * Allocation-free residual check.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- applications whose
+ * device memory all belongs to a pool or arena they must not bypass, loops
+ * where an allocation (which may synchronise the device) is not allowed, and
+ * hosts that give plug-ins no allocator.  It needs no mg_ctx.
+ *
+ * For rhs b and pressure p on grid g with face coefficients beta it writes
+ * out[0] = ||b0 - A p||_2 / ||b0||_2 (0 if ||b0|| = 0), out[1] = ||b0||_2,
+ * out[2] = the mean of b over the live cells, out[3] = the number of live
+ * cells, where b0 = b - mean on live cells (cells with an open face) and 0
+ * elsewhere -- the same quantities mg_solve reports in mg_stats (rel_resid,
+ * rhs_norm, rhs_mean_removed) for its initial iterate.  beta, rhs, p: device,
+ * read only; out: device, 4 doubles, written.  Stream-ordered on `stream`.
+ *
+ * Its only scratch memory is a static __device__ array of the library
+ * (4 * MG_NOALLOC_MAX_PLANES + 2 doubles, 128 KB on every GPU that loads the
+ * library, held until the process exits); grids with nz > MG_NOALLOC_MAX_PLANES
+ * are rejected with MG_ERR_ARG.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (e.g. on two streams) race and must be
+ * serialised by the caller.  Nothing is allocated or freed.
+ */
+#define MG_NOALLOC_MAX_PLANES 4096
+int mg_residual_norm_noalloc(const mg_grid *g, const double *const beta[3], const double *rhs, const double *p,
+                             double *out, void *stream);
+
 void mg_destroy(mg_ctx *c);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -50,6 +50,10 @@ int fail(int code, const char *fmt, ...)
 
 }  // namespace
 
+namespace mg {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace mg
+
 struct mg_ctx {
     mg_grid g{};
     mg_opts o{};

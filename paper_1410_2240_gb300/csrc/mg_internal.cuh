@@ -45,6 +45,9 @@ enum Scal {
 // total kernels launched by this library in this process
 unsigned long long launch_count();
 
+// set the message mg_last_error() returns on this thread
+void set_last_error(const char *msg);
+
 // ---- kernel launchers (mg_kernels.cu); all stream-ordered, return cudaError_t of the launch ----
 cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
                                double *bx, double *by, double *bz, cudaStream_t s);

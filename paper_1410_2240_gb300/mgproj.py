@@ -76,6 +76,7 @@ _lib.mg_update.argtypes = [_vp, _PP]
 _lib.mg_kernel_launches.restype = ctypes.c_uint64
 _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.mg_profile_reset.argtypes = [_vp]
+_lib.mg_residual_norm_noalloc.argtypes = [ctypes.POINTER(Grid), _PP, _vp, _vp, _vp, _vp]
 _lib.mg_destroy.argtypes = [_vp]
 
 PROF_SMOOTH, PROF_RESTRICT, PROF_PROLONG, PROF_RESID64 = 0, 1, 2, 3
@@ -88,8 +89,8 @@ def kernel_launches() -> int:
 #: every symbol declared in include/mgproj.h
 EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_solve", "mg_vcycle", "mg_divergence",
            "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
-           "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset", "mg_destroy",
-           "mg_last_error"]
+           "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset",
+           "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error"]
 
 
 class MGError(RuntimeError):
