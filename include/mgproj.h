@@ -79,6 +79,10 @@ typedef struct {
     mg_precision prec;    /* MG_FP64 or MG_MIXED [MG_FP64] */
     int inner_cycles;     /* MG_MIXED: FP32 V-cycles per FP64 refinement step [1] */
     int profile;          /* nonzero: time finest-grid kernels with CUDA events (mg_profile_read) [0] */
+    int smoother;         /* 0 auto (fused red-black sweeps on FP32 levels of >= 32 x 8 x 8 cells,
+                             one pass per colour elsewhere), 1 one pass per colour, 2 fused wherever
+                             the level has >= 32 x 8 x 8 cells; every choice gives bit-identical
+                             results [0] */
 } mg_opts;
 
 /* Solve statistics (host struct, filled when non-NULL). */
@@ -221,9 +225,9 @@ int mg_level_array(mg_ctx *c, int level, int which, double *out);
  * with opts.profile != 0, the number of timed launches and their summed device
  * time (ms, CUDA events on the context's stream) of one kernel group since the
  * last mg_profile_reset; the stream must be idle (any solve returns so).
- * Groups: 0 = finest-grid smoothing sweep of one colour (the precision the
- * cycles run in), 1 = finest-grid residual + restriction, 2 = finest-grid
- * prolongation, 3 = FP64 finest-grid residual (norm or mixed cast). */
+ * Groups: 0 = one finest-grid red-black smoothing sweep (both colours, in the
+ * precision the cycles run in), 1 = finest-grid residual + restriction, 2 =
+ * finest-grid prolongation, 3 = FP64 finest-grid residual (norm or mixed cast). */
 enum { MG_PROF_SMOOTH = 0, MG_PROF_RESTRICT = 1, MG_PROF_PROLONG = 2, MG_PROF_RESID64 = 3, MG_PROF_GROUPS = 4 };
 uint64_t mg_kernel_launches(void);
 int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total);

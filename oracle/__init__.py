@@ -19,6 +19,7 @@ Function -> paper passage:
                    restriction); smoother, transfers and cycle are the readings
                    listed in the design notes (the paper does not give them)
   cg_solve         the paper's earlier solver family (preconditioned CG)
+  MG.pcg           CG preconditioned by the multigrid cycle (the two combined)
   project_adjoint  derived adjoint of the projection
 """
 from __future__ import annotations
@@ -103,6 +104,8 @@ def _load(path: Optional[str] = None):
             lib.orc_mg_vcycle.argtypes = [v, _D, _D]
             lib.orc_mg_solve.argtypes = [v, _D, _D, d, i, _D]
             lib.orc_mg_solve.restype = i
+            lib.orc_mg_pcg.argtypes = [v, _D, _D, d, i, i, _D]
+            lib.orc_mg_pcg.restype = i
             lib.orc_cg_solve.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, d, i]
             lib.orc_cg_solve.restype = i
             lib.orc_divergence.argtypes = [i, i, i, d, d, _D, _D, _D, _D, _D, _D, _D]
@@ -287,6 +290,13 @@ class MG:
         p = _f64(p).copy()
         self._lib.orc_mg_vcycle(self._m, _p(_f64(b)), _p(p))
         return p
+
+    def pcg(self, b, p0=None, tol=1e-10, max_it=100, vcycles=1):
+        """Multigrid-preconditioned CG: returns (p, iterations, history); iterations < 0 if not converged."""
+        p = np.zeros(self.shape) if p0 is None else _f64(p0).copy()
+        hist = np.zeros(max_it)
+        it = self._lib.orc_mg_pcg(self._m, _p(_f64(b)), _p(p), tol, max_it, vcycles, _p(hist))
+        return p, it, hist[: abs(it)]
 
     def solve(self, b, p0=None, tol=1e-10, max_cycles=100):
         """Returns (p, cycles, history).  cycles < 0 if not converged."""

@@ -554,6 +554,73 @@ int orc_mg_solve(orc_mg *m, const double *b_in, double *p, double tol, int max_c
 }
 
 /* ------------------------------------------------------------------------- */
+/* Multigrid-preconditioned conjugate gradients (the paper's preconditioned-CG */
+/* family with the multigrid cycle as the preconditioner, Poisson-solver       */
+/* section).  PCG on the semi-definite A (the signs cancel in alpha and beta), */
+/* in the flexible (Polak-Ribiere) form beta = <r', z' - z> / <r, z>, which    */
+/* tolerates a preconditioner that is not exactly symmetric (the cycle's       */
+/* restriction is not the transpose of its prolongation); the preconditioner   */
+/* is nvc V-cycles from a zero guess.  The                                     */
+/* recursively updated residual decides convergence; the true residual is then */
+/* checked and the iteration restarted from the current p if it is above tol.  */
+/* Returns iterations (negative if not converged); hist[i] = recursive         */
+/* relative residual after iteration i+1.                                      */
+/* ------------------------------------------------------------------------- */
+static double dot(size_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+int orc_mg_pcg(orc_mg *m, const double *b_in, double *p, double tol, int max_it, int nvc, double *hist)
+{
+    orc_level *L = &m->lev[0];
+    size_t n = (size_t)L->nx * L->ny * L->nz;
+    int *label = (int *)malloc(n * sizeof(int));
+    int ncomp = orc_components(L->nx, L->ny, L->nz, L->bx, L->by, L->bz, label);
+    double *b = dalloc(n), *r = dalloc(n), *z = dalloc(n), *zo = dalloc(n), *d = dalloc(n), *q = dalloc(n);
+    memcpy(b, b_in, n * sizeof(double));
+    orc_remove_mean(n, label, ncomp, b);
+    double nb = norm2(n, b);
+    int it = 0, ok = (nb == 0.0);
+    if (ok) memset(p, 0, n * sizeof(double));
+    while (!ok && it < max_it) {
+        /* (re)start from the current p with its true residual */
+        orc_residual(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, b, p, r);
+        if (norm2(n, r) / nb <= tol) { ok = 1; break; }
+        memset(z, 0, n * sizeof(double));
+        for (int v = 0; v < nvc; v++) vcycle(m, 0, r, z);
+        memcpy(d, z, n * sizeof(double));
+        double rz = dot(n, r, z);
+        while (it < max_it) {
+            it++;
+            orc_apply_A(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, d, q);
+            double alpha = rz / dot(n, d, q);
+            for (size_t c = 0; c < n; c++) { p[c] += alpha * d[c]; r[c] -= alpha * q[c]; }
+            double rel = norm2(n, r) / nb;
+            if (hist) hist[it - 1] = rel;
+            if (rel <= tol) break;
+            memcpy(zo, z, n * sizeof(double));
+            memset(z, 0, n * sizeof(double));
+            for (int v = 0; v < nvc; v++) vcycle(m, 0, r, z);
+            double rzn = dot(n, r, z);
+            double beta = (rzn - dot(n, r, zo)) / rz;
+            rz = rzn;
+            for (size_t c = 0; c < n; c++) d[c] = z[c] + beta * d[c];
+        }
+    }
+    if (!ok && it <= max_it) {
+        orc_residual(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, b, p, r);
+        ok = norm2(n, r) / nb <= tol;
+    }
+    orc_remove_mean(n, label, ncomp, p);
+    free(label); free(b); free(r); free(z); free(zo); free(d); free(q);
+    if (nb == 0.0) return 0;
+    return ok ? it : -max_it;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Jacobi-preconditioned conjugate gradients on -A p = -b (the paper's old     */
 /* solver family, Poisson solver section), an algorithm independent of the    */
 /* multigrid one.  b is made compatible first; p's mean is removed at the end. */

@@ -63,6 +63,8 @@ struct mg_ctx {
     std::vector<double> hs;
     std::vector<LevelArrays<double>> L64;
     std::vector<LevelArrays<float>> L32;
+    std::vector<double *> palt64;  // second iterate buffer per level for fused sweeps (null if unused)
+    std::vector<float *> palt32;
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
     double *qbuf = nullptr;     // adjoint solution when the caller passes none
@@ -246,6 +248,25 @@ struct ProfScope {
 // prolongation, post-smooth nu2 x (black, red).
 // ---------------------------------------------------------------------------
 template <typename T>
+T *palt_of(mg_ctx *c, int l);
+template <>
+double *palt_of<double>(mg_ctx *c, int l) { return c->palt64.empty() ? nullptr : c->palt64[l]; }
+template <>
+float *palt_of<float>(mg_ctx *c, int l) { return c->palt32.empty() ? nullptr : c->palt32[l]; }
+
+// fused sweeps pay off on levels with at least one full 32 x 8 tile and 8 planes
+bool fused_level(const Dims &d) { return d.nx >= 32 && d.ny >= 8 && d.nz >= 8; }
+
+template <typename T>
+bool use_fused(const mg_ctx *c, int l)
+{
+    if (!fused_level(c->dims[l]) || l == c->nlev - 1) return false;
+    if (c->o.smoother == 1) return false;
+    if (c->o.smoother == 2) return true;
+    return sizeof(T) == 4;  // auto: FP32 sweeps are HBM-bound (fusing halves their traffic)
+}
+
+template <typename T>
 int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T *p)
 {
     cudaStream_t s = c->s;
@@ -254,35 +275,37 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
         CK(mg::launch_coarse_solve<T>(c->ncoarse, c->M, b, p, s));
         return MG_OK;
     }
-    const T h = (T)c->hs[l];
     const T h2 = (T)(c->hs[l] * c->hs[l]);
     const T ih2 = (T)(1.0 / (c->hs[l] * c->hs[l]));
     const bool fine = (l == 0);
-    auto smooth = [&](int colour) -> int {
+    const bool fused = use_fused<T>(c, l) && palt_of<T>(c, l) != nullptr;
+    T *cur = p, *alt = palt_of<T>(c, l);
+    // one red-black sweep, `first` colour first
+    auto sweep = [&](int first) -> int {
         ProfScope ps(c, MG_PROF_SMOOTH, fine);
-        CK(mg::launch_smooth<T>(d, h2, L[l], b, p, colour, s));
+        if (fused) {
+            CK(mg::launch_rb_sweep<T>(d, h2, L[l], b, cur, alt, first, s));
+            std::swap(cur, alt);
+        } else {
+            CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
+            CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first ^ 1, s));
+        }
         return MG_OK;
     };
-    for (int it = 0; it < c->o.nu1; it++) {
-        CKS(smooth(0));
-        CKS(smooth(1));
-    }
-    (void)h;
+    for (int it = 0; it < c->o.nu1; it++) CKS(sweep(0));
     const LevelArrays<T> &C = L[l + 1];
     {
         ProfScope ps(c, MG_PROF_RESTRICT, fine);
-        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, p, C.b, s));
+        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s));
     }
     CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
     CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
     {
         ProfScope ps(c, MG_PROF_PROLONG, fine);
-        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, p, s));
+        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, cur, s));
     }
-    for (int it = 0; it < c->o.nu2; it++) {
-        CKS(smooth(1));
-        CKS(smooth(0));
-    }
+    for (int it = 0; it < c->o.nu2; it++) CKS(sweep(1));
+    if (cur != p) CK(cudaMemcpyAsync(p, cur, d.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return MG_OK;
 }
 
@@ -443,6 +466,7 @@ void mg_default_opts(mg_opts *o)
     o->prec = MG_FP64;
     o->inner_cycles = 1;
     o->profile = 0;
+    o->smoother = 0;
 }
 
 const char *mg_last_error(void) { return g_err.c_str(); }
@@ -480,7 +504,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
-        o.inner_cycles < 1 || o.profile < 0)
+        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 2)
         return fail(MG_ERR_ARG, "mg_setup: invalid options");
 
     mg_ctx *c = new mg_ctx();
@@ -507,7 +531,6 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
         return bail(fail(MG_ERR_ARG, "mg_setup: coarsest grid %dx%dx%d has %zu cells > coarse_max_cells=%d", dc.nx,
                          dc.ny, dc.nz, dc.n(), o.coarse_max_cells));
     c->ncoarse = (int)dc.n();
-    cudaStream_t s = c->s;
     int st = MG_OK;
     c->L64.resize(c->nlev);
     for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<double>(c, c->L64[l], c->dims[l].n(), l > 0);
@@ -526,6 +549,20 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
         for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<float>(c, c->L32[l], c->dims[l].n(), true);
         if (st != MG_OK) return bail(st);
     }
+    // second iterate buffers for the fused sweeps
+    for (int l = 0; l + 1 < c->nlev && st == MG_OK; l++) {
+        const bool f64 = c->o.smoother == 2 && fused_level(c->dims[l]);
+        const bool f32 = c->o.prec == MG_MIXED && c->o.smoother != 1 && fused_level(c->dims[l]);
+        if (f64) {
+            c->palt64.resize(c->nlev, nullptr);
+            st = c->alloc(&c->palt64[l], c->dims[l].n());
+        }
+        if (f32 && st == MG_OK) {
+            c->palt32.resize(c->nlev, nullptr);
+            st = c->alloc(&c->palt32[l], c->dims[l].n());
+        }
+    }
+    if (st != MG_OK) return bail(st);
     if (c->o.profile) {
         c->pev.resize(2 * 32768);
         c->pgroup.resize(32768);

@@ -58,6 +58,10 @@ cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s);
+// one full red-black sweep (first colour, then the other) from p_old into p_new
+template <typename T>
+cudaError_t launch_rb_sweep(Dims d, T h2, const LevelArrays<T> &L, const T *b, const T *p_old, T *p_new, int first,
+                            cudaStream_t s);
 template <typename T>
 cudaError_t launch_resid_restrict(Dims fine, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
                                   cudaStream_t s);

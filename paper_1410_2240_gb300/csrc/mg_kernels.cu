@@ -232,6 +232,110 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
     p[c] += s;
 }
 
+// ---------------------------------------------------------------------------
+// Fused red-black sweep: both colours in one pass over HBM.
+//
+// The CTA owns a TX x TY tile of columns and a chunk of z-planes and marches up
+// the chunk with a two-plane wavefront: at step s it updates the FIRST colour on
+// plane s, then the SECOND colour on plane s-1 (whose first-colour neighbours on
+// planes s-2, s-1 and s are final by then).  It reads the iterate from p_old and
+// writes every cell of its tile to p_new, so CTAs never see each other's writes:
+// the first colour on a one-cell ring around the tile (and on one plane below
+// and above the chunk) is recomputed from p_old, exactly as the neighbouring CTA
+// computes it.  Per cell the arithmetic is that of k_smooth, so the result is
+// bit-identical to two colour passes.  Threads: one per column of the tile plus a
+// two-cell halo; ring 2 only loads, ring 1 also updates the first colour.
+// Shared memory holds three rotating planes of (p, bx, by): the x+ and y+ face
+// coefficients of a cell are its neighbour's low faces.
+// ---------------------------------------------------------------------------
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__((TX + 4) * (TY + 4))
+k_rb_sweep(int nx, int ny, int nz, int zc, T h2, LevelArrays<T> L, const T *__restrict__ b,
+           const T *__restrict__ p_old, T *__restrict__ p_new, int first)
+{
+    constexpr int W = TX + 4, H = TY + 4;
+    __shared__ T sp[3][H][W];
+    __shared__ T sbx[3][H][W];
+    __shared__ T sby[3][H][W];
+    const int lx = threadIdx.x % W, ly = threadIdx.x / W;
+    const int i = blockIdx.x * TX + lx - 2, j = blockIdx.y * TY + ly - 2;
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+    const bool dom = (i >= 0 && i < nx && j >= 0 && j < ny);
+    const bool ring1 = dom && lx >= 1 && lx <= TX + 2 && ly >= 1 && ly <= TY + 2;
+    const bool inner = dom && lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t col = dom ? (size_t)j * nx + i : 0;
+    const int second = first ^ 1;
+    const bool xlo = i > 0, xhi = i < nx - 1, ylo = j > 0, yhi = j < ny - 1;
+
+    // column registers: iterate at planes s-2 .. s+1, coefficients at planes s-1 .. s+1
+    T q_m2 = T(0), q_m1 = T(0), q_0 = T(0), q_p1 = T(0);
+    T bx_m1 = T(0), by_m1 = T(0), bz_m1 = T(0), di_m1 = T(0), b_m1 = T(0);
+    T bx_0 = T(0), by_0 = T(0), bz_0 = T(0), di_0 = T(0), b_0 = T(0);
+    T bx_p1 = T(0), by_p1 = T(0), bz_p1 = T(0), di_p1 = T(0), b_p1 = T(0);
+
+    auto load_plane = [&](int z, T &q, T &bxv, T &byv, T &bzv, T &div, T &bv) {
+        q = bxv = byv = bzv = div = bv = T(0);
+        if (!dom || z < 0 || z >= nz) return;
+        const size_t c = (size_t)z * sxy + col;
+        q = p_old[c];
+        bxv = L.bx[c];
+        byv = L.by[c];
+        if (ring1) {
+            bzv = L.bz[c];
+            div = L.dinv[c];
+            bv = b[c];
+        }
+    };
+    // prologue: planes z0-2 (iterate only) and z0-1
+    {
+        T t0, t1, t2, t3, t4;
+        load_plane(z0 - 2, q_m1, t0, t1, t2, t3, t4);
+        load_plane(z0 - 1, q_0, bx_0, by_0, bz_0, di_0, b_0);
+    }
+    int cur = 0;
+    for (int s = z0 - 1; s <= z1; s++) {
+        const int prv = (cur + 2) % 3;  // buffer of plane s-1
+        load_plane(s + 1, q_p1, bx_p1, by_p1, bz_p1, di_p1, b_p1);
+        sp[cur][ly][lx] = q_0;
+        sbx[cur][ly][lx] = bx_0;
+        sby[cur][ly][lx] = by_0;
+        __syncthreads();
+        // first colour on plane s
+        if (ring1 && s >= 0 && s < nz && ((i + j + s) & 1) == first) {
+            T acc = T(0);
+            if (xlo) acc = fma(bx_0, sp[cur][ly][lx - 1], acc);
+            if (xhi) acc = fma(sbx[cur][ly][lx + 1], sp[cur][ly][lx + 1], acc);
+            if (ylo) acc = fma(by_0, sp[cur][ly - 1][lx], acc);
+            if (yhi) acc = fma(sby[cur][ly + 1][lx], sp[cur][ly + 1][lx], acc);
+            if (s > 0) acc = fma(bz_0, q_m1, acc);
+            if (s < nz - 1) acc = fma(bz_p1, q_p1, acc);
+            q_0 = di_0 * fma(-h2, b_0, acc);
+            sp[cur][ly][lx] = q_0;
+        }
+        __syncthreads();
+        // second colour on plane s-1, then plane s-1 is final for this tile
+        const int z = s - 1;
+        if (inner && z >= z0 && z < z1) {
+            if (((i + j + z) & 1) == second) {
+                T acc = T(0);
+                if (xlo) acc = fma(bx_m1, sp[prv][ly][lx - 1], acc);
+                if (xhi) acc = fma(sbx[prv][ly][lx + 1], sp[prv][ly][lx + 1], acc);
+                if (ylo) acc = fma(by_m1, sp[prv][ly - 1][lx], acc);
+                if (yhi) acc = fma(sby[prv][ly + 1][lx], sp[prv][ly + 1][lx], acc);
+                if (z > 0) acc = fma(bz_m1, q_m2, acc);
+                if (z < nz - 1) acc = fma(bz_0, q_0, acc);
+                q_m1 = di_m1 * fma(-h2, b_m1, acc);
+            }
+            p_new[(size_t)z * sxy + col] = q_m1;
+        }
+        q_m2 = q_m1; q_m1 = q_0; q_0 = q_p1;
+        bx_m1 = bx_0; by_m1 = by_0; bz_m1 = bz_0; di_m1 = di_0; b_m1 = b_0;
+        bx_0 = bx_p1; by_0 = by_p1; bz_0 = bz_p1; di_0 = di_p1; b_0 = b_p1;
+        cur = (cur + 1) % 3;
+    }
+}
+
 // Exact coarsest-grid solve e = M b with the dense minimum-norm inverse M (FP64 always).
 template <typename T>
 __global__ void k_coarse_solve(int n, const double *__restrict__ M, const T *__restrict__ b, T *__restrict__ e)
@@ -575,6 +679,28 @@ cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_
 }
 template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t);
 template cudaError_t launch_prolong<float>(Dims, const float *, const float *, float *, cudaStream_t);
+
+// Tiles of 32 x 8 columns; z-chunks sized so that the grid has about 4 CTAs per SM.
+template <typename T>
+cudaError_t launch_rb_sweep(Dims d, T h2, const LevelArrays<T> &L, const T *b, const T *p_old, T *p_new, int first,
+                            cudaStream_t s)
+{
+    constexpr int TX = 32, TY = 8;
+    const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY;
+    const int want = 4 * 152;
+    int chunks = (want + tx * ty - 1) / (tx * ty);
+    int zc = (d.nz + chunks - 1) / chunks;
+    if (zc < 8) zc = 8;
+    if (zc > d.nz) zc = d.nz;
+    const dim3 grid((unsigned)tx, (unsigned)ty, (unsigned)((d.nz + zc - 1) / zc));
+    note_launch();
+    k_rb_sweep<T, TX, TY><<<grid, (TX + 4) * (TY + 4), 0, s>>>(d.nx, d.ny, d.nz, zc, h2, L, b, p_old, p_new, first);
+    return cudaGetLastError();
+}
+template cudaError_t launch_rb_sweep<double>(Dims, double, const LevelArrays<double> &, const double *,
+                                             const double *, double *, int, cudaStream_t);
+template cudaError_t launch_rb_sweep<float>(Dims, float, const LevelArrays<float> &, const float *, const float *,
+                                            float *, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s)

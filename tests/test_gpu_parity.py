@@ -177,3 +177,36 @@ def test_adjoint_faces_and_phi_grad_bit_exact_given_p_q(mgp, name):
     # phi chain rule bit-exact on the oracle's grad_beta
     gphi_g = host(mgp.phi_grad(beta_g, faces_dev(gb_o), case.h, rho_air=case.lam))
     assert np.array_equal(gphi_g, O.phi_grad(beta_o, gb_o, case.lam))
+
+
+FUSED_CASES = {
+    "c2_64": lambda: synth.case_c2(64),
+    "ragged_160x32x32": lambda: synth.small_case(160, 32, 32, solid="ellipsoid", seed=41),
+    "ragged_48x24x40": lambda: synth.small_case(48, 24, 40, solid="ellipsoid", seed=42),
+    "aniso_64x32x16": lambda: synth.small_case(64, 32, 16, solid="ellipsoid", seed=43),
+}
+
+
+@pytest.mark.parametrize("name", list(FUSED_CASES))
+def test_fused_sweep_bit_identical_to_colour_passes(mgp, name):
+    """The fused red-black sweep (one pass, overlapped tiles, z-wavefront) gives bit-identical
+    V-cycles (FP64) and mixed solves (FP32 cycles) to one pass per colour."""
+    case = FUSED_CASES[name]()
+    beta = mgp.face_coeffs(dev(case.phi), case.h, None if case.solid is None else dev(case.solid, dtype=torch.uint8),
+                           rho_air=case.lam)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    b = O.remove_mean(case_rhs(case, beta_o), *O.components(beta_o))
+    bd = dev(b)
+    colour = mgp.Context(beta, case.h, smoother=1, coarse_max_cells=2048)
+    fused = mgp.Context(beta, case.h, smoother=2, coarse_max_cells=2048)
+    p1 = torch.zeros_like(bd)
+    p2 = torch.zeros_like(bd)
+    for _ in range(3):
+        colour.vcycle(bd, p1)
+        fused.vcycle(bd, p2)
+        assert torch.equal(p1, p2)
+    m1 = mgp.Context(beta, case.h, prec="mixed", smoother=1, coarse_max_cells=2048)
+    m0 = mgp.Context(beta, case.h, prec="mixed", smoother=0, coarse_max_cells=2048)
+    q1, s1 = m1.solve(bd, tol=1e-10)
+    q0, s0 = m0.solve(bd, tol=1e-10)
+    assert s1.cycles == s0.cycles and torch.equal(q1, q0)

@@ -56,6 +56,10 @@ MUTANTS = [
      [T2.test_adjoint_phi_gradient_central_differences]),
     ("pseudo-inverse keeps the null space", "if (fabs(lam) <= 1e-9 * lmax) continue;", "if (fabs(lam) == 0.0) continue;",
      [T1.test_pinv_matches_numpy_and_penrose_conditions]),
+    ("PCG drops the flexible correction of beta", "double beta = (rzn - dot(n, r, zo)) / rz;", "double beta = (rzn + dot(n, r, zo)) / rz;",
+     [lambda: T2.test_pcg_and_stationary_cycles_agree("c1")]),
+    ("PCG residual update sign", "p[c] += alpha * d[c]; r[c] -= alpha * q[c];", "p[c] += alpha * d[c]; r[c] += alpha * q[c];",
+     [lambda: T2.test_pcg_matches_dense_pseudoinverse(1)]),
     ("component search ignores upper z faces", "if (k < nz - 1) { nb[m] = IX(i, j, k + 1); fb[m++] = bz[IX(i, j, k + 1)]; }", "",
      [T1.test_components_counts]),
 ]

@@ -1,4 +1,5 @@
 """Pins of the oracle's solvers, projection and adjoint (CPU only)."""
+import math
 import numpy as np
 import pytest
 
@@ -207,3 +208,45 @@ def test_adjoint_u_gradient_is_exact_for_linear_loss():
     dl = sum(np.vdot(a - b, w) for a, b, w in zip(u2, u, case.w))
     pred = sum(np.vdot(g, x) for g, x in zip(gu, d))
     assert abs(dl - pred) <= 1e-11 * (abs(dl) + abs(pred))
+
+
+# --- multigrid-preconditioned CG (the next solver row) ------------------------
+
+@pytest.mark.parametrize("vcycles", [1, 2])
+def test_pcg_matches_dense_pseudoinverse(vcycles):
+    case = synth.small_case(8, solid="ellipsoid", seed=21)
+    beta = O.face_coeffs(case.phi, case.solid, case.lam)
+    lab, nc = O.components(beta)
+    p_dense, _ = O.dense_solve(beta, case.rhs, case.h, lab, nc)
+    p, it, _ = O.MG(beta, case.h).pcg(case.rhs, tol=1e-13, vcycles=vcycles)
+    assert it > 0
+    assert np.linalg.norm(p - p_dense) <= 1e-11 * np.linalg.norm(p_dense)
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_64"])
+def test_pcg_and_stationary_cycles_agree(name):
+    case = synth.case_c1() if name == "c1" else synth.case_c2(64)
+    beta = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = case.rhs if case.rhs is not None else O.divergence(beta, case.u_star, case.h)
+    mg = O.MG(beta, case.h)
+    p_mg, c1, _ = mg.solve(rhs, tol=1e-13, max_cycles=200)
+    for k in (1, 2):
+        p, it, hist = mg.pcg(rhs, tol=1e-13, vcycles=k)
+        assert it > 0
+        assert np.linalg.norm(p - p_mg) <= 1e-10 * np.linalg.norm(p_mg)
+        assert it < c1  # Krylov acceleration of the same cycle needs fewer iterations
+    lab, nc = O.components(beta)
+    b = O.remove_mean(rhs, lab, nc)
+    p, it, _ = mg.pcg(rhs, tol=1e-10, vcycles=2)
+    assert np.linalg.norm(O.residual(beta, b, p, case.h)) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_pcg_closed_form_eigenmode():
+    nx, ny, nz = 16, 12, 8
+    h = 1.0 / nx
+    beta = O.face_coeffs(np.ones((nz, ny, nx)), None, 1e-3)
+    k = (3, 2, 1)
+    v = synth.fourier_mode(nx, ny, nz, *k)
+    lam = -(4 / h ** 2) * sum(math.sin(math.pi * kd / (2 * n)) ** 2 for kd, n in zip(k, (nx, ny, nz)))
+    p, it, _ = O.MG(beta, h).pcg(v, tol=1e-13, vcycles=1)
+    np.testing.assert_allclose(p, v / lam, rtol=0, atol=1e-12 * np.abs(v / lam).max())
