@@ -46,6 +46,10 @@ B_VCYCLE32 = 161.0    # V(2,2), all levels, FP32
 B_VCYCLE64 = 322.0    # V(2,2), all levels, FP64
 B_RESID64 = 48.0      # FP64 residual + norm (p, b, bx, by, bz read; dinv mask)
 B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
+SWEEP_KERNEL = {0: "k_smooth<float> x2 colour passes", 1: "k_smooth<float> x2 colour passes",
+                2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
+PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
+               ("coarse_levels", 6), ("hierarchy_update", 7))
 
 
 def parse_args():
@@ -59,7 +63,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per FP64 refinement step")
-    ap.add_argument("--smoother", type=int, default=0, help="0 auto, 1 one pass per colour, 2 fused")
+    ap.add_argument("--smoother", type=int, default=0, help="0 auto, 1 per colour, 2 fused, 3 fused + TMA")
+    ap.add_argument("--krylov", type=int, default=0, help="1: multigrid-preconditioned CG")
     return ap.parse_args()
 
 
@@ -304,7 +309,7 @@ def run_ours(args):
     K, W = args.steps, max(args.warmup, 3)
 
     # ---- mixed (headline) ----
-    opts = {"inner_cycles": args.inner, "smoother": args.smoother}
+    opts = {"inner_cycles": args.inner, "smoother": args.smoother, "krylov": args.krylov, "krylov": args.krylov}
     step = Step(case, "mixed", profile=1, **opts)
     dev_uuid = None
     try:
@@ -333,7 +338,7 @@ def run_ours(args):
     steps_total = sum(a + b for a, b in step.cycles)
     solve_ms_total = sum(step.solve_ms)  # the solves alone (CUDA events inside the library)
     mixed_vcycle_gbs = (B_VCYCLE32 + B_REFINE) * n * steps_total / (solve_ms_total / 1e3) / 1e9
-    prof = {g: step.ctx.profile_read(i) for g, i in (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3))}
+    prof = {g: step.ctx.profile_read(i) for g, i in PROF_GROUPS}
     p_mixed = step.p.detach().cpu().numpy() if rank == 0 else None
     del step
     torch.cuda.empty_cache()
@@ -341,7 +346,8 @@ def run_ours(args):
     # ---- plain FP64 on the same step ----
     fp64 = None
     if not args.no_fp64:
-        s64 = Step(case, "fp64", profile=1, smoother=args.smoother)
+        s64 = Step(case, "fp64", profile=1, smoother=args.smoother, krylov=args.krylov,
+                   inner_cycles=args.inner if args.krylov else 1)
         K64 = max(2, K // 2)
         ms64, _ = time_steps(s64, K64, 3, world)
         sps64, ms64 = replica_throughput(ms64, 2 * K64, world)
@@ -352,7 +358,8 @@ def run_ours(args):
         fp64 = {"solves_per_s": sps64, "ms_per_step": ms64 / K64,
                 "cycles_fwd_bwd": list(cyc64),
                 "vcycle_hbm_gbs": (B_VCYCLE64 + B_RESID64) * n * tot64 / (sum(s64.solve_ms) / 1e3) / 1e9,
-                "fine_sweep_ms": sweep64, "fine_sweep_gbs": B_SWEEP64 * n / (sweep64 / 1e3) / 1e9}
+                "fine_sweep_ms": sweep64, "fine_sweep_gbs": B_SWEEP64 * n / (sweep64 / 1e3) / 1e9,
+                "kernel_ms": {g: dict(zip(("launches", "ms"), s64.ctx.profile_read(i))) for g, i in PROF_GROUPS}}
         p64 = s64.p.detach().cpu().numpy() if rank == 0 else None
         del s64
         torch.cuda.empty_cache()
@@ -370,7 +377,7 @@ def run_ours(args):
         "cycles_fwd_bwd": list(cyc_mixed),
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "k_rb_sweep<float,32,8> finest grid (one fused red-black sweep per launch)",
+                     "traffic": None, "kernel": SWEEP_KERNEL[args.smoother] + " (finest grid, FP32, one red-black sweep)",
                      "algorithmic_bytes_per_sweep": B_SWEEP32 * n, "sweep_ms": sweep_ms,
                      "peak_source": f"{peak_src} hbm_gbs (burst copy)"},
         "vcycle_hbm_gbs": {"mixed": mixed_vcycle_gbs, "fp64": fp64["vcycle_hbm_gbs"] if fp64 else None},

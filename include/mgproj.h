@@ -77,17 +77,24 @@ typedef struct {
     int check_every;      /* residual check every this many cycles [1] */
     int coarse_max_cells; /* largest coarsest grid solved densely [512] */
     mg_precision prec;    /* MG_FP64 or MG_MIXED [MG_FP64] */
-    int inner_cycles;     /* MG_MIXED: FP32 V-cycles per FP64 refinement step [1] */
+    int inner_cycles;     /* V-cycles per preconditioner application (krylov = 1) or, with
+                             krylov = 0 and MG_MIXED, FP32 V-cycles per FP64 refinement step [1] */
     int profile;          /* nonzero: time finest-grid kernels with CUDA events (mg_profile_read) [0] */
-    int smoother;         /* 0 auto (fused red-black sweeps on FP32 levels of >= 32 x 8 x 8 cells,
-                             one pass per colour elsewhere), 1 one pass per colour, 2 fused wherever
-                             the level has >= 32 x 8 x 8 cells; every choice gives bit-identical
-                             results [0] */
+    int smoother;         /* red-black sweep kernels; every choice gives bit-identical results:
+                             0 auto (currently 1, the fastest measured on GB300); 1 one pass per
+                             colour; 2 one fused pass per sweep with register-staged planes on
+                             levels of >= 32 x 8 x 8 cells (both precisions); 3 one fused pass per
+                             sweep with TMA-staged planes on FP32 levels of >= 32 x 8 x 8 cells
+                             with nx % 4 == 0, one pass per colour elsewhere [0] */
+    int krylov;           /* 0: stationary V-cycles (refinement steps when mixed); 1: conjugate
+                             gradients preconditioned by inner_cycles V-cycles from a zero guess
+                             (flexible Polak-Ribiere form; FP64 Krylov vectors, the cycles in the
+                             precision prec selects) [0] */
 } mg_opts;
 
 /* Solve statistics (host struct, filled when non-NULL). */
 typedef struct {
-    int cycles;              /* V-cycles (FP64) or refinement steps (mixed) run */
+    int cycles;              /* V-cycles (FP64), refinement steps (mixed) or CG iterations (krylov) */
     double rel_resid;        /* final ||b - A p||_2 / ||b||_2 over fluid cells, FP64 */
     double rhs_norm;         /* ||b||_2 after compatibility projection */
     double rhs_mean_removed; /* mean of the rhs over fluid cells that was subtracted */
@@ -227,8 +234,15 @@ int mg_level_array(mg_ctx *c, int level, int which, double *out);
  * last mg_profile_reset; the stream must be idle (any solve returns so).
  * Groups: 0 = one finest-grid red-black smoothing sweep (both colours, in the
  * precision the cycles run in), 1 = finest-grid residual + restriction, 2 =
- * finest-grid prolongation, 3 = FP64 finest-grid residual (norm or mixed cast). */
-enum { MG_PROF_SMOOTH = 0, MG_PROF_RESTRICT = 1, MG_PROF_PROLONG = 2, MG_PROF_RESID64 = 3, MG_PROF_GROUPS = 4 };
+ * finest-grid prolongation, 3 = FP64 finest-grid residual (norm, mixed cast,
+ * or the conjugate-gradient update), 4 = conjugate-gradient operator apply
+ * q = A d, 5 = conjugate-gradient dot products and direction update, 6 = all
+ * levels below the finest of one V-cycle (coarse-grid correction), 7 =
+ * hierarchy rebuild (mg_update). */
+enum {
+    MG_PROF_SMOOTH = 0, MG_PROF_RESTRICT = 1, MG_PROF_PROLONG = 2, MG_PROF_RESID64 = 3, MG_PROF_APPLY = 4,
+    MG_PROF_KRYLOV = 5, MG_PROF_COARSE = 6, MG_PROF_UPDATE = 7, MG_PROF_GROUPS = 8
+};
 uint64_t mg_kernel_launches(void);
 int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total);
 void mg_profile_reset(mg_ctx *c);

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmgproj.so")
-SOURCES = ["mg_kernels.cu", "mg_api.cu", "mg_noalloc.cu"]
+SOURCES = ["mg_kernels.cu", "mg_api.cu", "mg_noalloc.cu", "mg_sweep_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

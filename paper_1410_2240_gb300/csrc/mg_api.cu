@@ -65,6 +65,10 @@ struct mg_ctx {
     std::vector<LevelArrays<float>> L32;
     std::vector<double *> palt64;  // second iterate buffer per level for fused sweeps (null if unused)
     std::vector<float *> palt32;
+    // conjugate-gradient vectors (krylov = 1): FP64 r, d, q; z, z_old (FP64 cycles) or a
+    // second FP32 cycle output (mixed cycles)
+    double *kr = nullptr, *kd = nullptr, *kq = nullptr, *kz = nullptr, *kzo = nullptr;
+    float *ke_alt = nullptr;
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
     double *qbuf = nullptr;     // adjoint solution when the caller passes none
@@ -261,9 +265,26 @@ template <typename T>
 bool use_fused(const mg_ctx *c, int l)
 {
     if (!fused_level(c->dims[l]) || l == c->nlev - 1) return false;
-    if (c->o.smoother == 1) return false;
     if (c->o.smoother == 2) return true;
-    return sizeof(T) == 4;  // auto: FP32 sweeps are HBM-bound (fusing halves their traffic)
+    if (c->o.smoother == 3) return sizeof(T) == 4;
+    return false;  // auto and 1: one pass per colour (the measured fastest on GB300)
+}
+
+// FP32 levels in auto mode sweep with the TMA-staged kernel where its layout allows
+template <typename T>
+bool tma_level(const mg_ctx *c, int l)
+{
+    return sizeof(T) == 4 && c->o.smoother == 3 && mg::tma_sweep_supported(c->dims[l]);
+}
+inline cudaError_t launch_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *pold,
+                                    float *pnew, int first, double *dscal, cudaStream_t s)
+{
+    return mg::launch_rb_sweep_tma(d, h2, L, b, pold, pnew, first, dscal, s);
+}
+inline cudaError_t launch_sweep_tma(Dims, double, const LevelArrays<double> &, const double *, const double *,
+                                    double *, int, double *, cudaStream_t)
+{
+    return cudaErrorNotSupported;  // FP64 levels never take this path
 }
 
 template <typename T>
@@ -284,7 +305,10 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     auto sweep = [&](int first) -> int {
         ProfScope ps(c, MG_PROF_SMOOTH, fine);
         if (fused) {
-            CK(mg::launch_rb_sweep<T>(d, h2, L[l], b, cur, alt, first, s));
+            if (tma_level<T>(c, l))
+                CK(launch_sweep_tma(d, h2, L[l], b, cur, alt, first, c->dscal, s));
+            else
+                CK(mg::launch_rb_sweep<T>(d, h2, L[l], b, cur, alt, first, s));
             std::swap(cur, alt);
         } else {
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
@@ -298,8 +322,11 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
         ProfScope ps(c, MG_PROF_RESTRICT, fine);
         CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s));
     }
-    CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
-    CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
+    {
+        ProfScope ps(c, MG_PROF_COARSE, fine);
+        CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
+        CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
+    }
     {
         ProfScope ps(c, MG_PROF_PROLONG, fine);
         CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, cur, s));
@@ -309,11 +336,16 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     return MG_OK;
 }
 
-// read the device scalars into the pinned mirror (one stream sync)
+// read the device scalars into the pinned mirror (one stream sync); report a kernel whose
+// bounded wait expired
 int read_scalars(mg_ctx *c)
 {
     CK(cudaMemcpyAsync(c->hscal, c->dscal, mg::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
+    if (c->hscal[mg::S_ERR] != 0.0) {
+        CK(cudaMemsetAsync(c->dscal + mg::S_ERR, 0, sizeof(double), c->s));
+        return fail(MG_ERR_CUDA, "a pipelined smoothing kernel's bounded wait expired (data not delivered)");
+    }
     return MG_OK;
 }
 
@@ -445,6 +477,129 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
     return MG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multigrid-preconditioned conjugate gradients, flexible (Polak-Ribiere) form:
+//   r = b - A p; z = M r; d = z
+//   repeat: q = A d; alpha = <r,z>/<d,q>; p += alpha d; r -= alpha q
+//           z' = M r; beta = (<r,z'> - <r,z>) / <r_old,z>; d = z' + beta d
+// M = inner_cycles V-cycles from a zero guess, FP64 or FP32 (on r scaled by the
+// RMS of the previous residual).  Convergence is decided on the recursive r and
+// confirmed with the true residual (restart from p if it is above tol).
+// ---------------------------------------------------------------------------
+int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
+{
+    cudaStream_t s = c->s;
+    const Dims d = c->dims[0];
+    const size_t n = d.n();
+    const double ih2 = 1.0 / (c->hs[0] * c->hs[0]);
+    const bool mixed = c->o.prec == MG_MIXED;
+    stats_begin(st);
+    if (st) st->ms_setup = c->ms_setup;
+    CK(cudaEventRecord(c->ev0, s));
+    CK(mg::launch_rhs_prepare(d, rhs, c->L64[0].dinv, c->b0, c->partials, c->dscal, s));
+    float *e_cur = mixed ? c->L32[0].p : nullptr, *e_old = mixed ? c->ke_alt : nullptr;
+    int sc_cur = mg::S_SCALE0, sc_old = mg::S_SCALE1;
+    double *z = c->kz, *zo = c->kzo;
+    int it = 0, status = MG_OK, nhist = 0;
+    double rel = 0.0, nb2 = 0.0;
+    bool done = false, zeroed = false;
+    // precondition: z = M r (FP64) or e_cur = M (r / scale) (mixed)
+    auto precondition = [&]() -> int {
+        if (mixed) {
+            CK(cudaMemsetAsync(e_cur, 0, n * sizeof(float), s));
+            for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, e_cur));
+        } else {
+            CK(cudaMemsetAsync(z, 0, n * sizeof(double), s));
+            for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<double>(c, c->L64, 0, c->kr, z));
+        }
+        return MG_OK;
+    };
+    while (!done) {
+        // (re)start: true residual
+        {
+            ProfScope ps(c, MG_PROF_RESID64, true);
+            CK(mg::launch_pcg_resid(d, ih2, c->L64[0], c->b0, p, c->kr, mixed ? c->L32[0].b : nullptr, c->partials,
+                                    c->dscal, sc_cur, s));
+        }
+        CKS(read_scalars(c));
+        nb2 = c->hscal[mg::S_NB2];
+        if (st) {
+            st->rhs_norm = std::sqrt(nb2);
+            st->rhs_mean_removed = c->nlive > 0 ? c->hscal[mg::S_SUM_B] / c->nlive : 0.0;
+        }
+        if (!std::isfinite(nb2)) return fail(MG_ERR_NAN, "right-hand side is not finite");
+        if (nb2 == 0.0 || c->nlive == 0.0) {
+            CK(cudaMemsetAsync(p, 0, n * sizeof(double), s));
+            rel = 0.0;
+            zeroed = true;
+            break;
+        }
+        rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
+        if (rel <= tol) break;
+        if (!std::isfinite(rel)) {
+            status = fail(MG_ERR_NAN, "residual norm is not finite after %d iterations", it);
+            break;
+        }
+        if (it >= c->o.max_cycles) {
+            status = fail(MG_ERR_NOT_CONVERGED, "not converged: relative residual %.3e after %d iterations (tol %.1e)",
+                          rel, it, tol);
+            break;
+        }
+        CKS(precondition());
+        if (mixed) {
+            CK(mg::launch_pcg_dots<float>(n, c->kr, e_cur, nullptr, c->partials, c->dscal, sc_cur, -1, s));
+            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 1, s));
+        } else {
+            CK(mg::launch_pcg_dots<double>(n, c->kr, z, nullptr, c->partials, c->dscal, -1, -1, s));
+            CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, 1, s));
+        }
+        for (;;) {
+            it++;
+            {
+                ProfScope ps(c, MG_PROF_APPLY, true);
+                CK(mg::launch_pcg_apply(d, ih2, c->L64[0], c->kd, c->kq, c->partials, c->dscal, s));
+            }
+            std::swap(e_cur, e_old);
+            std::swap(sc_cur, sc_old);
+            std::swap(z, zo);
+            {
+                ProfScope ps(c, MG_PROF_RESID64, true);
+                CK(mg::launch_pcg_update(n, c->kd, c->kq, p, c->kr, mixed ? c->L32[0].b : nullptr, c->partials, c->dscal,
+                                         sc_cur, s));
+            }
+            CKS(read_scalars(c));
+            rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
+            if (st && nhist < 256) st->resid_hist[nhist++] = rel;
+            if (rel <= tol || !std::isfinite(rel) || it >= c->o.max_cycles) break;
+            CKS(precondition());
+            ProfScope ps(c, MG_PROF_KRYLOV, true);
+            if (mixed) {
+                CK(mg::launch_pcg_dots<float>(n, c->kr, e_cur, e_old, c->partials, c->dscal, sc_cur, sc_old, s));
+                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 0, s));
+            } else {
+                CK(mg::launch_pcg_dots<double>(n, c->kr, z, zo, c->partials, c->dscal, -1, -1, s));
+                CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, 0, s));
+            }
+        }
+        if (!std::isfinite(rel)) {
+            status = fail(MG_ERR_NAN, "residual norm is not finite after %d iterations", it);
+            break;
+        }
+        // the loop top re-checks with the true residual (and restarts if needed)
+    }
+    (void)done;
+    if (!zeroed && (status == MG_OK || status == MG_ERR_NOT_CONVERGED))
+        CK(mg::launch_sub_mean_p(d, c->L64[0].dinv, p, c->dscal, s));
+    CK(cudaEventRecord(c->ev1, s));
+    CK(cudaEventSynchronize(c->ev1));
+    if (st) {
+        st->cycles = it;
+        st->rel_resid = rel;
+        cudaEventElapsedTime(&st->ms_solve, c->ev0, c->ev1);
+    }
+    return status;
+}
+
 int ensure(mg_ctx *c, double **p, size_t n)
 {
     if (*p) return MG_OK;
@@ -467,6 +622,7 @@ void mg_default_opts(mg_opts *o)
     o->inner_cycles = 1;
     o->profile = 0;
     o->smoother = 0;
+    o->krylov = 0;
 }
 
 const char *mg_last_error(void) { return g_err.c_str(); }
@@ -504,7 +660,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
-        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 2)
+        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1)
         return fail(MG_ERR_ARG, "mg_setup: invalid options");
 
     mg_ctx *c = new mg_ctx();
@@ -549,10 +705,20 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
         for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<float>(c, c->L32[l], c->dims[l].n(), true);
         if (st != MG_OK) return bail(st);
     }
+    if (c->o.krylov) {
+        const size_t n0 = c->dims[0].n();
+        st = c->alloc(&c->kr, n0);
+        if (st == MG_OK) st = c->alloc(&c->kd, n0);
+        if (st == MG_OK) st = c->alloc(&c->kq, n0);
+        if (st == MG_OK && c->o.prec == MG_MIXED) st = c->alloc(&c->ke_alt, n0);
+        if (st == MG_OK && c->o.prec != MG_MIXED) st = c->alloc(&c->kz, n0);
+        if (st == MG_OK && c->o.prec != MG_MIXED) st = c->alloc(&c->kzo, n0);
+        if (st != MG_OK) return bail(st);
+    }
     // second iterate buffers for the fused sweeps
     for (int l = 0; l + 1 < c->nlev && st == MG_OK; l++) {
         const bool f64 = c->o.smoother == 2 && fused_level(c->dims[l]);
-        const bool f32 = c->o.prec == MG_MIXED && c->o.smoother != 1 && fused_level(c->dims[l]);
+        const bool f32 = c->o.prec == MG_MIXED && c->o.smoother >= 2 && fused_level(c->dims[l]);
         if (f64) {
             c->palt64.resize(c->nlev, nullptr);
             st = c->alloc(&c->palt64[l], c->dims[l].n());
@@ -585,7 +751,10 @@ int mg_update(mg_ctx *c, const double *const face_coeffs[3])
     if (!c || !face_coeffs || !face_coeffs[0] || !face_coeffs[1] || !face_coeffs[2])
         return fail(MG_ERR_ARG, "mg_update: null argument");
     const auto t0 = std::chrono::steady_clock::now();
-    CKS(compute_hierarchy(c, face_coeffs));
+    {
+        ProfScope ps(c, MG_PROF_UPDATE, true);
+        CKS(compute_hierarchy(c, face_coeffs));
+    }
     c->ms_setup = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return MG_OK;
 }
@@ -596,7 +765,7 @@ int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stat
     if (!c || !rhs || !p) return fail(MG_ERR_ARG, "mg_solve: null argument");
     if (rhs == p) return fail(MG_ERR_ARG, "mg_solve: rhs and p must not alias");
     if (!(tol > 0.0)) return fail(MG_ERR_ARG, "mg_solve: tol must be > 0");
-    return solve_impl(c, rhs, p, tol, stats);
+    return c->o.krylov ? pcg_impl(c, rhs, p, tol, stats) : solve_impl(c, rhs, p, tol, stats);
 }
 
 int mg_vcycle(mg_ctx *c, const double *rhs, double *p)
@@ -638,7 +807,7 @@ int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], dou
     if (!(dt > 0.0) || !(tol > 0.0)) return fail(MG_ERR_ARG, "mg_project: dt and tol must be > 0");
     CKS(ensure(c, &c->rhs_tmp, c->dims[0].n()));
     CKS(mg_divergence(c, u_star, dt, c->rhs_tmp));
-    const int st = solve_impl(c, c->rhs_tmp, p, tol, stats);
+    const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, p, tol, stats) : solve_impl(c, c->rhs_tmp, p, tol, stats);
     if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
     const std::string keep = g_err;
     CKS(mg_correct(c, u_star, p, dt, u));
@@ -670,7 +839,7 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
     CK(mg::launch_face_mul(n, L.bx, L.by, L.bz, w[0], w[1], w[2], grad_u[0], grad_u[1], grad_u[2], c->s));
     CK(mg::launch_divergence(c->dims[0], 1.0 / c->g.h, L.bx, L.by, L.bz, grad_u[0], grad_u[1], grad_u[2], c->rhs_tmp,
                              c->s));
-    const int st = solve_impl(c, c->rhs_tmp, q, tol, stats);
+    const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, q, tol, stats) : solve_impl(c, c->rhs_tmp, q, tol, stats);
     if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
     const std::string keep = g_err;
     double *gb[3] = {nullptr, nullptr, nullptr};

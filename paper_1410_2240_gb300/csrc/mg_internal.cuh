@@ -39,11 +39,17 @@ enum Scal {
     S_SCALE0 = 4,  // mixed refinement: scale of the FP32 residual (ping)
     S_SCALE1 = 5,  // (pong)
     S_NLIVE = 6,   // number of live fine cells (as double)
+    S_RZ = 7,      // PCG: <r, z>
+    S_RZN = 8,     // PCG: new <r, z>
+    S_RZO = 9,     // PCG: <r_new, z_old> (flexible beta)
+    S_SIGMA = 10,  // PCG: <d, A d>
+    S_ERR = 11,    // set to nonzero by a kernel whose bounded wait expired
     S_COUNT = 16
 };
 
 // total kernels launched by this library in this process
 unsigned long long launch_count();
+void note_kernel_launch();
 
 // set the message mg_last_error() returns on this thread
 void set_last_error(const char *msg);
@@ -58,6 +64,11 @@ cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s);
+// FP32 fused sweep with TMA-staged planes (mg_sweep_tma.cu)
+bool tma_sweep_supported(Dims d);
+cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,
+                                float *p_new, int first, double *dscal, cudaStream_t s);
+
 // one full red-black sweep (first colour, then the other) from p_old into p_new
 template <typename T>
 cudaError_t launch_rb_sweep(Dims d, T h2, const LevelArrays<T> &L, const T *b, const T *p_old, T *p_new, int first,
@@ -82,6 +93,19 @@ cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, 
                               cudaStream_t s);
 cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, double *p, const double *dscal,
                               int scale_slot, cudaStream_t s);
+
+// multigrid-preconditioned CG (FP64 Krylov vectors)
+cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
+                             double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s);
+template <typename Z>
+cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, double *partials, double *dscal,
+                            int sz_slot, int so_slot, cudaStream_t s);
+template <typename Z>
+cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s);
+cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *dv, double *q,
+                             double *partials, double *dscal, cudaStream_t s);
+cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
+                              double *partials, double *dscal, int scale_slot, cudaStream_t s);
 
 // projection and adjoint
 cudaError_t launch_divergence(Dims d, double scale, const double *bx, const double *by, const double *bz,

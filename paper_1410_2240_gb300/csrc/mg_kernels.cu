@@ -16,6 +16,7 @@ namespace mg {
 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void note_kernel_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
@@ -592,6 +593,138 @@ __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const d
     gphi[c] = __dmul_rn(neg_half_drho, s);
 }
 
+// ---------------------------------------------------------------------------
+// Multigrid-preconditioned CG (flexible form).  FP64 Krylov vectors; the
+// preconditioned vector z is FP64 (plain FP64 solves) or s * e32 with the FP32
+// cycle's output e32 and the scale s the FP32 right-hand side was divided by.
+// Device scalars (Scal): S_RZ <r,z>, S_RZN / S_RZO new <r,z> and <r,z_old>,
+// S_SIGMA <d, A d>, S_RR ||r||^2.
+// ---------------------------------------------------------------------------
+
+// r = b - A p (FP64); optionally r32 = r / scale, scale = RMS of b (first pass) written to scale_slot
+__global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<double> L, const double *__restrict__ b,
+                            const double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
+                            double *__restrict__ dscal, int scale_slot, double *__restrict__ partials)
+{
+    const unsigned n = (unsigned)nx * ny * nz;
+    const size_t sxy = (size_t)nx * ny;
+    double inv_scale = 1.0;
+    if (r32) {
+        const double rms = sqrt(dscal[S_NB2] / dscal[S_NLIVE]);
+        const double sc = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
+        inv_scale = 1.0 / sc;
+        if (blockIdx.x == 0 && threadIdx.x == 0) dscal[scale_slot] = sc;
+    }
+    double rr = 0.0, sp = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(idx, nx, ny, i, j, k);
+        const double v = residual_at<double>(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        r[idx] = v;
+        if (r32) r32[idx] = (float)(v * inv_scale);
+        rr += v * v;
+        if (L.dinv[idx] > 0.0) sp += p[idx];
+    }
+    rr = block_sum<kRedThreads>(rr);
+    sp = block_sum<kRedThreads>(sp);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = rr;
+        partials[2 * blockIdx.x + 1] = sp;
+    }
+}
+
+// <r, z> and <r, z_old> with z = sz * Z, z_old = so * Zo (Z double: scales 1)
+template <typename Z>
+__global__ void k_pcg_dots(unsigned n, const double *__restrict__ r, const Z *__restrict__ z, const Z *__restrict__ zo,
+                           const double *__restrict__ dscal, int sz_slot, int so_slot, double *__restrict__ partials)
+{
+    const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
+    const double so = so_slot >= 0 ? dscal[so_slot] : 1.0;
+    double a = 0.0, c = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const double rv = r[idx];
+        a = fma(rv, sz * (double)z[idx], a);
+        if (zo) c = fma(rv, so * (double)zo[idx], c);
+    }
+    a = block_sum<kRedThreads>(a);
+    c = block_sum<kRedThreads>(c);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = c;
+    }
+}
+
+// d = sz * Z + beta d,  beta = (<r,z> - <r,z_old>) / <r_old, z_old>  (first: beta = 0)
+template <typename Z>
+__global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, const double *__restrict__ dscal,
+                          int sz_slot, int first)
+{
+    const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
+    const double beta = first ? 0.0 : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ];
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        d[idx] = fma(beta, first ? 0.0 : d[idx], sz * (double)z[idx]);
+}
+
+__global__ void k_pcg_shift_rz(double *dscal) { dscal[S_RZ] = dscal[S_RZN]; }
+
+// q = A d and <d, q>
+__global__ void k_pcg_apply(int nx, int ny, int nz, double ih2, LevelArrays<double> L, const double *__restrict__ d,
+                            double *__restrict__ q, double *__restrict__ partials)
+{
+    const unsigned n = (unsigned)nx * ny * nz;
+    const size_t sxy = (size_t)nx * ny;
+    double dq = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(idx, nx, ny, i, j, k);
+        const double dc = d[idx];
+        double s = 0.0;
+        if (i > 0) s = fma(L.bx[idx], d[idx - 1] - dc, s);
+        if (i < nx - 1) s = fma(L.bx[idx + 1], d[idx + 1] - dc, s);
+        if (j > 0) s = fma(L.by[idx], d[idx - nx] - dc, s);
+        if (j < ny - 1) s = fma(L.by[idx + nx], d[idx + nx] - dc, s);
+        if (k > 0) s = fma(L.bz[idx], d[idx - sxy] - dc, s);
+        if (k < nz - 1) s = fma(L.bz[idx + sxy], d[idx + sxy] - dc, s);
+        const double qv = s * ih2;
+        q[idx] = qv;
+        dq = fma(dc, qv, dq);
+    }
+    dq = block_sum<kRedThreads>(dq);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = dq;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// alpha = <r,z>/<d,Ad>; p += alpha d; r -= alpha q; ||r||^2; optionally r32 = r / scale with
+// scale = RMS of the previous residual (written to scale_slot)
+__global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
+                             double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
+                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials)
+{
+    const double alpha = dscal[S_RZ] / dscal[S_SIGMA];
+    double inv_scale = 1.0;
+    if (r32) {
+        const double rms = sqrt(dscal[S_RR] / dscal[S_NLIVE]);
+        const double sc = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
+        inv_scale = 1.0 / sc;
+        if (blockIdx.x == 0 && threadIdx.x == 0) dscal[scale_slot] = sc;
+    }
+    double rr = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        p[idx] = fma(alpha, d[idx], p[idx]);
+        const double rv = fma(-alpha, q[idx], r[idx]);
+        r[idx] = rv;
+        if (r32) r32[idx] = (float)(rv * inv_scale);
+        rr = fma(rv, rv, rr);
+    }
+    rr = block_sum<kRedThreads>(rr);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = rr;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
 inline dim3 row_grid(int threads_x, int ny, int nz)
 {
     return dim3((unsigned)((threads_x + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)nz);
@@ -827,6 +960,68 @@ cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, cons
     note_launch();
     k_phi_grad<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, neg_half_drho, bx, by, bz, gbx,
                                                                    gby, gbz, gphi);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
+                             double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s)
+{
+    const unsigned g = red_grid(d.n());
+    note_launch();
+    k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
+    return cudaGetLastError();
+}
+
+template <typename Z>
+cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, double *partials, double *dscal,
+                            int sz_slot, int so_slot, cudaStream_t s)
+{
+    const unsigned g = red_grid(n);
+    note_launch();
+    k_pcg_dots<Z><<<g, kRedThreads, 0, s>>>((unsigned)n, r, z, zo, dscal, sz_slot, so_slot, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RZN, S_RZO);
+    return cudaGetLastError();
+}
+template cudaError_t launch_pcg_dots<double>(size_t, const double *, const double *, const double *, double *,
+                                             double *, int, int, cudaStream_t);
+template cudaError_t launch_pcg_dots<float>(size_t, const double *, const float *, const float *, double *, double *,
+                                            int, int, cudaStream_t);
+
+template <typename Z>
+cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s)
+{
+    note_launch();
+    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, first);
+    note_launch();
+    k_pcg_shift_rz<<<1, 1, 0, s>>>(dscal);
+    return cudaGetLastError();
+}
+template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, cudaStream_t);
+template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, cudaStream_t);
+
+cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *dv, double *q,
+                             double *partials, double *dscal, cudaStream_t s)
+{
+    const unsigned g = red_grid(d.n());
+    note_launch();
+    k_pcg_apply<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, dv, q, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_SIGMA, -1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
+                              double *partials, double *dscal, int scale_slot, cudaStream_t s)
+{
+    const unsigned g = red_grid(n);
+    note_launch();
+    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, -1);
     return cudaGetLastError();
 }
 

@@ -41,7 +41,8 @@ class Bc(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("coarse_max_cells", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("profile", ctypes.c_int), ("smoother", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("profile", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -79,7 +80,7 @@ _lib.mg_profile_reset.argtypes = [_vp]
 _lib.mg_residual_norm_noalloc.argtypes = [ctypes.POINTER(Grid), _PP, _vp, _vp, _vp, _vp]
 _lib.mg_destroy.argtypes = [_vp]
 
-PROF_SMOOTH, PROF_RESTRICT, PROF_PROLONG, PROF_RESID64 = 0, 1, 2, 3
+PROF_SMOOTH, PROF_RESTRICT, PROF_PROLONG, PROF_RESID64, PROF_APPLY, PROF_KRYLOV, PROF_COARSE, PROF_UPDATE = range(8)
 
 
 def kernel_launches() -> int:

@@ -184,13 +184,16 @@ FUSED_CASES = {
     "ragged_160x32x32": lambda: synth.small_case(160, 32, 32, solid="ellipsoid", seed=41),
     "ragged_48x24x40": lambda: synth.small_case(48, 24, 40, solid="ellipsoid", seed=42),
     "aniso_64x32x16": lambda: synth.small_case(64, 32, 16, solid="ellipsoid", seed=43),
+    "odd_x_34x16x16": lambda: synth.small_case(34, 16, 16, solid="none", seed=44),
+    "c3_256": lambda: synth.case_c3(256),
 }
 
 
 @pytest.mark.parametrize("name", list(FUSED_CASES))
 def test_fused_sweep_bit_identical_to_colour_passes(mgp, name):
-    """The fused red-black sweep (one pass, overlapped tiles, z-wavefront) gives bit-identical
-    V-cycles (FP64) and mixed solves (FP32 cycles) to one pass per colour."""
+    """The fused red-black sweeps (one pass, overlapped tiles, z-wavefront; register-staged for
+    smoother=2, TMA-staged for FP32 in auto mode) give bit-identical V-cycles (FP64) and mixed
+    solves (FP32 cycles) to one pass per colour."""
     case = FUSED_CASES[name]()
     beta = mgp.face_coeffs(dev(case.phi), case.h, None if case.solid is None else dev(case.solid, dtype=torch.uint8),
                            rho_air=case.lam)
@@ -206,7 +209,45 @@ def test_fused_sweep_bit_identical_to_colour_passes(mgp, name):
         fused.vcycle(bd, p2)
         assert torch.equal(p1, p2)
     m1 = mgp.Context(beta, case.h, prec="mixed", smoother=1, coarse_max_cells=2048)
-    m0 = mgp.Context(beta, case.h, prec="mixed", smoother=0, coarse_max_cells=2048)
     q1, s1 = m1.solve(bd, tol=1e-10)
-    q0, s0 = m0.solve(bd, tol=1e-10)
-    assert s1.cycles == s0.cycles and torch.equal(q1, q0)
+    for sm in (0, 2, 3):
+        m = mgp.Context(beta, case.h, prec="mixed", smoother=sm, coarse_max_cells=2048)
+        q, st = m.solve(bd, tol=1e-10)
+        assert st.cycles == s1.cycles and torch.equal(q, q1), sm
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_64", "ell16", "odd_coarse_24", "aniso_64x32x16"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("vcycles", [1, 2])
+def test_pcg_solve_matches_oracle(mgp, name, prec, vcycles):
+    """Multigrid-preconditioned CG on the GPU: residual 1e-10 by the oracle's operator, the oracle's
+    solution to 1e-9, and (FP64) the oracle's PCG iteration count within one."""
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case, prec=prec, krylov=1, inner_cycles=vcycles)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = case_rhs(case, beta_o)
+    mg = O.MG(beta_o, case.h, max_coarse=4096)
+    p_o, _, _ = mg.solve(rhs, tol=1e-12, max_cycles=300)
+    p_g, st = ctx.solve(dev(rhs), tol=1e-10)
+    pg = host(p_g)
+    lab, nc = O.components(beta_o)
+    b = O.remove_mean(rhs, lab, nc)
+    assert np.linalg.norm(O.residual(beta_o, b, pg, case.h)) / np.linalg.norm(b) <= 1.0001e-10
+    assert rel(pg, p_o) <= 1e-9
+    if prec == "fp64":
+        _, it_o, _ = mg.pcg(rhs, tol=1e-10, vcycles=vcycles)
+        assert abs(st.cycles - it_o) <= 1, (st.cycles, it_o)
+
+
+def test_pcg_projection_and_adjoint(mgp):
+    case = SMALL["c2_64"]
+    beta_g, ctx = _ctx(mgp, case, prec="mixed", krylov=1, inner_cycles=2)
+    uo, po, beta_o, rhs = O.project(case.phi, case.solid, case.u_star, case.h, lam=case.lam, tol=1e-12)
+    ug, pg, st = ctx.project(faces_dev(case.u_star), tol=1e-10)
+    scale = max(np.abs(x).max() for x in uo)
+    for a, b in zip(faces_host(ug), uo):
+        assert np.abs(a - b).max() <= 1e-8 * scale
+    gu_o, gb_o, _ = O.project_adjoint(beta_o, po, case.w, case.h, lam=case.lam, tol=1e-12)
+    gu_g, gb_g, st = ctx.project_adjoint(faces_dev(case.w), dev(po), tol=1e-12)
+    for a, b in zip(faces_host(gu_g), gu_o):
+        assert np.abs(a - b).max() <= 1e-8 * max(np.abs(b).max(), 1.0)
