@@ -90,6 +90,9 @@ typedef struct {
                              gradients preconditioned by inner_cycles V-cycles from a zero guess
                              (flexible Polak-Ribiere form; FP64 Krylov vectors, the cycles in the
                              precision prec selects) [0] */
+    int coarse_graph;     /* 1: replay the coarse-grid part of each V-cycle (all levels below the
+                             finest) as one CUDA graph captured on first use on a private stream;
+                             0: launch its kernels one by one.  Identical results [1] */
 } mg_opts;
 
 /* Solve statistics (host struct, filled when non-NULL). */

@@ -26,7 +26,9 @@ def _context(beta, h, prec):
     if mg is None:
         if len(_CONTEXTS) >= 4:
             _CONTEXTS.pop(next(iter(_CONTEXTS))).close()
-        mg = _CONTEXTS[key] = mgproj.Context(beta, h, prec=prec)
+        # CG preconditioned by V-cycles: 2 cycles per application with FP32 cycles, 1 with FP64
+        mg = _CONTEXTS[key] = mgproj.Context(beta, h, prec=prec, krylov=1,
+                                             inner_cycles=2 if prec == mgproj.MG_MIXED else 1)
     else:
         mg.update(beta)
     return mg

@@ -68,6 +68,7 @@ struct mg_ctx {
     // conjugate-gradient vectors (krylov = 1): FP64 r, d, q; z, z_old (FP64 cycles) or a
     // second FP32 cycle output (mixed cycles)
     double *kr = nullptr, *kd = nullptr, *kq = nullptr, *kz = nullptr, *kzo = nullptr;
+    double *kdiag = nullptr;  // finest-grid sum of face coefficients (CG operator)
     float *ke_alt = nullptr;
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
@@ -78,6 +79,12 @@ struct mg_ctx {
     double *dscal = nullptr;    // device scalars (mg::Scal)
     double *hscal = nullptr;    // pinned host mirror of dscal
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // the coarse-grid correction of one V-cycle (everything below the finest level) as a
+    // CUDA graph per precision, captured on first use on a private stream
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t coarse_graph[2] = {nullptr, nullptr};  // [0] FP64, [1] FP32
+    unsigned long long coarse_graph_kernels[2] = {0, 0};   // kernel nodes per graph (launch counter)
+    bool capturing = false;
     float ms_setup = 0.f;
     double nlive = 0.0;
     std::vector<void *> allocs;
@@ -106,6 +113,9 @@ struct mg_ctx {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
+        for (cudaGraphExec_t g : coarse_graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
 
@@ -234,7 +244,7 @@ struct ProfScope {
     int slot = -1;
     ProfScope(mg_ctx *c_, int group, bool on) : c(c_)
     {
-        if (!on || !c->o.profile || c->pused + 2 > c->pev.size()) return;
+        if (!on || !c->o.profile || c->capturing || c->pused + 2 > c->pev.size()) return;
         slot = (int)c->pused;
         c->pused += 2;
         c->pgroup[slot / 2] = group;
@@ -288,6 +298,9 @@ inline cudaError_t launch_sweep_tma(Dims, double, const LevelArrays<double> &, c
 }
 
 template <typename T>
+int coarse_correction_graph(mg_ctx *c, const std::vector<LevelArrays<T>> &L);
+
+template <typename T>
 int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T *p)
 {
     cudaStream_t s = c->s;
@@ -324,8 +337,12 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     }
     {
         ProfScope ps(c, MG_PROF_COARSE, fine);
-        CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
-        CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
+        if (fine && c->o.coarse_graph && !c->capturing)
+            CKS(coarse_correction_graph<T>(c, L));
+        else {
+            CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
+            CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
+        }
     }
     {
         ProfScope ps(c, MG_PROF_PROLONG, fine);
@@ -333,6 +350,50 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     }
     for (int it = 0; it < c->o.nu2; it++) CKS(sweep(1));
     if (cur != p) CK(cudaMemcpyAsync(p, cur, d.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return MG_OK;
+}
+
+// The coarse-grid correction of a V-cycle on the finest level: zero the level-1
+// correction, V-cycle levels 1..coarsest.  Its buffers are the context's own, so one
+// captured graph per precision serves every call; it is launched on the caller's stream.
+template <typename T>
+int coarse_correction_graph(mg_ctx *c, const std::vector<LevelArrays<T>> &L)
+{
+    const int slot = sizeof(T) == 4 ? 1 : 0;
+    if (!c->coarse_graph[slot]) {
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = c->s;
+        c->s = c->cap_stream;
+        c->capturing = true;
+        cudaGraph_t g = nullptr;
+        int st = MG_OK;
+        const unsigned long long k0 = mg::launch_count();
+        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = [&]() -> int {
+                CK(cudaMemsetAsync(L[1].p, 0, c->dims[1].n() * sizeof(T), c->s));
+                CKS(vcycle<T>(c, L, 1, L[1].b, L[1].p));
+                return MG_OK;
+            }();
+            e = cudaStreamEndCapture(c->cap_stream, &g);
+        }
+        c->s = user;
+        c->capturing = false;
+        c->coarse_graph_kernels[slot] = mg::launch_count() - k0;
+        if (st != MG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, "coarse-grid graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->coarse_graph[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->coarse_graph[slot] = nullptr;
+            return fail(MG_ERR_CUDA, "coarse-grid graph instantiation failed: %s", cudaGetErrorString(e));
+        }
+    }
+    CK(cudaGraphLaunch(c->coarse_graph[slot], c->s));
+    for (unsigned long long k = 0; k < c->coarse_graph_kernels[slot]; k++) mg::note_kernel_launch();
     return MG_OK;
 }
 
@@ -451,6 +512,7 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
         CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv, s));
     }
     CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
+    if (c->kdiag) CK(mg::launch_diag(c->dims[0], c->L64[0].bx, c->L64[0].by, c->L64[0].bz, c->kdiag, s));
     // coarsest operator to the host
     const int nc = c->ncoarse;
     std::vector<double> cb[3];
@@ -547,7 +609,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
         }
         CKS(precondition());
         if (mixed) {
-            CK(mg::launch_pcg_dots<float>(n, c->kr, e_cur, nullptr, c->partials, c->dscal, sc_cur, -1, s));
+            CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, nullptr, c->partials, c->dscal, sc_cur, sc_cur, -1, s));
             CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 1, s));
         } else {
             CK(mg::launch_pcg_dots<double>(n, c->kr, z, nullptr, c->partials, c->dscal, -1, -1, s));
@@ -557,7 +619,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             it++;
             {
                 ProfScope ps(c, MG_PROF_APPLY, true);
-                CK(mg::launch_pcg_apply(d, ih2, c->L64[0], c->kd, c->kq, c->partials, c->dscal, s));
+                CK(mg::launch_pcg_apply(d, ih2, c->L64[0], c->kdiag, c->kd, c->kq, c->partials, c->dscal, s));
             }
             std::swap(e_cur, e_old);
             std::swap(sc_cur, sc_old);
@@ -574,7 +636,8 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             CKS(precondition());
             ProfScope ps(c, MG_PROF_KRYLOV, true);
             if (mixed) {
-                CK(mg::launch_pcg_dots<float>(n, c->kr, e_cur, e_old, c->partials, c->dscal, sc_cur, sc_old, s));
+                CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, e_old, c->partials, c->dscal, sc_cur, sc_cur, sc_old,
+                                         s));
                 CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 0, s));
             } else {
                 CK(mg::launch_pcg_dots<double>(n, c->kr, z, zo, c->partials, c->dscal, -1, -1, s));
@@ -623,6 +686,7 @@ void mg_default_opts(mg_opts *o)
     o->profile = 0;
     o->smoother = 0;
     o->krylov = 0;
+    o->coarse_graph = 1;
 }
 
 const char *mg_last_error(void) { return g_err.c_str(); }
@@ -660,7 +724,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
-        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1)
+        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1)
         return fail(MG_ERR_ARG, "mg_setup: invalid options");
 
     mg_ctx *c = new mg_ctx();
@@ -708,6 +772,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (c->o.krylov) {
         const size_t n0 = c->dims[0].n();
         st = c->alloc(&c->kr, n0);
+        if (st == MG_OK) st = c->alloc(&c->kdiag, n0);
         if (st == MG_OK) st = c->alloc(&c->kd, n0);
         if (st == MG_OK) st = c->alloc(&c->kq, n0);
         if (st == MG_OK && c->o.prec == MG_MIXED) st = c->alloc(&c->ke_alt, n0);

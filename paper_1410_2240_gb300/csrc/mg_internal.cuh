@@ -26,8 +26,9 @@ struct LevelArrays {
     T *p = nullptr;                                  // correction (levels >= 1)
 };
 
-// Number of CTAs of the grid-stride reduction kernels (a multiple of the 152 SMs).
-constexpr int kRedBlocks = 608;
+// Number of CTAs of the grid-stride vector and reduction kernels (16 per SM on 152 SMs,
+// enough loads in flight to keep HBM busy).
+constexpr int kRedBlocks = 2432;
 constexpr int kRedThreads = 256;
 
 // Device scalar slots (FP64) in ctx->dscal.
@@ -100,10 +101,13 @@ cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, c
 template <typename Z>
 cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, double *partials, double *dscal,
                             int sz_slot, int so_slot, cudaStream_t s);
+cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const float *zo, double *partials,
+                              double *dscal, int sr_slot, int sz_slot, int so_slot, cudaStream_t s);
 template <typename Z>
 cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s);
-cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *dv, double *q,
-                             double *partials, double *dscal, cudaStream_t s);
+cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
+                             double *q, double *partials, double *dscal, cudaStream_t s);
+cudaError_t launch_diag(Dims d, const double *bx, const double *by, const double *bz, double *diag, cudaStream_t s);
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
                               double *partials, double *dscal, int scale_slot, cudaStream_t s);
 

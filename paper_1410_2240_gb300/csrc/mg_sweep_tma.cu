@@ -11,8 +11,8 @@
 // per-colour smoother (fused multiply-adds in the order x-, x+, y-, y+, z-, z+),
 // so the result is bit-identical to two colour passes.
 //
-// Data movement: one elected thread streams whole plane tiles of the six inputs
-// (p, bx, by, bz, dinv, b) from HBM into a ring of shared-memory stages with TMA
+// Data movement: one elected thread streams whole plane tiles of the five inputs
+// (p, bx, by, bz, b) from HBM into a ring of shared-memory stages with TMA
 // (cp.async.bulk.tensor.3d, completion counted on one mbarrier per stage), several
 // planes ahead of the compute.  The tile is (TX + 8) x (TY + 4): a halo of 4
 // columns in x keeps every copy's start on a 16-byte boundary, 2 rows in y; cells
@@ -31,18 +31,31 @@
 namespace mg {
 namespace {
 
-constexpr int TX = 32, TY = 8;       // interior tile
+#ifndef MG_TMA_TX
+#define MG_TMA_TX 32
+#endif
+#ifndef MG_TMA_TY
+#define MG_TMA_TY 8
+#endif
+#ifndef MG_TMA_STAGES
+#define MG_TMA_STAGES 6
+#endif
+#ifndef MG_TMA_CTAS_PER_SM
+#define MG_TMA_CTAS_PER_SM 3
+#endif
+constexpr int TX = MG_TMA_TX, TY = MG_TMA_TY;  // interior tile
 constexpr int BW = TX + 8;           // TMA box width (x halo 4 each side)
 constexpr int BH = TY + 4;           // TMA box height (y halo 2 each side)
 constexpr int CW = TX + 2, CH = TY + 2;  // compute region: interior + ring 1
-constexpr int NA = 6;                // arrays per plane: p, bx, by, bz, dinv, b
-constexpr int STAGES = 6;            // resident planes s-1, s, s+1 plus 3 in flight
-constexpr int TILE = BW * BH;        // floats per array tile (1920 B, a multiple of 128 B)
+constexpr int NA = 5;                // arrays per plane: p, bx, by, bz, b (1/diag is formed on the fly)
+constexpr int STAGES = MG_TMA_STAGES;  // resident planes s-1, s, s+1, the rest in flight
+constexpr int TILE = BW * BH;        // floats per array tile (a multiple of 32 floats = 128 B)
+static_assert((TILE * sizeof(float)) % 128 == 0, "tiles must stay 128-byte aligned");
 constexpr int THREADS = CW * CH;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * NA * TILE * sizeof(float) + STAGES * sizeof(unsigned long long) + 128;
 constexpr long kWaitLimit = 1L << 24;
 
-enum { A_P = 0, A_BX = 1, A_BY = 2, A_BZ = 3, A_DI = 4, A_B = 5 };
+enum { A_P = 0, A_BX = 1, A_BY = 2, A_BZ = 3, A_B = 4 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -90,6 +103,13 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 struct Maps {
     CUtensorMap m[NA];
 };
+
+// 1 / (sum of the six face coefficients), summed in the order of the per-colour smoother
+__device__ __forceinline__ float inv_diag32(float bxl, float bxh, float byl, float byh, float bzl, float bzh)
+{
+    const float sum = ((((bxl + bxh) + byl) + byh) + bzl) + bzh;
+    return sum > 0.f ? 1.f / sum : 0.f;
+}
 
 __global__ void __launch_bounds__(THREADS) k_rb_sweep_tma(const __grid_constant__ Maps maps, int nx, int ny, int nz,
                                                           int zc, float h2, float *__restrict__ p_new, int first,
@@ -163,13 +183,16 @@ __global__ void __launch_bounds__(THREADS) k_rb_sweep_tma(const __grid_constant_
         if (dom && s >= 0 && s < nz && ((i + j + s) & 1) == first) {
             const float *tbx = tile(s, A_BX), *tby = tile(s, A_BY);
             float acc = 0.f;
-            if (xlo) acc = fmaf(at(tbx, sy, sx), at(tp, sy, sx - 1), acc);
-            if (xhi) acc = fmaf(at(tbx, sy, sx + 1), at(tp, sy, sx + 1), acc);
-            if (ylo) acc = fmaf(at(tby, sy, sx), at(tp, sy - 1, sx), acc);
-            if (yhi) acc = fmaf(at(tby, sy + 1, sx), at(tp, sy + 1, sx), acc);
-            if (s > 0) acc = fmaf(at(tile(s, A_BZ), sy, sx), q_m1, acc);
-            if (s < nz - 1) acc = fmaf(at(tile(s + 1, A_BZ), sy, sx), q_p1, acc);
-            q_0 = at(tile(s, A_DI), sy, sx) * fmaf(-h2, at(tile(s, A_B), sy, sx), acc);
+            const float bxl = at(tbx, sy, sx), bxh = xhi ? at(tbx, sy, sx + 1) : 0.f;
+            const float byl = at(tby, sy, sx), byh = yhi ? at(tby, sy + 1, sx) : 0.f;
+            const float bzl = at(tile(s, A_BZ), sy, sx), bzh = (s < nz - 1) ? at(tile(s + 1, A_BZ), sy, sx) : 0.f;
+            if (xlo) acc = fmaf(bxl, at(tp, sy, sx - 1), acc);
+            if (xhi) acc = fmaf(bxh, at(tp, sy, sx + 1), acc);
+            if (ylo) acc = fmaf(byl, at(tp, sy - 1, sx), acc);
+            if (yhi) acc = fmaf(byh, at(tp, sy + 1, sx), acc);
+            if (s > 0) acc = fmaf(bzl, q_m1, acc);
+            if (s < nz - 1) acc = fmaf(bzh, q_p1, acc);
+            q_0 = inv_diag32(bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, at(tile(s, A_B), sy, sx), acc);
             tp[sy * BW + sx] = q_0;
         }
         __syncthreads();
@@ -179,13 +202,16 @@ __global__ void __launch_bounds__(THREADS) k_rb_sweep_tma(const __grid_constant_
             if (((i + j + z) & 1) == second) {
                 const float *tq = tile(z, A_P), *tbx = tile(z, A_BX), *tby = tile(z, A_BY);
                 float acc = 0.f;
-                if (xlo) acc = fmaf(at(tbx, sy, sx), at(tq, sy, sx - 1), acc);
-                if (xhi) acc = fmaf(at(tbx, sy, sx + 1), at(tq, sy, sx + 1), acc);
-                if (ylo) acc = fmaf(at(tby, sy, sx), at(tq, sy - 1, sx), acc);
-                if (yhi) acc = fmaf(at(tby, sy + 1, sx), at(tq, sy + 1, sx), acc);
-                if (z > 0) acc = fmaf(at(tile(z, A_BZ), sy, sx), q_m2, acc);
-                if (z < nz - 1) acc = fmaf(at(tile(s, A_BZ), sy, sx), q_0, acc);
-                q_m1 = at(tile(z, A_DI), sy, sx) * fmaf(-h2, at(tile(z, A_B), sy, sx), acc);
+                const float bxl = at(tbx, sy, sx), bxh = xhi ? at(tbx, sy, sx + 1) : 0.f;
+                const float byl = at(tby, sy, sx), byh = yhi ? at(tby, sy + 1, sx) : 0.f;
+                const float bzl = at(tile(z, A_BZ), sy, sx), bzh = (z < nz - 1) ? at(tile(s, A_BZ), sy, sx) : 0.f;
+                if (xlo) acc = fmaf(bxl, at(tq, sy, sx - 1), acc);
+                if (xhi) acc = fmaf(bxh, at(tq, sy, sx + 1), acc);
+                if (ylo) acc = fmaf(byl, at(tq, sy - 1, sx), acc);
+                if (yhi) acc = fmaf(byh, at(tq, sy + 1, sx), acc);
+                if (z > 0) acc = fmaf(bzl, q_m2, acc);
+                if (z < nz - 1) acc = fmaf(bzh, q_0, acc);
+                q_m1 = inv_diag32(bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, at(tile(z, A_B), sy, sx), acc);
             }
             p_new[(size_t)z * sxy + col] = q_m1;
         }
@@ -260,8 +286,8 @@ bool tma_sweep_supported(Dims d)
     return d.nx % 4 == 0 && d.nx >= TX && d.ny >= TY && d.nz >= 8;
 }
 
-cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,
-                                float *p_new, int first, double *dscal, cudaStream_t s)
+cudaError_t launch_rb_sweep_tma_zc(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,
+                                   float *p_new, int first, double *dscal, cudaStream_t s, int zc_force)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -270,7 +296,7 @@ cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, c
         attr_set = true;
     }
     Maps maps;
-    const float *src[NA] = {p_old, L.bx, L.by, L.bz, L.dinv, b};
+    const float *src[NA] = {p_old, L.bx, L.by, L.bz, b};
     for (int a = 0; a < NA; a++) {
         cudaError_t e = map_of(src[a], d.nx, d.ny, d.nz, &maps.m[a]);
         if (e != cudaSuccess) return e;
@@ -278,7 +304,7 @@ cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, c
     const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY;
     // z-chunk: balance whole waves of resident CTAs (3 per SM on 152 SMs) against the two
     // extra planes each chunk recomputes
-    const int wave = 3 * 152;
+    const int wave = MG_TMA_CTAS_PER_SM * 152;
     int zc = d.nz;
     double best = 1e300;
     for (int cand : {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024}) {
@@ -291,10 +317,17 @@ cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, c
             zc = c;
         }
     }
+    if (zc_force > 0) zc = zc_force < d.nz ? zc_force : d.nz;
     const dim3 grid((unsigned)tx, (unsigned)ty, (unsigned)((d.nz + zc - 1) / zc));
     note_kernel_launch();
     k_rb_sweep_tma<<<grid, THREADS, SMEM_BYTES, s>>>(maps, d.nx, d.ny, d.nz, zc, h2, p_new, first, dscal);
     return cudaGetLastError();
+}
+
+cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,
+                                float *p_new, int first, double *dscal, cudaStream_t s)
+{
+    return launch_rb_sweep_tma_zc(d, h2, L, b, p_old, p_new, first, dscal, s, 0);
 }
 
 }  // namespace mg

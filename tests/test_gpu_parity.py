@@ -251,3 +251,19 @@ def test_pcg_projection_and_adjoint(mgp):
     gu_g, gb_g, st = ctx.project_adjoint(faces_dev(case.w), dev(po), tol=1e-12)
     for a, b in zip(faces_host(gu_g), gu_o):
         assert np.abs(a - b).max() <= 1e-8 * max(np.abs(b).max(), 1.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_coarse_graph_identical_to_launches(mgp, prec):
+    """Replaying the coarse-grid correction as a CUDA graph changes nothing."""
+    case = SMALL["c2_64"]
+    beta = mgp.face_coeffs(dev(case.phi), case.h, dev(case.solid, dtype=torch.uint8), rho_air=case.lam)
+    rhs = mgp.Context(beta, case.h).divergence(faces_dev(case.u_star))
+    out = []
+    for g in (0, 1):
+        ctx = mgp.Context(beta, case.h, prec=prec, coarse_graph=g, krylov=1, inner_cycles=2)
+        p, st = ctx.solve(rhs, tol=1e-10)
+        p2, st2 = ctx.solve(rhs, torch.zeros_like(rhs), tol=1e-10)  # the graph is replayed
+        assert torch.equal(p, p2)
+        out.append((p, st.cycles))
+    assert out[0][1] == out[1][1] and torch.equal(out[0][0], out[1][0])
