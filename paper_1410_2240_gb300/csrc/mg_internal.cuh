@@ -63,8 +63,10 @@ cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *di
 cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s);
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
+// one colour of a red-black sweep on planes [z0, z1) (z1 < 0: to the last plane)
 template <typename T>
-cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s);
+cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
+                          int z0 = 0, int z1 = -1);
 // FP32 fused sweep with TMA-staged planes (mg_sweep_tma.cu)
 bool tma_sweep_supported(Dims d);
 cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,

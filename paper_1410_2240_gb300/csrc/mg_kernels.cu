@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 
 #include "mg_internal.cuh"
 
@@ -159,9 +160,9 @@ __device__ __forceinline__ T inv_diag(T stored, T bxl, T bxh, T byl, T byh, T bz
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T *__restrict__ b,
-                         T *__restrict__ p, int colour)
+                         T *__restrict__ p, int colour, int z0)
 {
-    const int j = blockIdx.y, k = blockIdx.z;
+    const int j = blockIdx.y, k = blockIdx.z + z0;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
@@ -177,6 +178,30 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
     if (k > 0) s = fma(bzl, p[c - sxy], s);
     if (k < nz - 1) s = fma(bzh, p[c + sxy], s);
     p[c] = inv_diag<T>(sizeof(T) == 8 ? L.dinv[c] : T(0), bxl, bxh, byl, byh, bzl, bzh) * fma(-h2, b[c], s);
+}
+
+// Trilinear cell-centred prolongation of the coarse correction ec at fine cell (i,j,k): weights
+// 3/4 on the parent and 1/4 on the next coarse cell toward the fine cell, per axis, that index
+// clamped to the domain; the 8 weighted values are accumulated with fused multiply-adds in the
+// order K, J, I.
+template <typename T>
+__device__ __forceinline__ T prolong_at(int i, int j, int k, int NX, int NY, int NZ, const T *__restrict__ ec)
+{
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int I1 = min(max((i & 1) ? I0 + 1 : I0 - 1, 0), NX - 1);
+    const int J1 = min(max((j & 1) ? J0 + 1 : J0 - 1, 0), NY - 1);
+    const int K1 = min(max((k & 1) ? K0 + 1 : K0 - 1, 0), NZ - 1);
+    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
+    const T w[2] = {T(0.75), T(0.25)};
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int bb = 0; bb < 2; bb++)
+#pragma unroll
+            for (int d = 0; d < 2; d++)
+                s = fma(w[a] * w[bb] * w[d], ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]], s);
+    return s;
 }
 
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
@@ -229,22 +254,7 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
     if (i >= nx) return;
     const size_t c = ((size_t)k * ny + j) * nx + i;
     if (dinv[c] == T(0)) return;
-    const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int I1 = min(max((i & 1) ? I0 + 1 : I0 - 1, 0), NX - 1);
-    const int J1 = min(max((j & 1) ? J0 + 1 : J0 - 1, 0), NY - 1);
-    const int K1 = min(max((k & 1) ? K0 + 1 : K0 - 1, 0), NZ - 1);
-    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
-    const T w[2] = {T(0.75), T(0.25)};
-    T s = T(0);
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int bb = 0; bb < 2; bb++)
-#pragma unroll
-            for (int d = 0; d < 2; d++)
-                s = fma(w[a] * w[bb] * w[d], ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]], s);
-    p[c] += s;
+    p[c] += prolong_at<T>(i, j, k, nx / 2, ny / 2, nz / 2, ec);
 }
 
 // ---------------------------------------------------------------------------
@@ -518,9 +528,17 @@ __global__ void k_divergence(int nx, int ny, int nz, double scale, const double 
 }
 
 // u_f = u*_f - dt beta_f (p_c - p_nb) / h on open low faces; closed faces copy u*.
-__global__ void k_correct(int nx, int ny, int nz, double dt, double h, const double *__restrict__ bx,
-                          const double *__restrict__ by, const double *__restrict__ bz, const double *__restrict__ p,
-                          const double *ux0, const double *uy0, const double *uz0, double *ux, double *uy, double *uz)
+// x / h, rounded once: a multiply by 1/h when h is a power of two (then x * (1/h) is exact and
+// equal to the quotient), an IEEE division otherwise
+__device__ __forceinline__ double div_h(double x, double h, double inv_h, bool pow2)
+{
+    return pow2 ? __dmul_rn(x, inv_h) : x / h;
+}
+
+__global__ void k_correct(int nx, int ny, int nz, double dt, double h, double inv_h, int pow2,
+                          const double *__restrict__ bx, const double *__restrict__ by, const double *__restrict__ bz,
+                          const double *__restrict__ p, const double *ux0, const double *uy0, const double *uz0,
+                          double *ux, double *uy, double *uz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
@@ -528,15 +546,15 @@ __global__ void k_correct(int nx, int ny, int nz, double dt, double h, const dou
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     const double pc = p[c];
     double b = bx[c], u = ux0[c];
-    if (i > 0 && b > 0.0) u = __dsub_rn(u, __dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - 1])) / h);
+    if (i > 0 && b > 0.0) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
     ux[c] = u;
     b = by[c];
     u = uy0[c];
-    if (j > 0 && b > 0.0) u = __dsub_rn(u, __dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - nx])) / h);
+    if (j > 0 && b > 0.0) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - nx])), h, inv_h, pow2));
     uy[c] = u;
     b = bz[c];
     u = uz0[c];
-    if (k > 0 && b > 0.0) u = __dsub_rn(u, __dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - sxy])) / h);
+    if (k > 0 && b > 0.0) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - sxy])), h, inv_h, pow2));
     uz[c] = u;
 }
 
@@ -554,11 +572,11 @@ __global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double
 
 // grad_u = w - G q (open faces) / w (closed);  grad_beta = dt (G p)((G q) - w) (open) / 0 (closed)
 __device__ __forceinline__ void adj_face(double b, double pc, double pn, double qc, double qn, double w, double h,
-                                         double dt, double &gu, double &gb)
+                                         double inv_h, bool pow2, double dt, double &gu, double &gb)
 {
     if (b > 0.0) {
-        const double gq = __dsub_rn(qc, qn) / h;
-        const double gp = __dsub_rn(pc, pn) / h;
+        const double gq = div_h(__dsub_rn(qc, qn), h, inv_h, pow2);
+        const double gp = div_h(__dsub_rn(pc, pn), h, inv_h, pow2);
         gu = __dsub_rn(w, gq);
         gb = __dmul_rn(__dmul_rn(dt, gp), __dsub_rn(gq, w));
     } else {
@@ -567,7 +585,8 @@ __device__ __forceinline__ void adj_face(double b, double pc, double pn, double 
     }
 }
 
-__global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double dt, const double *__restrict__ bx,
+__global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double inv_h, int pow2, double dt,
+                                const double *__restrict__ bx,
                                 const double *__restrict__ by, const double *__restrict__ bz,
                                 const double *__restrict__ p, const double *__restrict__ q,
                                 const double *__restrict__ wx, const double *__restrict__ wy,
@@ -580,13 +599,13 @@ __global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double dt, con
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     const double pc = p[c], qc = q[c];
     double gu, gb;
-    adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, dt, gu, gb);
+    adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, inv_h, pow2, dt, gu, gb);
     gux[c] = gu;
     if (gbx) gbx[c] = gb;
-    adj_face(by[c], pc, j > 0 ? p[c - nx] : 0.0, qc, j > 0 ? q[c - nx] : 0.0, wy[c], h, dt, gu, gb);
+    adj_face(by[c], pc, j > 0 ? p[c - nx] : 0.0, qc, j > 0 ? q[c - nx] : 0.0, wy[c], h, inv_h, pow2, dt, gu, gb);
     guy[c] = gu;
     if (gby) gby[c] = gb;
-    adj_face(bz[c], pc, k > 0 ? p[c - sxy] : 0.0, qc, k > 0 ? q[c - sxy] : 0.0, wz[c], h, dt, gu, gb);
+    adj_face(bz[c], pc, k > 0 ? p[c - sxy] : 0.0, qc, k > 0 ? q[c - sxy] : 0.0, wz[c], h, inv_h, pow2, dt, gu, gb);
     guz[c] = gu;
     if (gbz) gbz[c] = gb;
 }
@@ -681,21 +700,22 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
 {
     const double sr = dscal[sr_slot];
     double a = 0.0, c = 0.0;
-    float fa = 0.f, fc = 0.f;
-    int cnt = 0;
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const float rv = r32[idx];
-        fa = fmaf(rv, z[idx], fa);
-        if (zo) fc = fmaf(rv, zo[idx], fc);
-        if (++cnt == 16) {  // flush the FP32 partial sums every 16 elements
-            a += fa;
-            c += fc;
-            fa = fc = 0.f;
-            cnt = 0;
+    const unsigned n4 = n / 4, stride = gridDim.x * blockDim.x;
+    const float4 *r4 = reinterpret_cast<const float4 *>(r32);
+    const float4 *z4 = reinterpret_cast<const float4 *>(z);
+    const float4 *o4 = reinterpret_cast<const float4 *>(zo);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += stride) {
+        const float4 rv = r4[v], zv = z4[v];
+        a += (double)fmaf(rv.w, zv.w, fmaf(rv.z, zv.z, fmaf(rv.y, zv.y, rv.x * zv.x)));
+        if (zo) {
+            const float4 ov = o4[v];
+            c += (double)fmaf(rv.w, ov.w, fmaf(rv.z, ov.z, fmaf(rv.y, ov.y, rv.x * ov.x)));
         }
     }
-    a += fa;
-    c += fc;
+    for (unsigned idx = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        a += (double)(r32[idx] * z[idx]);
+        if (zo) c += (double)(r32[idx] * zo[idx]);
+    }
     a = block_sum<kRedThreads>(a) * sr * dscal[sz_slot];
     c = block_sum<kRedThreads>(c) * (so_slot >= 0 ? sr * dscal[so_slot] : 0.0);
     if (threadIdx.x == 0) {
@@ -711,7 +731,16 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
 {
     const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
     const double beta = first ? 0.0 : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ];
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+    const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
+    double2 *d2 = reinterpret_cast<double2 *>(d);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
+        const double z0 = (double)z[2 * v], z1 = (double)z[2 * v + 1];
+        double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
+        dv.x = fma(beta, dv.x, sz * z0);
+        dv.y = fma(beta, dv.y, sz * z1);
+        d2[v] = dv;
+    }
+    for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride)
         d[idx] = fma(beta, first ? 0.0 : d[idx], sz * (double)z[idx]);
 }
 
@@ -767,7 +796,7 @@ __global__ void k_diag(int nx, int ny, int nz, const double *__restrict__ bx, co
 }
 
 // alpha = <r,z>/<d,Ad>; p += alpha d; r -= alpha q; ||r||^2; optionally r32 = r / scale with
-// scale = RMS of the previous residual (written to scale_slot)
+// scale = RMS of the previous residual (written to scale_slot).  Two elements per iteration.
 __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
                              double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
                              double *__restrict__ dscal, int scale_slot, double *__restrict__ partials)
@@ -782,7 +811,26 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
     }
     const float inv_scale32 = (float)inv_scale;
     double rr = 0.0;
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
+    const double2 *d2 = reinterpret_cast<const double2 *>(d);
+    const double2 *q2 = reinterpret_cast<const double2 *>(q);
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+    double2 *rv2 = reinterpret_cast<double2 *>(r);
+    float2 *r32v = reinterpret_cast<float2 *>(r32);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
+        const double2 dv = d2[v], qv = q2[v];
+        double2 pv = p2[v], rv = rv2[v];
+        pv.x = fma(alpha, dv.x, pv.x);
+        pv.y = fma(alpha, dv.y, pv.y);
+        rv.x = fma(-alpha, qv.x, rv.x);
+        rv.y = fma(-alpha, qv.y, rv.y);
+        p2[v] = pv;
+        rv2[v] = rv;
+        if (r32) r32v[v] = make_float2((float)rv.x * inv_scale32, (float)rv.y * inv_scale32);
+        rr = fma(rv.x, rv.x, rr);
+        rr = fma(rv.y, rv.y, rr);
+    }
+    for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         p[idx] = fma(alpha, d[idx], p[idx]);
         const double rv = fma(-alpha, q[idx], r[idx]);
         r[idx] = rv;
@@ -849,16 +897,20 @@ cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_
 }
 
 template <typename T>
-cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s)
+cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
+                          int z0, int z1)
 {
+    if (z1 < 0) z1 = d.nz;
+    if (z1 <= z0) return cudaSuccess;
     note_launch();
-    k_smooth<T><<<row_grid((d.nx + 1) / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour);
+    k_smooth<T><<<row_grid((d.nx + 1) / 2, d.ny, z1 - z0), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour,
+                                                                                z0);
     return cudaGetLastError();
 }
 template cudaError_t launch_smooth<double>(Dims, double, const LevelArrays<double> &, const double *, double *, int,
-                                           cudaStream_t);
+                                           cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> &, const float *, float *, int,
-                                          cudaStream_t);
+                                          cudaStream_t, int, int);
 
 template <typename T>
 cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
@@ -1001,8 +1053,10 @@ cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const 
                            double *uy, double *uz, cudaStream_t s)
 {
     note_launch();
-    k_correct<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, dt, h, bx, by, bz, p, ux0, uy0, uz0,
-                                                                  ux, uy, uz);
+    int ex;
+    const bool pow2 = std::frexp(h, &ex) == 0.5;
+    k_correct<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, dt, h, 1.0 / h, pow2, bx, by, bz, p,
+                                                                  ux0, uy0, uz0, ux, uy, uz);
     return cudaGetLastError();
 }
 
@@ -1020,8 +1074,11 @@ cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, 
                                  double *gbz, cudaStream_t s)
 {
     note_launch();
-    k_adjoint_faces<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h, dt, bx, by, bz, p, q, wx,
-                                                                        wy, wz, gux, guy, guz, gbx, gby, gbz);
+    int ex;
+    const bool pow2 = std::frexp(h, &ex) == 0.5;
+    k_adjoint_faces<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h, 1.0 / h, pow2, dt, bx, by,
+                                                                        bz, p, q, wx, wy, wz, gux, guy, guz, gbx, gby,
+                                                                        gbz);
     return cudaGetLastError();
 }
 
