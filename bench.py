@@ -48,6 +48,9 @@ B_RESID64 = 48.0      # FP64 residual + norm (p, b, bx, by, bz read; dinv mask)
 B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
 SWEEP_KERNEL = {0: "k_smooth<float> x2 colour passes", 1: "k_smooth<float> x2 colour passes",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
+# DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth<float> colour
+# passes) from an ncu capture of this workload (profiles/k_smooth_float_256_colour_pass.md)
+SWEEP_TRAFFIC_256 = 335.560704e6 + 52.387840e6 + 335.560448e6 + 52.075264e6
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))
 
@@ -380,7 +383,8 @@ def run_ours(args):
         "cycles_fwd_bwd": list(cyc_mixed),
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": SWEEP_KERNEL[args.smoother] + " (finest grid, FP32, one red-black sweep)",
+                     "traffic": SWEEP_TRAFFIC_256 if (args.n == 256 and args.smoother in (0, 1)) else None,
+                     "traffic_unit": "bytes per sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum)", "kernel": SWEEP_KERNEL[args.smoother] + " (finest grid, FP32, one red-black sweep)",
                      "algorithmic_bytes_per_sweep": B_SWEEP32 * n, "sweep_ms": sweep_ms,
                      "peak_source": f"{peak_src} hbm_gbs (burst copy)"},
         "vcycle_hbm_gbs": {"mixed": mixed_vcycle_gbs, "fp64": fp64["vcycle_hbm_gbs"] if fp64 else None},
