@@ -61,7 +61,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=256, help="grid size per axis (256 = the benchmark workload)")
+    ap.add_argument("--n", type=int, default=256, help="grid size per axis of the c3 workload (256 = the benchmark)")
+    ap.add_argument("--workload", choices=["c3", "c4", "c5"], default="c3",
+                    help="c3: 256^3 ellipsoid case (the metric's); c4: 512x256x128 tank with 200 bubbles; "
+                         "c5: 1024x512x256 plunging wave + hull")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -74,10 +77,26 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_name(n):
+def workload_name(n, workload="c3"):
+    step = (f"step = face coeffs + hierarchy + projection + adjoint projection + phi chain rule "
+            f"(2 solves to rel. resid {TOL:g})")
+    if workload == "c4":
+        return ("512x256x128 tow-tank box [0,4]x[0,2]x[0,1] (16.8M cells), flat surface + 0.01 S, 200 seeded air "
+                "bubbles r~U[2h,6h], rho ratio 1e-3, u*~N(0,0.1), w~N(0,1) seed 4; " + step)
+    if workload == "c5":
+        return ("1024x512x256 box (134M cells), plunging overturned interface (cubic-displaced tanh), box hull "
+                "0.4x0.05x0.04 with rounded bow, rho ratio 1e-3, u*/w FP32 seed 5 promoted to FP64; " + step)
     return (f"{n}^3 unit cube, 4-mode free surface (amp 0.08, seed 2) + piercing ellipsoid (0.3,0.06,0.05), "
-            f"rho_air/rho_water 1e-3, u*~N(0,0.1) seed 3, w~N(0,1); step = face coeffs + hierarchy + projection "
-            f"+ adjoint projection + phi chain rule (2 solves to rel. resid {TOL:g})")
+            f"rho_air/rho_water 1e-3, u*~N(0,0.1) seed 3, w~N(0,1); " + step)
+
+
+def make_case(args):
+    from paper_1410_2240_gb300 import synth
+    if args.workload == "c4":
+        return synth.case_c4()
+    if args.workload == "c5":
+        return synth.case_c5()
+    return synth.case_c3(args.n)
 
 
 # ---------------------------------------------------------------------------
@@ -188,7 +207,7 @@ class Step:
         self.case = case
         dev = lambda a, dt=torch.float64: torch.from_numpy(a).to(device="cuda", dtype=dt)
         self.phi = dev(case.phi)
-        self.solid = dev(case.solid, torch.uint8)
+        self.solid = dev(case.solid, torch.uint8) if case.solid is not None else None
         self.u_star = tuple(dev(x) for x in case.u_star)
         self.w = tuple(dev(x) for x in case.w)
         self.beta = mgproj.face_coeffs(self.phi, case.h, self.solid, rho_air=case.lam)
@@ -246,7 +265,7 @@ def e2e_leg(case, K, W):
     from paper_1410_2240_gb300.autograd import project
     pin = lambda a, dt=torch.float64: torch.from_numpy(a).to(dtype=dt).pin_memory()
     h_phi = pin(case.phi)
-    h_solid = pin(case.solid, torch.uint8)
+    h_solid = pin(case.solid, torch.uint8) if case.solid is not None else None
     h_u = tuple(pin(x) for x in case.u_star)
     h_w = tuple(pin(x) for x in case.w)
     o_u = tuple(torch.empty_like(x).pin_memory() for x in h_u)
@@ -255,7 +274,7 @@ def e2e_leg(case, K, W):
 
     def one():
         phi = h_phi.to("cuda", non_blocking=True).requires_grad_(True)
-        solid = h_solid.to("cuda", non_blocking=True)
+        solid = h_solid.to("cuda", non_blocking=True) if h_solid is not None else None
         u = tuple(x.to("cuda", non_blocking=True).requires_grad_(True) for x in h_u)
         w = tuple(x.to("cuda", non_blocking=True) for x in h_w)
         (ux, uy, uz), p = project(u, phi, case.h, solid=solid, rho_air=case.lam, tol=TOL, precision="mixed")
@@ -275,7 +294,7 @@ def e2e_leg(case, K, W):
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     n = case.ncell
-    h2d = (7 * 8 + 1) * n
+    h2d = (7 * 8 + (1 if h_solid is not None else 0)) * n
     d2h = 7 * 8 * n
     return {"value": 2 * K / sec, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": 1e3 * sec / K, "api": "paper_1410_2240_gb300.autograd.project (mixed) + backward"}
@@ -300,6 +319,21 @@ def cpu_baseline(case):
                       f"{TOL:g} (face coeffs + rhs + hierarchy {t1 - t0:.1f} s, {abs(cyc)} V-cycles {t2 - t1:.1f} s)"}, p_ref
 
 
+# algorithmic bytes per finest cell and call of each event-timed group of a mixed step
+GROUP_BYTES = {"smooth": B_SWEEP32, "restrict": 20.5, "prolong": 8.5, "resid64": 48.0, "cg_apply": 48.0,
+               "cg_vectors": 32.0}
+
+
+def kernel_gbs(kernel_ms, n):
+    """Algorithmic GB/s of the finest-grid kernel groups (bytes per cell x cells x calls / time)."""
+    out = {}
+    for g, bpc in GROUP_BYTES.items():
+        v = kernel_ms.get(g)
+        if v and v["launches"] and v["ms"] > 0:
+            out[g] = bpc * n * v["launches"] / (v["ms"] / 1e3) / 1e9
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -311,7 +345,7 @@ def run_ours(args):
         __graft_entry__.build()
     barrier(world)
     from paper_1410_2240_gb300 import mgproj
-    case = synth.case_c3(args.n)
+    case = make_case(args)
     n = case.ncell
     K, W = args.steps, max(args.warmup, 3)
 
@@ -376,14 +410,15 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.n), "cells": n, "precision": "mixed (FP32 V-cycles, FP64 "
+        "config": {"workload": workload_name(args.n, args.workload), "cells": n, "precision": "mixed (FP32 V-cycles, FP64 "
                    "residual/accumulation/coarsest solve)", "tol": TOL, "solves_per_step": 2,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: each FP64 fine array is %.0f MB, ~1.5 GB touched per step" % (8 * n / 1e6)},
         "cycles_fwd_bwd": list(cyc_mixed),
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": SWEEP_TRAFFIC_256 if (args.n == 256 and args.smoother in (0, 1)) else None,
+                     "traffic": (SWEEP_TRAFFIC_256 if (args.workload == "c3" and args.n == 256 and args.smoother in (0, 1))
+                                 else None),
                      "traffic_unit": "bytes per sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum)", "kernel": SWEEP_KERNEL[args.smoother] + " (finest grid, FP32, one red-black sweep)",
                      "algorithmic_bytes_per_sweep": B_SWEEP32 * n, "sweep_ms": sweep_ms,
                      "peak_source": f"{peak_src} hbm_gbs (burst copy)"},
@@ -392,9 +427,11 @@ def run_ours(args):
         "kernel_ms": {g: {"launches": c, "ms": t} for g, (c, t) in prof.items()},
         "clocks": clk,
     }
+    out["projections_per_s"] = value / 2.0  # one projection step = forward + adjoint
+    out["kernel_gbs"] = kernel_gbs(out["kernel_ms"], n)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_leg(case, max(2, K // 4), 2)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "c5":
         cb, p_or = cpu_baseline(case)
         out["cpu_baseline"] = cb
         rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -6,6 +6,7 @@
 // factorisation per connected component of a rank-one-shifted operator).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -133,6 +134,21 @@ bool grid_ok(const mg_grid *g)
 // from one Cholesky factorisation of the shifted matrix -A + (a/m) 1 1^T (see
 // below); isolated cells get zero rows and columns.
 // ---------------------------------------------------------------------------
+// dot product with four partial sums (lets the compiler keep several FMA chains in flight)
+inline double dot4(const double *a, const double *b, int n)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int q = 0;
+    for (; q + 4 <= n; q += 4) {
+        s0 += a[q] * b[q];
+        s1 += a[q + 1] * b[q + 1];
+        s2 += a[q + 2] * b[q + 2];
+        s3 += a[q + 3] * b[q + 3];
+    }
+    for (; q < n; q++) s0 += a[q] * b[q];
+    return (s0 + s1) + (s2 + s3);
+}
+
 int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &bx, const std::vector<double> &by,
                    const std::vector<double> &bz, std::vector<double> &M)
 {
@@ -189,31 +205,55 @@ int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &
         const double a = tr / m, shift = a / m;
         for (int x = 0; x < m; x++)
             for (int y = 0; y < m; y++) S[(size_t)x * m + y] = -A[(size_t)mem[x] * n + mem[y]] + shift;
-        // Cholesky S = L L^T (lower triangle, in place)
-        for (int j = 0; j < m; j++) {
-            double d = S[(size_t)j * m + j];
-            for (int q = 0; q < j; q++) d -= S[(size_t)j * m + q] * S[(size_t)j * m + q];
-            if (!(d > 0.0)) return fail(MG_ERR_ARG, "coarsest-grid operator is not semi-definite");
-            const double ljj = std::sqrt(d);
-            S[(size_t)j * m + j] = ljj;
-            for (int i = j + 1; i < m; i++) {
-                double v = S[(size_t)i * m + j];
-                for (int q = 0; q < j; q++) v -= S[(size_t)i * m + q] * S[(size_t)j * m + q];
-                S[(size_t)i * m + j] = v / ljj;
+        // Cholesky S = C C^T (C lower, in place), left-looking by 32-column panels: the panel's
+        // diagonal block serially, then its rows below in parallel (one parallel region per panel)
+        const int PB = 32;
+        int bad = 0;
+        for (int j0 = 0; j0 < m && !bad; j0 += PB) {
+            const int j1 = std::min(j0 + PB, m);
+            for (int j = j0; j < j1 && !bad; j++) {
+                double *rj = &S[(size_t)j * m];
+                const double dd = rj[j] - dot4(rj, rj, j);
+                if (!(dd > 0.0)) {
+                    bad = 1;
+                    break;
+                }
+                rj[j] = std::sqrt(dd);
+                for (int i = j + 1; i < j1; i++) {
+                    double *ri = &S[(size_t)i * m];
+                    ri[j] = (ri[j] - dot4(ri, rj, j)) / rj[j];
+                }
+            }
+            if (bad) break;
+#pragma omp parallel for schedule(static) if (m - j1 > 64)
+            for (int i = j1; i < m; i++) {
+                double *ri = &S[(size_t)i * m];
+                for (int j = j0; j < j1; j++) {
+                    const double *rj = &S[(size_t)j * m];
+                    ri[j] = (ri[j] - dot4(ri, rj, j)) / rj[j];
+                }
             }
         }
-        // X = S^-1 column by column (forward then backward substitution)
-        std::vector<double> X((size_t)m * m), y(m);
-        for (int col = 0; col < m; col++) {
-            for (int i = 0; i < m; i++) {
-                double v = (i == col) ? 1.0 : 0.0;
-                for (int q = 0; q < i; q++) v -= S[(size_t)i * m + q] * y[q];
-                y[i] = v / S[(size_t)i * m + i];
+        if (bad) return fail(MG_ERR_ARG, "coarsest-grid operator is not semi-definite");
+        // W = C^-1 (lower), stored by columns as rows of WT (upper): column j solves C w = e_j
+        std::vector<double> WT((size_t)m * m, 0.0);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int j = 0; j < m; j++) {
+            double *w = &WT[(size_t)j * m];
+            for (int i = j; i < m; i++) {
+                const double *ci = &S[(size_t)i * m];
+                w[i] = ((i == j ? 1.0 : 0.0) - dot4(ci + j, w + j, i - j)) / ci[i];
             }
-            for (int i = m - 1; i >= 0; i--) {
-                double v = y[i];
-                for (int q = i + 1; q < m; q++) v -= S[(size_t)q * m + i] * X[(size_t)q * m + col];
-                X[(size_t)i * m + col] = v / S[(size_t)i * m + i];
+        }
+        // X = S^-1 = W^T W: X[x][y] = sum_{q >= max(x,y)} WT[x][q] WT[y][q]
+        std::vector<double> X((size_t)m * m);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int x = 0; x < m; x++) {
+            const double *wx = &WT[(size_t)x * m];
+            for (int y = 0; y <= x; y++) {
+                const double v = dot4(wx + x, &WT[(size_t)y * m] + x, m - x);
+                X[(size_t)x * m + y] = v;
+                X[(size_t)y * m + x] = v;
             }
         }
         // A^+ = -L^+ = -(X - J/(a m))

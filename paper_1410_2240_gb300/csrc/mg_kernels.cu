@@ -366,17 +366,20 @@ k_rb_sweep(int nx, int ny, int nz, int zc, T h2, LevelArrays<T> L, const T *__re
 }
 
 // Exact coarsest-grid solve e = M b with the dense minimum-norm inverse M (FP64 always).
+// One warp per row (coalesced row reads, shuffle reduction); b staged in shared memory.
 template <typename T>
 __global__ void k_coarse_solve(int n, const double *__restrict__ M, const T *__restrict__ b, T *__restrict__ e)
 {
     extern __shared__ double sb[];
     for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)b[i];
     __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int r = blockIdx.x * warps + warp; r < n; r += gridDim.x * warps) {
         const double *row = M + (size_t)r * n;
         double s = 0.0;
-        for (int q = 0; q < n; q++) s += row[q] * sb[q];
-        e[r] = (T)s;
+        for (int q = lane; q < n; q += 32) s = fma(row[q], sb[q], s);
+        s = warp_sum(s);
+        if (lane == 0) e[r] = (T)s;
     }
 }
 
@@ -961,8 +964,10 @@ template cudaError_t launch_rb_sweep<float>(Dims, float, const LevelArrays<float
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s)
 {
+    const int rows_per_cta = 8;  // one warp per row
     note_launch();
-    k_coarse_solve<T><<<1, 256, (size_t)n * sizeof(double), s>>>(n, M, b, e);
+    k_coarse_solve<T><<<(n + rows_per_cta - 1) / rows_per_cta, 32 * rows_per_cta, (size_t)n * sizeof(double), s>>>(n, M, b,
+                                                                                                                e);
     return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<double>(int, const double *, const double *, double *, cudaStream_t);
