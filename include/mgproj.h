@@ -24,7 +24,10 @@
  * cells, area 0, static body).
  *
  * Pointers: every array argument is a DEVICE pointer (cudaMalloc'd or from a
- * caching allocator) unless marked "host".  The caller owns every buffer it
+ * caching allocator) unless marked "host", and starts on a 16-byte boundary
+ * (every cudaMalloc and PyTorch allocation does; a view offset by an odd
+ * number of doubles does not): the kernels move aligned pairs, and a call
+ * given an unaligned array returns MG_ERR_ARG.  The caller owns every buffer it
  * passes; the library never frees or retains them beyond the call, except as
  * stated for mg_setup.  All work is ordered on the CUDA stream given to
  * mg_setup (or to the stand-alone calls); pass NULL for the legacy default

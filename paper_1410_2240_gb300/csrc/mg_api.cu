@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -121,6 +122,14 @@ struct mg_ctx {
 };
 
 namespace {
+
+// every device array starts on a 16-byte boundary (the kernels move aligned pairs); null passes
+bool aligned16(std::initializer_list<const void *> ptrs)
+{
+    for (const void *q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 16 != 0) return false;
+    return true;
+}
 
 bool grid_ok(const mg_grid *g)
 {
@@ -549,10 +558,11 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
         if (l > 0)
             CK(mg::launch_restrict_coeffs(c->dims[l - 1], c->L64[l - 1].bx, c->L64[l - 1].by, c->L64[l - 1].bz,
                                           c->L64[l].bx, c->L64[l].by, c->L64[l].bz, s));
-        CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv, s));
+        // the finest level's diagonal (CG operator) comes out of the same pass
+        CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv,
+                                       l == 0 ? c->kdiag : nullptr, s));
     }
     CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
-    if (c->kdiag) CK(mg::launch_diag(c->dims[0], c->L64[0].bx, c->L64[0].by, c->L64[0].bz, c->kdiag, s));
     // coarsest operator to the host
     const int nc = c->ncoarse;
     std::vector<double> cb[3];
@@ -739,6 +749,8 @@ int mg_face_coeffs(const mg_grid *g, const double *phi, const uint8_t *solid_mas
     if (!phi || !beta_out || !beta_out[0] || !beta_out[1] || !beta_out[2])
         return fail(MG_ERR_ARG, "mg_face_coeffs: null pointer");
     if (!(rho_air > 0.0) || !(rho_water > 0.0)) return fail(MG_ERR_ARG, "mg_face_coeffs: densities must be > 0");
+    if (!aligned16({phi, solid_mask, beta_out[0], beta_out[1], beta_out[2]}))
+        return fail(MG_ERR_ARG, "mg_face_coeffs: arrays must be 16-byte aligned");
     const Dims d{g->nx, g->ny, g->nz};
     CK(mg::launch_face_coeffs(d, phi, solid_mask, rho_air, rho_water - rho_air, beta_out[0], beta_out[1], beta_out[2],
                               (cudaStream_t)stream));
@@ -756,6 +768,8 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_setup: bad grid");
     if (!face_coeffs || !face_coeffs[0] || !face_coeffs[1] || !face_coeffs[2])
         return fail(MG_ERR_ARG, "mg_setup: null face coefficient pointer");
+    if (!aligned16({face_coeffs[0], face_coeffs[1], face_coeffs[2], solid_mask}))
+        return fail(MG_ERR_ARG, "mg_setup: arrays must be 16-byte aligned");
     if (bc)
         for (int w = 0; w < 6; w++)
             if (bc->wall[w] != MG_BC_NEUMANN) return fail(MG_ERR_ARG, "mg_setup: only Neumann walls are supported");
@@ -855,6 +869,8 @@ int mg_update(mg_ctx *c, const double *const face_coeffs[3])
     g_err.clear();
     if (!c || !face_coeffs || !face_coeffs[0] || !face_coeffs[1] || !face_coeffs[2])
         return fail(MG_ERR_ARG, "mg_update: null argument");
+    if (!aligned16({face_coeffs[0], face_coeffs[1], face_coeffs[2]}))
+        return fail(MG_ERR_ARG, "mg_update: arrays must be 16-byte aligned");
     const auto t0 = std::chrono::steady_clock::now();
     {
         ProfScope ps(c, MG_PROF_UPDATE, true);
@@ -869,6 +885,7 @@ int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stat
     g_err.clear();
     if (!c || !rhs || !p) return fail(MG_ERR_ARG, "mg_solve: null argument");
     if (rhs == p) return fail(MG_ERR_ARG, "mg_solve: rhs and p must not alias");
+    if (!aligned16({rhs, p})) return fail(MG_ERR_ARG, "mg_solve: arrays must be 16-byte aligned");
     if (!(tol > 0.0)) return fail(MG_ERR_ARG, "mg_solve: tol must be > 0");
     return c->o.krylov ? pcg_impl(c, rhs, p, tol, stats) : solve_impl(c, rhs, p, tol, stats);
 }
@@ -877,6 +894,7 @@ int mg_vcycle(mg_ctx *c, const double *rhs, double *p)
 {
     g_err.clear();
     if (!c || !rhs || !p) return fail(MG_ERR_ARG, "mg_vcycle: null argument");
+    if (!aligned16({rhs, p})) return fail(MG_ERR_ARG, "mg_vcycle: arrays must be 16-byte aligned");
     return vcycle<double>(c, c->L64, 0, rhs, p);
 }
 
@@ -885,6 +903,7 @@ int mg_divergence(mg_ctx *c, const double *const u[3], double dt, double *rhs)
     g_err.clear();
     if (!c || !u || !u[0] || !u[1] || !u[2] || !rhs) return fail(MG_ERR_ARG, "mg_divergence: null argument");
     if (!(dt > 0.0)) return fail(MG_ERR_ARG, "mg_divergence: dt must be > 0");
+    if (!aligned16({u[0], u[1], u[2], rhs})) return fail(MG_ERR_ARG, "mg_divergence: arrays must be 16-byte aligned");
     const LevelArrays<double> &L = c->L64[0];
     CK(mg::launch_divergence(c->dims[0], 1.0 / (dt * c->g.h), L.bx, L.by, L.bz, u[0], u[1], u[2], rhs, c->s));
     return MG_OK;
@@ -896,6 +915,8 @@ int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double
     if (!c || !u_star || !u || !p) return fail(MG_ERR_ARG, "mg_correct: null argument");
     for (int a = 0; a < 3; a++)
         if (!u_star[a] || !u[a]) return fail(MG_ERR_ARG, "mg_correct: null face array");
+    if (!aligned16({u_star[0], u_star[1], u_star[2], u[0], u[1], u[2], p}))
+        return fail(MG_ERR_ARG, "mg_correct: arrays must be 16-byte aligned");
     const LevelArrays<double> &L = c->L64[0];
     CK(mg::launch_correct(c->dims[0], dt, c->g.h, L.bx, L.by, L.bz, p, u_star[0], u_star[1], u_star[2], u[0], u[1],
                           u[2], c->s));
@@ -910,6 +931,8 @@ int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], dou
     for (int a = 0; a < 3; a++)
         if (!u_star[a] || !u[a]) return fail(MG_ERR_ARG, "mg_project: null face array");
     if (!(dt > 0.0) || !(tol > 0.0)) return fail(MG_ERR_ARG, "mg_project: dt and tol must be > 0");
+    if (!aligned16({u_star[0], u_star[1], u_star[2], u[0], u[1], u[2], p}))
+        return fail(MG_ERR_ARG, "mg_project: arrays must be 16-byte aligned");
     CKS(ensure(c, &c->rhs_tmp, c->dims[0].n()));
     CKS(mg_divergence(c, u_star, dt, c->rhs_tmp));
     const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, p, tol, stats) : solve_impl(c, c->rhs_tmp, p, tol, stats);
@@ -931,6 +954,9 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
             if ((const double *)grad_u[a] == w[b]) return fail(MG_ERR_ARG, "mg_project_adjoint: grad_u aliases w");
     }
     if (!(dt > 0.0) || !(tol > 0.0)) return fail(MG_ERR_ARG, "mg_project_adjoint: dt and tol must be > 0");
+    if (!aligned16({w[0], w[1], w[2], grad_u[0], grad_u[1], grad_u[2], p, q_out}) ||
+        (grad_beta && !aligned16({grad_beta[0], grad_beta[1], grad_beta[2]})))
+        return fail(MG_ERR_ARG, "mg_project_adjoint: arrays must be 16-byte aligned");
     const size_t n = c->dims[0].n();
     CKS(ensure(c, &c->rhs_tmp, n));
     double *q = q_out;
@@ -964,6 +990,8 @@ int mg_phi_grad(const mg_grid *g, const double *const beta[3], const double *con
     if (!beta || !grad_beta || !grad_phi) return fail(MG_ERR_ARG, "mg_phi_grad: null argument");
     for (int a = 0; a < 3; a++)
         if (!beta[a] || !grad_beta[a]) return fail(MG_ERR_ARG, "mg_phi_grad: null face array");
+    if (!aligned16({beta[0], beta[1], beta[2], grad_beta[0], grad_beta[1], grad_beta[2], grad_phi}))
+        return fail(MG_ERR_ARG, "mg_phi_grad: arrays must be 16-byte aligned");
     const Dims d{g->nx, g->ny, g->nz};
     CK(mg::launch_phi_grad(d, -0.5 * (rho_water - rho_air), beta[0], beta[1], beta[2], grad_beta[0], grad_beta[1],
                            grad_beta[2], grad_phi, (cudaStream_t)stream));
@@ -986,6 +1014,7 @@ int mg_level_array(mg_ctx *c, int level, int which, double *out)
     g_err.clear();
     if (!c || !out || level < 0 || level >= c->nlev || which < 0 || which > 3)
         return fail(MG_ERR_ARG, "mg_level_array: bad argument");
+    if (!aligned16({out})) return fail(MG_ERR_ARG, "mg_level_array: out must be 16-byte aligned");
     const LevelArrays<double> &L = c->L64[level];
     const double *src = which == 0 ? L.bx : which == 1 ? L.by : which == 2 ? L.bz : L.dinv;
     CK(cudaMemcpyAsync(out, src, c->dims[level].n() * sizeof(double), cudaMemcpyDeviceToDevice, c->s));

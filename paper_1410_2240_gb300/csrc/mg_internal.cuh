@@ -59,7 +59,7 @@ void set_last_error(const char *msg);
 cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
                                double *bx, double *by, double *bz, cudaStream_t s);
 template <typename T>
-cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s);
+cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, T *diag, cudaStream_t s);
 cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s);
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
@@ -109,7 +109,6 @@ template <typename Z>
 cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s);
 cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
                              double *q, double *partials, double *dscal, cudaStream_t s);
-cudaError_t launch_diag(Dims d, const double *bx, const double *by, const double *bz, double *diag, cudaStream_t s);
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
                               double *partials, double *dscal, int scale_slot, cudaStream_t s);
 

@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 
 #include "mg_internal.cuh"
 
@@ -80,43 +81,126 @@ __device__ __forceinline__ void cell_of(unsigned idx, int nx, int ny, int &i, in
 // rho = rho_a + drho*phi, beta = 2/(rho_L + rho_R) on open faces.  Rounded as
 // separate IEEE operations (no contraction) so that it is reproducible.
 // ---------------------------------------------------------------------------
+// Set-up kernels walk kRun cells up a z-column per thread.  A quotient x / den depends on den
+// alone, so each keeps its last divisor and quotient and divides again only when the divisor's
+// bits change: in a uniform region (pure air, pure water, constant coefficients) that is once
+// per run instead of once per cell, and the results are those of dividing every time.
+constexpr int kRun = 16;
+
+__device__ __forceinline__ bool same_bits(double a, double b)
+{
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_int(a) == __float_as_int(b); }
+
+// a / b as a call: the compiler cannot run a call speculatively, so a memo that skips the
+// division really skips it (an inlined division is if-converted and runs on every lane, and on
+// this part's narrow FP64 unit it costs as much as the rest of the pass)
+template <typename T>
+__device__ __noinline__ T div_call(T a, T b)
+{
+    return a / b;
+}
+
+// x > 0 and x == 0 decided on the integer pipe (an FP64 comparison occupies the FP64 unit, the
+// limiting resource of the FP64 passes).  pos_bits(x) equals x > 0 for every x but a NaN with a
+// clear sign bit; the coefficients, inverse diagonals and live masks it is applied to are never
+// NaN for finite input.  zero_bits(x) equals x == 0 for every x.
+__device__ __forceinline__ bool pos_bits(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool zero_bits(float x) { return (__float_as_int(x) << 1) == 0; }
+
+inline dim3 run_grid(int nx, int ny, int nz)
+{
+    return dim3((unsigned)((nx + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)((nz + kRun - 1) / kRun));
+}
+
+// beta_f = 2 / (rho_L + rho_R), rho = rho_a + drho phi (each operation rounded separately); 0 on
+// walls and on faces touching a solid cell.  The density of the cell below is carried up the run.
 __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__ phi,
                               const uint8_t *__restrict__ solid, double rho_a, double drho, double *__restrict__ bx,
                               double *__restrict__ by, double *__restrict__ bz)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
+    const int k0 = blockIdx.z * kRun, k1 = min(k0 + kRun, nz);
     const size_t sxy = (size_t)nx * ny;
-    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
-    const bool sc = solid && solid[c];
-    const double rc = __dadd_rn(rho_a, __dmul_rn(drho, phi[c]));
-    double v = 0.0;
-    if (i > 0 && !sc && !(solid && solid[c - 1])) v = 2.0 / __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - 1])), rc);
-    bx[c] = v;
-    v = 0.0;
-    if (j > 0 && !sc && !(solid && solid[c - nx])) v = 2.0 / __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - nx])), rc);
-    by[c] = v;
-    v = 0.0;
-    if (k > 0 && !sc && !(solid && solid[c - sxy])) v = 2.0 / __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - sxy])), rc);
-    bz[c] = v;
+    // divisor memo per face direction (2 / 1 = 2 exactly)
+    double dx_last = 1.0, qx_last = 2.0, dy_last = 1.0, qy_last = 2.0, dz_last = 1.0, qz_last = 2.0;
+    size_t c = (size_t)k0 * sxy + (size_t)j * nx + i;
+    bool s_below = k0 > 0 && solid && solid[c - sxy];
+    double r_below = k0 > 0 ? __dadd_rn(rho_a, __dmul_rn(drho, phi[c - sxy])) : 0.0;
+    for (int k = k0; k < k1; k++, c += sxy) {
+        const bool sc = solid && solid[c];
+        const double rc = __dadd_rn(rho_a, __dmul_rn(drho, phi[c]));
+        double v = 0.0;
+        if (i > 0 && !sc && !(solid && solid[c - 1])) {
+            const double den = __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - 1])), rc);
+            if (!same_bits(den, dx_last)) {
+                dx_last = den;
+                qx_last = div_call(2.0, den);
+            }
+            v = qx_last;
+        }
+        bx[c] = v;
+        v = 0.0;
+        if (j > 0 && !sc && !(solid && solid[c - nx])) {
+            const double den = __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - nx])), rc);
+            if (!same_bits(den, dy_last)) {
+                dy_last = den;
+                qy_last = div_call(2.0, den);
+            }
+            v = qy_last;
+        }
+        by[c] = v;
+        v = 0.0;
+        if (k > 0 && !sc && !s_below) {
+            const double den = __dadd_rn(r_below, rc);
+            if (!same_bits(den, dz_last)) {
+                dz_last = den;
+                qz_last = div_call(2.0, den);
+            }
+            v = qz_last;
+        }
+        bz[c] = v;
+        s_below = sc;
+        r_below = rc;
+    }
 }
 
-// dinv = 1 / (sum of the six face coefficients), summed x-, x+, y-, y+, z-, z+; 0 if none is open.
+// dinv = 1 / (sum of the six face coefficients), summed x-, x+, y-, y+, z-, z+; 0 if none is
+// open.  diag (optional) = the sum itself.  kRun cells per thread with the divisor memo above.
 template <typename T>
 __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, const T *__restrict__ by,
-                           const T *__restrict__ bz, T *__restrict__ dinv)
+                           const T *__restrict__ bz, T *__restrict__ dinv, T *__restrict__ diag)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
+    const int k0 = blockIdx.z * kRun, k1 = min(k0 + kRun, nz);
     const size_t sxy = (size_t)nx * ny;
-    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
-    T s = bx[c];
-    s += (i < nx - 1) ? bx[c + 1] : T(0);
-    s += by[c];
-    s += (j < ny - 1) ? by[c + nx] : T(0);
-    s += bz[c];
-    s += (k < nz - 1) ? bz[c + sxy] : T(0);
-    dinv[c] = (s > T(0)) ? T(1) / s : T(0);
+    T s_last = T(1), q_last = T(1);
+    size_t c = (size_t)k0 * sxy + (size_t)j * nx + i;
+    T bz_lo = bz[c];
+    for (int k = k0; k < k1; k++, c += sxy) {
+        const T bz_hi = (k < nz - 1) ? bz[c + sxy] : T(0);
+        T s = bx[c];
+        s += (i < nx - 1) ? bx[c + 1] : T(0);
+        s += by[c];
+        s += (j < ny - 1) ? by[c + nx] : T(0);
+        s += bz_lo;
+        s += bz_hi;
+        bz_lo = bz_hi;
+        if (diag) diag[c] = s;
+        T q = T(0);
+        if (s > T(0)) {
+            if (!same_bits(s, s_last)) {
+                s_last = s;
+                q_last = div_call(T(1), s);
+            }
+            q = q_last;
+        }
+        dinv[c] = q;
+    }
 }
 
 // Coarse face coefficient = mean of the 2x2 coplanar fine faces it covers.
@@ -184,26 +268,6 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
 // 3/4 on the parent and 1/4 on the next coarse cell toward the fine cell, per axis, that index
 // clamped to the domain; the 8 weighted values are accumulated with fused multiply-adds in the
 // order K, J, I.
-template <typename T>
-__device__ __forceinline__ T prolong_at(int i, int j, int k, int NX, int NY, int NZ, const T *__restrict__ ec)
-{
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int I1 = min(max((i & 1) ? I0 + 1 : I0 - 1, 0), NX - 1);
-    const int J1 = min(max((j & 1) ? J0 + 1 : J0 - 1, 0), NY - 1);
-    const int K1 = min(max((k & 1) ? K0 + 1 : K0 - 1, 0), NZ - 1);
-    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
-    const T w[2] = {T(0.75), T(0.25)};
-    T s = T(0);
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int bb = 0; bb < 2; bb++)
-#pragma unroll
-            for (int d = 0; d < 2; d++)
-                s = fma(w[a] * w[bb] * w[d], ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]], s);
-    return s;
-}
-
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
 template <typename T>
 __device__ __forceinline__ T residual_at(int i, int j, int k, size_t c, int nx, int ny, int nz, size_t sxy, T ih2,
@@ -219,6 +283,25 @@ __device__ __forceinline__ T residual_at(int i, int j, int k, size_t c, int nx, 
     if (k > 0) s = fma(L.bz[c], p[c - sxy] - pc, s);
     if (k < nz - 1) s = fma(L.bz[c + sxy], p[c + sxy] - pc, s);
     return fma(-s, ih2, b[c]);
+}
+
+// FP64 residual for the solver's convergence checks.  Where p and its in-domain neighbours are
+// all zero (bitwise, either sign) every product beta (0 - 0) is a signed zero, the sum stays +0
+// and residual_at returns b[c] exactly (for finite coefficients): the test runs on the integer
+// pipe and skips the FP64 arithmetic, which dominates this pass on a zero initial guess.
+__device__ __forceinline__ double residual64_at(int i, int j, int k, size_t c, int nx, int ny, int nz, size_t sxy,
+                                                double ih2, const LevelArrays<double> &L,
+                                                const double *__restrict__ b, const double *__restrict__ p)
+{
+    unsigned long long z = __double_as_longlong(p[c]);
+    if (i > 0) z |= __double_as_longlong(p[c - 1]);
+    if (i < nx - 1) z |= __double_as_longlong(p[c + 1]);
+    if (j > 0) z |= __double_as_longlong(p[c - nx]);
+    if (j < ny - 1) z |= __double_as_longlong(p[c + nx]);
+    if (k > 0) z |= __double_as_longlong(p[c - sxy]);
+    if (k < nz - 1) z |= __double_as_longlong(p[c + sxy]);
+    if ((z << 1) == 0ull) return b[c];
+    return residual_at<double>(i, j, k, c, nx, ny, nz, sxy, ih2, L, b, p);
 }
 
 // Residual and cell-centred full weighting: coarse b = mean of the 8 children's residuals.
@@ -244,17 +327,147 @@ __global__ void k_resid_restrict(int nx, int ny, int nz, T ih2, LevelArrays<T> L
     bc[((size_t)K * NY + J) * NX + I] = T(0.125) * s;
 }
 
-// Trilinear cell-centred prolongation added to p: weights 3/4 (parent) and 1/4 (next
-// coarse cell on the fine cell's side) per axis; that index clamps at walls.
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// The same residual + full weighting for FP32, reading each coarse cell's 2x2x2 children as four
+// x-pairs: every row it touches (the children's rows, their y and z neighbour rows, the x halo
+// cells, the face rows) is loaded once as a pair, 44 loads per coarse cell instead of 112
+// stride-2 scalar loads, which made the per-cell form bound by L1 wavefronts.  Each child's
+// residual takes residual_at's terms and conditions in residual_at's order, and the 8 are summed
+// in the same order, so the result is identical.  Arrays 16-byte aligned, fine dims even.
+__global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelArrays<float> L,
+                                       const float *__restrict__ b, const float *__restrict__ p,
+                                       float *__restrict__ bc)
+{
+    const int NX = nx / 2, NY = ny / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= NX) return;
+    const size_t sxy = (size_t)nx * ny;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+    const bool xhi = i0 + 2 < nx, ylo = j0 > 0, yhi = j0 + 2 < ny, zlo = k0 > 0, zhi = k0 + 2 < nz;
+    auto ld2 = [](const float *a, size_t c) { return *reinterpret_cast<const float2 *>(a + c); };
+    const float2 zero2 = make_float2(0.f, 0.f);
+    // row base of fine row (j, k) at x = i0
+    auto row = [&](int j, int k) { return (size_t)k * sxy + (size_t)j * nx + i0; };
+    float2 pc[2][2], bb[2][2], fx[2][2];
+    float pxm[2][2], pxp[2][2], fxp[2][2];
+    float2 fy[2][3], fz[2][3];      // fy[dk][row j0, j0+1, j0+2], fz[dj][plane k0, k0+1, k0+2]
+    float2 pym[2], pyp[2], pzm[2], pzp[2];  // pym[dk] = p(j0-1, k0+dk) ...; pzm[dj] = p(j0+dj, k0-1) ...
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++) {
+            const size_t c = row(j0 + dj, k0 + dk);
+            pc[dj][dk] = ld2(p, c);
+            bb[dj][dk] = ld2(b, c);
+            fx[dj][dk] = ld2(L.bx, c);
+            pxm[dj][dk] = i0 > 0 ? p[c - 1] : 0.f;
+            pxp[dj][dk] = xhi ? p[c + 2] : 0.f;
+            fxp[dj][dk] = xhi ? L.bx[c + 2] : 0.f;
+        }
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++) {
+        fy[dk][0] = ld2(L.by, row(j0, k0 + dk));
+        fy[dk][1] = ld2(L.by, row(j0 + 1, k0 + dk));
+        fy[dk][2] = yhi ? ld2(L.by, row(j0 + 2, k0 + dk)) : zero2;
+        pym[dk] = ylo ? ld2(p, row(j0 - 1, k0 + dk)) : zero2;
+        pyp[dk] = yhi ? ld2(p, row(j0 + 2, k0 + dk)) : zero2;
+    }
+#pragma unroll
+    for (int dj = 0; dj < 2; dj++) {
+        fz[dj][0] = ld2(L.bz, row(j0 + dj, k0));
+        fz[dj][1] = ld2(L.bz, row(j0 + dj, k0 + 1));
+        fz[dj][2] = zhi ? ld2(L.bz, row(j0 + dj, k0 + 2)) : zero2;
+        pzm[dj] = zlo ? ld2(p, row(j0 + dj, k0 - 1)) : zero2;
+        pzp[dj] = zhi ? ld2(p, row(j0 + dj, k0 + 2)) : zero2;
+    }
+    auto comp = [](float2 v, int d) { return d ? v.y : v.x; };
+    float sum = 0.f;
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++)
+#pragma unroll
+            for (int di = 0; di < 2; di++) {
+                const int i = i0 + di, j = j0 + dj, k = k0 + dk;
+                const float pcv = comp(pc[dj][dk], di);
+                float s = 0.f;
+                if (i > 0) s = fmaf(comp(fx[dj][dk], di), (di ? pc[dj][dk].x : pxm[dj][dk]) - pcv, s);
+                if (i < nx - 1) s = fmaf(di ? fxp[dj][dk] : fx[dj][dk].y, (di ? pxp[dj][dk] : pc[dj][dk].y) - pcv, s);
+                if (j > 0) s = fmaf(comp(fy[dk][dj], di), comp(dj ? pc[0][dk] : pym[dk], di) - pcv, s);
+                if (j < ny - 1) s = fmaf(comp(fy[dk][dj + 1], di), comp(dj ? pyp[dk] : pc[1][dk], di) - pcv, s);
+                if (k > 0) s = fmaf(comp(fz[dj][dk], di), comp(dk ? pc[dj][0] : pzm[dj], di) - pcv, s);
+                if (k < nz - 1) s = fmaf(comp(fz[dj][dk + 1], di), comp(dk ? pzp[dj] : pc[dj][1], di) - pcv, s);
+                sum += fmaf(-s, ih2, comp(bb[dj][dk], di));
+            }
+    bc[((size_t)K * NY + J) * NX + I] = 0.125f * sum;
+}
+
+// Trilinear cell-centred prolongation added to p (cells with no open face keep p): weights 3/4
+// (parent) and 1/4 (next coarse cell on the fine cell's side) per axis; that index clamps at
+// walls.  One thread per coarse cell handles its 2x2x2 children as four x-pairs: the 3x3x3 coarse
+// neighbourhood is loaded once and every fine load is issued before the dead-cell test, so a
+// thread keeps 8 pair loads in flight (one load per thread, then a dependent one, leaves the pass
+// bound by memory latency).  A child's 8 products w_z w_y w_x e are summed with fma, z outermost
+// and x innermost, the parent before the neighbour on each axis.  p and dinv are aligned to a
+// pair (16-byte aligned arrays, even nx).
 template <typename T>
 __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, const T *__restrict__ dinv,
-                          T *__restrict__ p)
+                                T *__restrict__ p)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= nx) return;
-    const size_t c = ((size_t)k * ny + j) * nx + i;
-    if (dinv[c] == T(0)) return;
-    p[c] += prolong_at<T>(i, j, k, nx / 2, ny / 2, nz / 2, ec);
+    using P2 = typename Pair<T>::type;
+    const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= NX) return;
+    // neighbourhood index 0 = lower neighbour (clamped), 1 = parent, 2 = upper neighbour (clamped)
+    const int Is[3] = {max(I - 1, 0), I, min(I + 1, NX - 1)};
+    const int Js[3] = {max(J - 1, 0), J, min(J + 1, NY - 1)};
+    const int Ks[3] = {max(K - 1, 0), K, min(K + 1, NZ - 1)};
+    P2 dv[2][2], pv[2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            const size_t c = ((size_t)(2 * K + dz) * ny + (2 * J + dy)) * nx + 2 * I;
+            dv[dz][dy] = *reinterpret_cast<const P2 *>(dinv + c);
+            pv[dz][dy] = *reinterpret_cast<const P2 *>(p + c);
+        }
+    T e[3][3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) e[a][bb][d] = ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]];
+    const T w[2] = {T(0.75), T(0.25)};
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            T out[2];
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                // parent first, then the neighbour on the child's side
+                const int ka[2] = {1, dz ? 2 : 0}, jb[2] = {1, dy ? 2 : 0}, id[2] = {1, dx ? 2 : 0};
+                T s = T(0);
+#pragma unroll
+                for (int a = 0; a < 2; a++)
+#pragma unroll
+                    for (int bb = 0; bb < 2; bb++)
+#pragma unroll
+                        for (int d = 0; d < 2; d++) s = fma(w[a] * w[bb] * w[d], e[ka[a]][jb[bb]][id[d]], s);
+                const T dval = dx ? dv[dz][dy].y : dv[dz][dy].x;
+                const T pold = dx ? pv[dz][dy].y : pv[dz][dy].x;
+                out[dx] = zero_bits(dval) ? pold : pold + s;
+            }
+            const size_t c = ((size_t)(2 * K + dz) * ny + (2 * J + dy)) * nx + 2 * I;
+            P2 o;
+            o.x = out[0];
+            o.y = out[1];
+            *reinterpret_cast<P2 *>(p + c) = o;
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -390,7 +603,7 @@ __global__ void k_count_live(unsigned n, const double *__restrict__ dinv, double
 {
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        a += (dinv[idx] > 0.0) ? 1.0 : 0.0;
+        a += pos_bits(dinv[idx]) ? 1.0 : 0.0;
     a = block_sum<kRedThreads>(a);
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = a;
@@ -404,7 +617,7 @@ __global__ void k_sum_live(unsigned n, const double *__restrict__ v, const doubl
 {
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        if (dinv[idx] > 0.0) a += v[idx];
+        if (pos_bits(dinv[idx])) a += v[idx];
     a = block_sum<kRedThreads>(a);
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = a;
@@ -419,7 +632,7 @@ __global__ void k_rhs_center(unsigned n, const double *__restrict__ rhs, const d
     const double mean = dscal[S_SUM_B] / dscal[S_NLIVE];
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const double v = (dinv[idx] > 0.0) ? rhs[idx] - mean : 0.0;
+        const double v = pos_bits(dinv[idx]) ? rhs[idx] - mean : 0.0;
         b0[idx] = v;
         a += v * v;
     }
@@ -440,9 +653,9 @@ __global__ void k_resid_norm(int nx, int ny, int nz, double ih2, LevelArrays<dou
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_of(idx, nx, ny, i, j, k);
-        const double r = residual_at<double>(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        const double r = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         rr += r * r;
-        if (L.dinv[idx] > 0.0) sp += p[idx];
+        if (pos_bits(L.dinv[idx])) sp += p[idx];
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
@@ -458,7 +671,7 @@ __global__ void k_sub_mean_p(unsigned n, const double *__restrict__ dinv, double
 {
     const double mean = dscal[S_SUM_P] / dscal[S_NLIVE];
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        p[idx] = (dinv[idx] > 0.0) ? p[idx] - mean : 0.0;
+        p[idx] = pos_bits(dinv[idx]) ? p[idx] - mean : 0.0;
 }
 
 // Mixed refinement: r = b - A p in FP64, stored as FP32 r / scale_in; partial ||r||^2.
@@ -473,9 +686,9 @@ __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<dou
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_of(idx, nx, ny, i, j, k);
-        const double r = residual_at<double>(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        const double r = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         rr += r * r;
-        if (L.dinv[idx] > 0.0) sp += p[idx];
+        if (pos_bits(L.dinv[idx])) sp += p[idx];
         r32[idx] = (float)(r * inv_scale);
     }
     rr = block_sum<kRedThreads>(rr);
@@ -521,12 +734,12 @@ __global__ void k_divergence(int nx, int ny, int nz, double scale, const double 
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     double d = 0.0;
-    if (i < nx - 1 && bx[c + 1] > 0.0) d += ux[c + 1];
-    if (bx[c] > 0.0) d -= ux[c];
-    if (j < ny - 1 && by[c + nx] > 0.0) d += uy[c + nx];
-    if (by[c] > 0.0) d -= uy[c];
-    if (k < nz - 1 && bz[c + sxy] > 0.0) d += uz[c + sxy];
-    if (bz[c] > 0.0) d -= uz[c];
+    if (i < nx - 1 && pos_bits(bx[c + 1])) d += ux[c + 1];
+    if (pos_bits(bx[c])) d -= ux[c];
+    if (j < ny - 1 && pos_bits(by[c + nx])) d += uy[c + nx];
+    if (pos_bits(by[c])) d -= uy[c];
+    if (k < nz - 1 && pos_bits(bz[c + sxy])) d += uz[c + sxy];
+    if (pos_bits(bz[c])) d -= uz[c];
     rhs[c] = scale * d;
 }
 
@@ -535,7 +748,7 @@ __global__ void k_divergence(int nx, int ny, int nz, double scale, const double 
 // equal to the quotient), an IEEE division otherwise
 __device__ __forceinline__ double div_h(double x, double h, double inv_h, bool pow2)
 {
-    return pow2 ? __dmul_rn(x, inv_h) : x / h;
+    return pow2 ? __dmul_rn(x, inv_h) : div_call(x, h);
 }
 
 __global__ void k_correct(int nx, int ny, int nz, double dt, double h, double inv_h, int pow2,
@@ -549,15 +762,15 @@ __global__ void k_correct(int nx, int ny, int nz, double dt, double h, double in
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     const double pc = p[c];
     double b = bx[c], u = ux0[c];
-    if (i > 0 && b > 0.0) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
+    if (i > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
     ux[c] = u;
     b = by[c];
     u = uy0[c];
-    if (j > 0 && b > 0.0) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - nx])), h, inv_h, pow2));
+    if (j > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - nx])), h, inv_h, pow2));
     uy[c] = u;
     b = bz[c];
     u = uz0[c];
-    if (k > 0 && b > 0.0) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - sxy])), h, inv_h, pow2));
+    if (k > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - sxy])), h, inv_h, pow2));
     uz[c] = u;
 }
 
@@ -577,7 +790,7 @@ __global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double
 __device__ __forceinline__ void adj_face(double b, double pc, double pn, double qc, double qn, double w, double h,
                                          double inv_h, bool pow2, double dt, double &gu, double &gb)
 {
-    if (b > 0.0) {
+    if (pos_bits(b)) {
         const double gq = div_h(__dsub_rn(qc, qn), h, inv_h, pow2);
         const double gp = div_h(__dsub_rn(pc, pn), h, inv_h, pow2);
         gu = __dsub_rn(w, gq);
@@ -659,11 +872,11 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_of(idx, nx, ny, i, j, k);
-        const double v = residual_at<double>(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        const double v = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         r[idx] = v;
         if (r32) r32[idx] = (float)(v * inv_scale);
         rr += v * v;
-        if (L.dinv[idx] > 0.0) sp += p[idx];
+        if (pos_bits(L.dinv[idx])) sp += p[idx];
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
@@ -781,23 +994,6 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, double ih2, LevelArrays<doub
     }
 }
 
-// diag = sum of the six face coefficients (the same sum, in the same order, as k_diag_inv)
-__global__ void k_diag(int nx, int ny, int nz, const double *__restrict__ bx, const double *__restrict__ by,
-                       const double *__restrict__ bz, double *__restrict__ diag)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= nx) return;
-    const size_t sxy = (size_t)nx * ny;
-    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
-    double s = bx[c];
-    s += (i < nx - 1) ? bx[c + 1] : 0.0;
-    s += by[c];
-    s += (j < ny - 1) ? by[c + nx] : 0.0;
-    s += bz[c];
-    s += (k < nz - 1) ? bz[c + sxy] : 0.0;
-    diag[c] = s;
-}
-
 // alpha = <r,z>/<d,Ad>; p += alpha d; r -= alpha q; ||r||^2; optionally r32 = r / scale with
 // scale = RMS of the previous residual (written to scale_slot).  Two elements per iteration.
 __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
@@ -867,21 +1063,22 @@ cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, 
                                double *bx, double *by, double *bz, cudaStream_t s)
 {
     note_launch();
-    k_face_coeffs<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, phi, solid, rho_a, drho, bx, by,
+    k_face_coeffs<<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, phi, solid, rho_a, drho, bx, by,
                                                                       bz);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s)
+cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, T *diag, cudaStream_t s)
 {
     note_launch();
-    k_diag_inv<T><<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv);
+    k_diag_inv<T><<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv, diag);
     return cudaGetLastError();
 }
-template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *,
+template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *, double *,
                                              cudaStream_t);
-template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, cudaStream_t);
+template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, float *,
+                                            cudaStream_t);
 
 cudaError_t launch_restrict_coeffs(Dims f, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s)
@@ -920,8 +1117,12 @@ cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const 
                                   cudaStream_t s)
 {
     note_launch();
-    k_resid_restrict<T><<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p,
-                                                                                        bc);
+    if constexpr (std::is_same<T, float>::value)
+        k_resid_restrict_pairs<<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L,
+                                                                                               b, p, bc);
+    else
+        k_resid_restrict<T><<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b,
+                                                                                            p, bc);
     return cudaGetLastError();
 }
 template cudaError_t launch_resid_restrict<double>(Dims, double, const LevelArrays<double> &, const double *,
@@ -933,7 +1134,7 @@ template <typename T>
 cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s)
 {
     note_launch();
-    k_prolong<T><<<row_grid(f.nx, f.ny, f.nz), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p);
+    k_prolong<T><<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p);
     return cudaGetLastError();
 }
 template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t);
@@ -1145,13 +1346,6 @@ cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int s
 }
 template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, cudaStream_t);
 template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, cudaStream_t);
-
-cudaError_t launch_diag(Dims d, const double *bx, const double *by, const double *bz, double *diag, cudaStream_t s)
-{
-    note_launch();
-    k_diag<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, diag);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
                              double *q, double *partials, double *dscal, cudaStream_t s)

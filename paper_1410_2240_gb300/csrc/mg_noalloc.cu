@@ -181,6 +181,10 @@ extern "C" int mg_residual_norm_noalloc(const mg_grid *g, const double *const be
     }
     if (!beta || !beta[0] || !beta[1] || !beta[2] || !rhs || !p || !out)
         return noalloc_fail(MG_ERR_ARG, "mg_residual_norm_noalloc: null pointer");
+    for (const void *q : {(const void *)beta[0], (const void *)beta[1], (const void *)beta[2], (const void *)rhs,
+                          (const void *)p, (const void *)out})
+        if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
+            return noalloc_fail(MG_ERR_ARG, "mg_residual_norm_noalloc: arrays must be 16-byte aligned");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -127,6 +127,8 @@ def _dev(t: torch.Tensor, shape, dtype=torch.float64, name="tensor"):
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}, got {tuple(t.shape)}")
+    if t.data_ptr() % 16:
+        raise ValueError(f"{name} must start on a 16-byte boundary (a view offset into its storage does not)")
     return _vp(t.data_ptr())
 
 

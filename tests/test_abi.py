@@ -53,3 +53,36 @@ def test_no_cpu_fallback_in_product_package():
         if fn.endswith(".py"):
             src = open(os.path.join(pkg, fn)).read()
             assert "import oracle" not in src and "from oracle" not in src, fn
+
+
+def test_unaligned_arrays_are_rejected_before_any_device_work():
+    """Every array argument must start on a 16-byte boundary.  The check precedes any CUDA call,
+    so addresses that are never dereferenced exercise it here; it is skipped where a GPU is
+    visible, so that fake addresses can never reach a kernel."""
+    import torch
+    if torch.cuda.is_available():
+        import pytest
+        pytest.skip("fake device addresses are only passed where no GPU is visible")
+    from paper_1410_2240_gb300.build import build
+
+    class Grid(ctypes.Structure):
+        _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double)]
+
+    lib = ctypes.CDLL(build())
+    lib.mg_last_error.restype = ctypes.c_char_p
+    P3 = ctypes.c_void_p * 3
+    good, bad = 0x10000, 0x10008  # bad: 8-byte aligned only
+    g = Grid(8, 8, 8, 0.125)
+    lib.mg_face_coeffs.argtypes = [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                   ctypes.c_double, P3, ctypes.c_void_p]
+    assert lib.mg_face_coeffs(ctypes.byref(g), bad, None, 1e-3, 1.0, P3(good, good, good), None) == 1
+    assert b"16-byte" in lib.mg_last_error()
+    assert lib.mg_face_coeffs(ctypes.byref(g), good, None, 1e-3, 1.0, P3(good, bad, good), None) == 1
+    lib.mg_phi_grad.argtypes = [ctypes.POINTER(Grid), P3, P3, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                ctypes.c_void_p]
+    assert lib.mg_phi_grad(ctypes.byref(g), P3(good, good, good), P3(good, good, good), 1e-3, 1.0, bad, None) == 1
+    assert b"16-byte" in lib.mg_last_error()
+    lib.mg_residual_norm_noalloc.argtypes = [ctypes.POINTER(Grid), P3, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.mg_residual_norm_noalloc(ctypes.byref(g), P3(good, good, good), good, bad, good, None) == 1
+    assert b"16-byte" in lib.mg_last_error()
