@@ -14,6 +14,7 @@
 #include <cstring>
 #include <initializer_list>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mg_internal.cuh"
@@ -72,6 +73,9 @@ struct mg_ctx {
     double *kr = nullptr, *kd = nullptr, *kq = nullptr, *kz = nullptr, *kzo = nullptr;
     double *kdiag = nullptr;  // finest-grid sum of face coefficients (CG operator)
     float *ke_alt = nullptr;
+    // layout of the finest FP32 iterate / right-hand side (L32[0].p, L32[0].b, ke_alt): colour-split
+    // for the per-colour smoother in mixed precision, natural otherwise
+    mg::Split split0;
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
     double *qbuf = nullptr;     // adjoint solution when the caller passes none
@@ -362,6 +366,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const T ih2 = (T)(1.0 / (c->hs[l] * c->hs[l]));
     const bool fine = (l == 0);
     const bool fused = use_fused<T>(c, l) && palt_of<T>(c, l) != nullptr;
+    const mg::Split sp = (sizeof(T) == 4 && l == 0) ? c->split0 : mg::Split{};
     T *cur = p, *alt = palt_of<T>(c, l);
     // one red-black sweep, `first` colour first
     auto sweep = [&](int first) -> int {
@@ -372,6 +377,11 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
             else
                 CK(mg::launch_rb_sweep<T>(d, h2, L[l], b, cur, alt, first, s));
             std::swap(cur, alt);
+        } else if (sp.half) {
+            if constexpr (std::is_same<T, float>::value) {
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s));
+            }
         } else {
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first ^ 1, s));
@@ -382,7 +392,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const LevelArrays<T> &C = L[l + 1];
     {
         ProfScope ps(c, MG_PROF_RESTRICT, fine);
-        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s));
+        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s, sp));
     }
     {
         ProfScope ps(c, MG_PROF_COARSE, fine);
@@ -395,7 +405,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     }
     {
         ProfScope ps(c, MG_PROF_PROLONG, fine);
-        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, cur, s));
+        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, cur, s, sp));
     }
     for (int it = 0; it < c->o.nu2; it++) CKS(sweep(1));
     if (cur != p) CK(cudaMemcpyAsync(p, cur, d.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -482,7 +492,8 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
     int scale_slot = mg::S_SCALE0, next_slot = mg::S_SCALE1;
     if (mixed) {
         ProfScope ps(c, MG_PROF_RESID64, true);
-        CK(mg::launch_resid_cast(d, ih2, c->L64[0], c->b0, p, c->L32[0].b, c->partials, c->dscal, -1, next_slot, s));
+        CK(mg::launch_resid_cast(d, ih2, c->L64[0], c->b0, p, c->L32[0].b, c->partials, c->dscal, -1, next_slot, s,
+                                 c->split0));
     } else {
         ProfScope ps(c, MG_PROF_RESID64, true);
         CK(mg::launch_resid_norm(d, ih2, c->L64[0], c->b0, p, c->partials, c->dscal, s));
@@ -518,11 +529,11 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
         if (mixed) {
             CK(cudaMemsetAsync(c->L32[0].p, 0, d.n() * sizeof(float), s));
             for (int ic = 0; ic < c->o.inner_cycles; ic++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, c->L32[0].p));
-            CK(mg::launch_accumulate(d, c->L64[0].dinv, c->L32[0].p, p, c->dscal, scale_slot, s));
+            CK(mg::launch_accumulate(d, c->L64[0].dinv, c->L32[0].p, p, c->dscal, scale_slot, s, c->split0));
             std::swap(scale_slot, next_slot);
             ProfScope ps(c, MG_PROF_RESID64, true);
             CK(mg::launch_resid_cast(d, ih2, c->L64[0], c->b0, p, c->L32[0].b, c->partials, c->dscal, scale_slot,
-                                     next_slot, s));
+                                     next_slot, s, c->split0));
         } else {
             CKS(vcycle<double>(c, c->L64, 0, c->b0, p));
             if (cyc % c->o.check_every != 0 && cyc < c->o.max_cycles) continue;
@@ -631,7 +642,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
         {
             ProfScope ps(c, MG_PROF_RESID64, true);
             CK(mg::launch_pcg_resid(d, ih2, c->L64[0], c->b0, p, c->kr, mixed ? c->L32[0].b : nullptr, c->partials,
-                                    c->dscal, sc_cur, s));
+                                    c->dscal, sc_cur, s, c->split0));
         }
         CKS(read_scalars(c));
         nb2 = c->hscal[mg::S_NB2];
@@ -660,7 +671,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
         CKS(precondition());
         if (mixed) {
             CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, nullptr, c->partials, c->dscal, sc_cur, sc_cur, -1, s));
-            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 1, s));
+            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 1, s, c->split0));
         } else {
             CK(mg::launch_pcg_dots<double>(n, c->kr, z, nullptr, c->partials, c->dscal, -1, -1, s));
             CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, 1, s));
@@ -677,7 +688,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             {
                 ProfScope ps(c, MG_PROF_RESID64, true);
                 CK(mg::launch_pcg_update(n, c->kd, c->kq, p, c->kr, mixed ? c->L32[0].b : nullptr, c->partials, c->dscal,
-                                         sc_cur, s));
+                                         sc_cur, s, c->split0));
             }
             CKS(read_scalars(c));
             rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
@@ -688,7 +699,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             if (mixed) {
                 CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, e_old, c->partials, c->dscal, sc_cur, sc_cur, sc_old,
                                          s));
-                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 0, s));
+                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 0, s, c->split0));
             } else {
                 CK(mg::launch_pcg_dots<double>(n, c->kr, z, zo, c->partials, c->dscal, -1, -1, s));
                 CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, 0, s));
@@ -800,6 +811,10 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
         h *= 2.0;
     }
     c->nlev = (int)c->dims.size();
+    // the finest FP32 fields are colour-split when its sweeps are colour passes; a hierarchy of
+    // two or more levels has even dims on the finest
+    if (c->o.prec == MG_MIXED && c->o.smoother <= 1 && c->nlev >= 2)
+        c->split0 = mg::Split{c->dims[0].n() / 2, c->dims[0].nx, c->dims[0].ny};
     const Dims dc = c->dims.back();
     if ((long long)dc.n() > o.coarse_max_cells)
         return bail(fail(MG_ERR_ARG, "mg_setup: coarsest grid %dx%dx%d has %zu cells > coarse_max_cells=%d", dc.nx,

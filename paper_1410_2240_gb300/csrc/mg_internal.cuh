@@ -55,6 +55,15 @@ void note_kernel_launch();
 // set the message mg_last_error() returns on this thread
 void set_last_error(const char *msg);
 
+// Layout of the finest level's FP32 iterate and right-hand side.  half == 0: natural C order.
+// half == n / 2 (all dims even): colour-split, the cells of colour (i + j + k) & 1 == 0 in
+// [0, half) and of colour 1 in [half, n), cell c at slot c >> 1 of its colour's half.  Face
+// coefficients and every FP64 field keep the natural order.
+struct Split {
+    size_t half = 0;
+    int nx = 0, ny = 0;
+};
+
 // ---- kernel launchers (mg_kernels.cu); all stream-ordered, return cudaError_t of the launch ----
 cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
                                double *bx, double *by, double *bz, cudaStream_t s);
@@ -67,6 +76,9 @@ cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_
 template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
                           int z0 = 0, int z1 = -1);
+// one colour of a red-black sweep on the colour-split layout (FP32, all dims even)
+cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
+                                cudaStream_t s);
 // FP32 fused sweep with TMA-staged planes (mg_sweep_tma.cu)
 bool tma_sweep_supported(Dims d);
 cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,
@@ -76,11 +88,12 @@ cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, c
 template <typename T>
 cudaError_t launch_rb_sweep(Dims d, T h2, const LevelArrays<T> &L, const T *b, const T *p_old, T *p_new, int first,
                             cudaStream_t s);
+// b and p of the fine level in the layout sp (FP32 only may be split); bc natural
 template <typename T>
 cudaError_t launch_resid_restrict(Dims fine, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
-                                  cudaStream_t s);
+                                  cudaStream_t s, Split sp = {});
 template <typename T>
-cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s);
+cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp = {});
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s);
 
@@ -91,26 +104,29 @@ cudaError_t launch_rhs_prepare(Dims d, const double *rhs, const double *dinv, do
 cudaError_t launch_resid_norm(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
                               double *partials, double *dscal, cudaStream_t s);
 cudaError_t launch_sub_mean_p(Dims d, const double *dinv, double *p, const double *dscal, cudaStream_t s);
+// r32 / e32: the finest FP32 fields, in the layout sp
 cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
                               float *r32, double *partials, double *dscal, int scale_in, int scale_out,
-                              cudaStream_t s);
+                              cudaStream_t s, Split sp = {});
 cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, double *p, const double *dscal,
-                              int scale_slot, cudaStream_t s);
+                              int scale_slot, cudaStream_t s, Split sp = {});
 
 // multigrid-preconditioned CG (FP64 Krylov vectors)
 cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
-                             double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s);
+                             double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s,
+                             Split sp = {});
 template <typename Z>
 cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, double *partials, double *dscal,
                             int sz_slot, int so_slot, cudaStream_t s);
 cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const float *zo, double *partials,
                               double *dscal, int sr_slot, int sz_slot, int so_slot, cudaStream_t s);
 template <typename Z>
-cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s);
+cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s,
+                           Split sp = {});
 cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
                              double *q, double *partials, double *dscal, cudaStream_t s);
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
-                              double *partials, double *dscal, int scale_slot, cudaStream_t s);
+                              double *partials, double *dscal, int scale_slot, cudaStream_t s, Split sp = {});
 
 // projection and adjoint
 cudaError_t launch_divergence(Dims d, double scale, const double *bx, const double *by, const double *bz,

@@ -264,10 +264,49 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
     p[c] = inv_diag<T>(sizeof(T) == 8 ? L.dinv[c] : T(0), bxl, bxh, byl, byh, bzl, bzh) * fma(-h2, b[c], s);
 }
 
-// Trilinear cell-centred prolongation of the coarse correction ec at fine cell (i,j,k): weights
-// 3/4 on the parent and 1/4 on the next coarse cell toward the fine cell, per axis, that index
-// clamped to the domain; the 8 weighted values are accumulated with fused multiply-adds in the
-// order K, J, I.
+// Colour-split layout (Split in mg_internal.cuh): slot of natural cell c in a row of parity
+// q = (j + k) & 1, whose colour is (c & 1) ^ q (rows start at even indices).
+__device__ __forceinline__ size_t split_slot(size_t c, int q, size_t half)
+{
+    return (((int)(c & 1) ^ q) ? half : 0) + (c >> 1);
+}
+// parity (j + k) & 1 of the row holding natural index c
+__device__ __forceinline__ int row_parity(unsigned c, int nx, int ny)
+{
+    const unsigned row = c / (unsigned)nx;
+    return (int)((row % (unsigned)ny + row / (unsigned)ny) & 1u);
+}
+
+// One colour of red-black Gauss-Seidel on the colour-split layout (FP32, all dims even): the
+// cell's six neighbours are the other colour's slots m-1+(i&1), m+(i&1), m -+ nx/2, m -+ nx*ny/2
+// (m = c >> 1), read contiguously; b and the result are the own colour's slot m.  A pass moves
+// the face coefficients, half of p and half of b instead of all of p and b.  Same arithmetic, in
+// the same order, as k_smooth<float>.
+__global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
+                               float *__restrict__ p, int colour)
+{
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny, half = sxy * nz / 2;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    const size_t m = c >> 1, hx = nx / 2, hxy = sxy / 2;
+    const float *__restrict__ o = p + (colour ? 0 : half);  // the other colour
+    const int odd = i & 1;
+    float s = 0.f;
+    const float bxl = L.bx[c], bxh = (i < nx - 1) ? L.bx[c + 1] : 0.f;
+    const float byl = L.by[c], byh = (j < ny - 1) ? L.by[c + nx] : 0.f;
+    const float bzl = L.bz[c], bzh = (k < nz - 1) ? L.bz[c + sxy] : 0.f;
+    if (i > 0) s = fmaf(bxl, o[m - 1 + odd], s);
+    if (i < nx - 1) s = fmaf(bxh, o[m + odd], s);
+    if (j > 0) s = fmaf(byl, o[m - hx], s);
+    if (j < ny - 1) s = fmaf(byh, o[m + hx], s);
+    if (k > 0) s = fmaf(bzl, o[m - hxy], s);
+    if (k < nz - 1) s = fmaf(bzh, o[m + hxy], s);
+    const size_t own = (colour ? half : 0) + m;
+    p[own] = inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, b[own], s);
+}
+
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
 template <typename T>
 __device__ __forceinline__ T residual_at(int i, int j, int k, size_t c, int nx, int ny, int nz, size_t sxy, T ih2,
@@ -337,9 +376,10 @@ template <> struct Pair<double> { using type = double2; };
 // stride-2 scalar loads, which made the per-cell form bound by L1 wavefronts.  Each child's
 // residual takes residual_at's terms and conditions in residual_at's order, and the 8 are summed
 // in the same order, so the result is identical.  Arrays 16-byte aligned, fine dims even.
+template <bool SPLIT>
 __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelArrays<float> L,
                                        const float *__restrict__ b, const float *__restrict__ p,
-                                       float *__restrict__ bc)
+                                       float *__restrict__ bc, size_t half)
 {
     const int NX = nx / 2, NY = ny / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
@@ -348,9 +388,17 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
     const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
     const bool xhi = i0 + 2 < nx, ylo = j0 > 0, yhi = j0 + 2 < ny, zlo = k0 > 0, zhi = k0 + 2 < nz;
     auto ld2 = [](const float *a, size_t c) { return *reinterpret_cast<const float2 *>(a + c); };
+    // p and b pairs: natural, or the two colours' slots c >> 1 (row parity q decides the order)
+    auto ldf2 = [&](const float *a, size_t c, int q) {
+        if (!SPLIT) return ld2(a, c);
+        const size_t m = c >> 1;
+        return q ? make_float2(a[half + m], a[m]) : make_float2(a[m], a[half + m]);
+    };
+    auto ldf = [&](const float *a, size_t c, int q) { return SPLIT ? a[split_slot(c, q, half)] : a[c]; };
     const float2 zero2 = make_float2(0.f, 0.f);
-    // row base of fine row (j, k) at x = i0
+    // row base of fine row (j, k) at x = i0, and its parity
     auto row = [&](int j, int k) { return (size_t)k * sxy + (size_t)j * nx + i0; };
+    auto par = [](int j, int k) { return (j + k) & 1; };
     float2 pc[2][2], bb[2][2], fx[2][2];
     float pxm[2][2], pxp[2][2], fxp[2][2];
     float2 fy[2][3], fz[2][3];      // fy[dk][row j0, j0+1, j0+2], fz[dj][plane k0, k0+1, k0+2]
@@ -360,11 +408,12 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
 #pragma unroll
         for (int dj = 0; dj < 2; dj++) {
             const size_t c = row(j0 + dj, k0 + dk);
-            pc[dj][dk] = ld2(p, c);
-            bb[dj][dk] = ld2(b, c);
+            const int q = par(j0 + dj, k0 + dk);
+            pc[dj][dk] = ldf2(p, c, q);
+            bb[dj][dk] = ldf2(b, c, q);
             fx[dj][dk] = ld2(L.bx, c);
-            pxm[dj][dk] = i0 > 0 ? p[c - 1] : 0.f;
-            pxp[dj][dk] = xhi ? p[c + 2] : 0.f;
+            pxm[dj][dk] = i0 > 0 ? ldf(p, c - 1, q) : 0.f;
+            pxp[dj][dk] = xhi ? ldf(p, c + 2, q) : 0.f;
             fxp[dj][dk] = xhi ? L.bx[c + 2] : 0.f;
         }
 #pragma unroll
@@ -372,16 +421,16 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
         fy[dk][0] = ld2(L.by, row(j0, k0 + dk));
         fy[dk][1] = ld2(L.by, row(j0 + 1, k0 + dk));
         fy[dk][2] = yhi ? ld2(L.by, row(j0 + 2, k0 + dk)) : zero2;
-        pym[dk] = ylo ? ld2(p, row(j0 - 1, k0 + dk)) : zero2;
-        pyp[dk] = yhi ? ld2(p, row(j0 + 2, k0 + dk)) : zero2;
+        pym[dk] = ylo ? ldf2(p, row(j0 - 1, k0 + dk), par(j0 - 1, k0 + dk)) : zero2;
+        pyp[dk] = yhi ? ldf2(p, row(j0 + 2, k0 + dk), par(j0 + 2, k0 + dk)) : zero2;
     }
 #pragma unroll
     for (int dj = 0; dj < 2; dj++) {
         fz[dj][0] = ld2(L.bz, row(j0 + dj, k0));
         fz[dj][1] = ld2(L.bz, row(j0 + dj, k0 + 1));
         fz[dj][2] = zhi ? ld2(L.bz, row(j0 + dj, k0 + 2)) : zero2;
-        pzm[dj] = zlo ? ld2(p, row(j0 + dj, k0 - 1)) : zero2;
-        pzp[dj] = zhi ? ld2(p, row(j0 + dj, k0 + 2)) : zero2;
+        pzm[dj] = zlo ? ldf2(p, row(j0 + dj, k0 - 1), par(j0 + dj, k0 - 1)) : zero2;
+        pzp[dj] = zhi ? ldf2(p, row(j0 + dj, k0 + 2), par(j0 + dj, k0 + 2)) : zero2;
     }
     auto comp = [](float2 v, int d) { return d ? v.y : v.x; };
     float sum = 0.f;
@@ -413,9 +462,9 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
 // bound by memory latency).  A child's 8 products w_z w_y w_x e are summed with fma, z outermost
 // and x innermost, the parent before the neighbour on each axis.  p and dinv are aligned to a
 // pair (16-byte aligned arrays, even nx).
-template <typename T>
+template <typename T, bool SPLIT>
 __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, const T *__restrict__ dinv,
-                                T *__restrict__ p)
+                          T *__restrict__ p, size_t half)
 {
     using P2 = typename Pair<T>::type;
     const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
@@ -432,7 +481,14 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
         for (int dy = 0; dy < 2; dy++) {
             const size_t c = ((size_t)(2 * K + dz) * ny + (2 * J + dy)) * nx + 2 * I;
             dv[dz][dy] = *reinterpret_cast<const P2 *>(dinv + c);
-            pv[dz][dy] = *reinterpret_cast<const P2 *>(p + c);
+            if (SPLIT) {  // the pair's two colours at slot c >> 1 of each half
+                const size_t m = c >> 1;
+                const bool q = (2 * J + dy + 2 * K + dz) & 1;
+                pv[dz][dy].x = p[(q ? half : 0) + m];
+                pv[dz][dy].y = p[(q ? 0 : half) + m];
+            } else {
+                pv[dz][dy] = *reinterpret_cast<const P2 *>(p + c);
+            }
         }
     T e[3][3][3];
 #pragma unroll
@@ -463,10 +519,17 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
                 out[dx] = zero_bits(dval) ? pold : pold + s;
             }
             const size_t c = ((size_t)(2 * K + dz) * ny + (2 * J + dy)) * nx + 2 * I;
-            P2 o;
-            o.x = out[0];
-            o.y = out[1];
-            *reinterpret_cast<P2 *>(p + c) = o;
+            if (SPLIT) {
+                const size_t m = c >> 1;
+                const bool q = (2 * J + dy + 2 * K + dz) & 1;
+                p[(q ? half : 0) + m] = out[0];
+                p[(q ? 0 : half) + m] = out[1];
+            } else {
+                P2 o;
+                o.x = out[0];
+                o.y = out[1];
+                *reinterpret_cast<P2 *>(p + c) = o;
+            }
         }
 }
 
@@ -677,7 +740,8 @@ __global__ void k_sub_mean_p(unsigned n, const double *__restrict__ dinv, double
 // Mixed refinement: r = b - A p in FP64, stored as FP32 r / scale_in; partial ||r||^2.
 __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<double> L,
                              const double *__restrict__ b, const double *__restrict__ p, float *__restrict__ r32,
-                             const double *__restrict__ dscal, int scale_in, double *__restrict__ partials)
+                             const double *__restrict__ dscal, int scale_in, double *__restrict__ partials,
+                             size_t half)
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
@@ -689,7 +753,7 @@ __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<dou
         const double r = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         rr += r * r;
         if (pos_bits(L.dinv[idx])) sp += p[idx];
-        r32[idx] = (float)(r * inv_scale);
+        r32[half ? split_slot(idx, (j + k) & 1, half) : idx] = (float)(r * inv_scale);
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
@@ -712,13 +776,16 @@ __global__ void k_scale_from_nb2(double *dscal, int slot)
     dscal[slot] = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
 }
 
-// p += scale * e32 (the FP32 cycle leaves e32 = 0 on dead cells, so no mask is read)
+// p += scale * e32 (the FP32 cycle leaves e32 = 0 on dead cells, so no mask is read); e32 in
+// the layout (half, nx, ny)
 __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *__restrict__ p,
-                             const double *__restrict__ dscal, int scale_slot)
+                             const double *__restrict__ dscal, int scale_slot, size_t half, int nx, int ny)
 {
     const double s = dscal[scale_slot];
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        p[idx] = fma(s, (double)e32[idx], p[idx]);
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const size_t e = half ? split_slot(idx, row_parity(idx, nx, ny), half) : idx;
+        p[idx] = fma(s, (double)e32[e], p[idx]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -857,7 +924,7 @@ __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const d
 // r = b - A p (FP64); optionally r32 = r / scale, scale = RMS of b (first pass) written to scale_slot
 __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<double> L, const double *__restrict__ b,
                             const double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
-                            double *__restrict__ dscal, int scale_slot, double *__restrict__ partials)
+                            double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, size_t half)
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
@@ -874,7 +941,7 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
         cell_of(idx, nx, ny, i, j, k);
         const double v = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         r[idx] = v;
-        if (r32) r32[idx] = (float)(v * inv_scale);
+        if (r32) r32[half ? split_slot(idx, (j + k) & 1, half) : idx] = (float)(v * inv_scale);
         rr += v * v;
         if (pos_bits(L.dinv[idx])) sp += p[idx];
     }
@@ -943,14 +1010,20 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
 // d = sz * Z + beta d,  beta = (<r,z> - <r,z_old>) / <r_old, z_old>  (first: beta = 0)
 template <typename Z>
 __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, const double *__restrict__ dscal,
-                          int sz_slot, int first)
+                          int sz_slot, int first, size_t half, int nx, int ny)
 {
     const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
     const double beta = first ? 0.0 : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ];
     const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
     double2 *d2 = reinterpret_cast<double2 *>(d);
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
-        const double z0 = (double)z[2 * v], z1 = (double)z[2 * v + 1];
+        size_t i0 = 2 * v, i1 = 2 * v + 1;
+        if (half) {  // colour-split Z: the pair's colours sit at slot v of each half
+            const int q = row_parity(2 * v, nx, ny);
+            i0 = (q ? half : 0) + v;
+            i1 = (q ? 0 : half) + v;
+        }
+        const double z0 = (double)z[i0], z1 = (double)z[i1];
         double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
         dv.x = fma(beta, dv.x, sz * z0);
         dv.y = fma(beta, dv.y, sz * z1);
@@ -998,7 +1071,8 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, double ih2, LevelArrays<doub
 // scale = RMS of the previous residual (written to scale_slot).  Two elements per iteration.
 __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
                              double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
-                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials)
+                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, size_t half,
+                             int nx, int ny)
 {
     const double alpha = dscal[S_RZ] / dscal[S_SIGMA];
     double inv_scale = 1.0;
@@ -1025,7 +1099,16 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
         rv.y = fma(-alpha, qv.y, rv.y);
         p2[v] = pv;
         rv2[v] = rv;
-        if (r32) r32v[v] = make_float2((float)rv.x * inv_scale32, (float)rv.y * inv_scale32);
+        if (r32) {
+            const float r0 = (float)rv.x * inv_scale32, r1 = (float)rv.y * inv_scale32;
+            if (half) {  // colour-split r32: the pair's colours at slot v of each half
+                const int qp = row_parity(2 * v, nx, ny);
+                r32[(qp ? half : 0) + v] = r0;
+                r32[(qp ? 0 : half) + v] = r1;
+            } else {
+                r32v[v] = make_float2(r0, r1);
+            }
+        }
         rr = fma(rv.x, rv.x, rr);
         rr = fma(rv.y, rv.y, rr);
     }
@@ -1112,33 +1195,54 @@ template cudaError_t launch_smooth<double>(Dims, double, const LevelArrays<doubl
 template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> &, const float *, float *, int,
                                           cudaStream_t, int, int);
 
-template <typename T>
-cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
-                                  cudaStream_t s)
+cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
+                                cudaStream_t s)
 {
     note_launch();
-    if constexpr (std::is_same<T, float>::value)
-        k_resid_restrict_pairs<<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L,
-                                                                                               b, p, bc);
-    else
-        k_resid_restrict<T><<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b,
-                                                                                            p, bc);
+    k_smooth_split<<<row_grid(d.nx / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
+                                  cudaStream_t s, Split sp)
+{
+    note_launch();
+    const dim3 g = row_grid(f.nx / 2, f.ny / 2, f.nz / 2);
+    if constexpr (std::is_same<T, float>::value) {
+        if (sp.half)
+            k_resid_restrict_pairs<true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half);
+        else
+            k_resid_restrict_pairs<false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0);
+    } else {
+        if (sp.half) return cudaErrorInvalidValue;  // FP64 fields are never split
+        k_resid_restrict<T><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc);
+    }
     return cudaGetLastError();
 }
 template cudaError_t launch_resid_restrict<double>(Dims, double, const LevelArrays<double> &, const double *,
-                                                   const double *, double *, cudaStream_t);
+                                                   const double *, double *, cudaStream_t, Split);
 template cudaError_t launch_resid_restrict<float>(Dims, float, const LevelArrays<float> &, const float *,
-                                                  const float *, float *, cudaStream_t);
+                                                  const float *, float *, cudaStream_t, Split);
 
 template <typename T>
-cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s)
+cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp)
 {
     note_launch();
-    k_prolong<T><<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p);
+    const dim3 g = row_grid(f.nx / 2, f.ny / 2, f.nz / 2);
+    if constexpr (std::is_same<T, float>::value) {
+        if (sp.half) {
+            k_prolong<T, true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, sp.half);
+            return cudaGetLastError();
+        }
+    } else if (sp.half) {
+        return cudaErrorInvalidValue;  // FP64 fields are never split
+    }
+    k_prolong<T, false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, 0);
     return cudaGetLastError();
 }
-template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t);
-template cudaError_t launch_prolong<float>(Dims, const float *, const float *, float *, cudaStream_t);
+template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t, Split);
+template cudaError_t launch_prolong<float>(Dims, const float *, const float *, float *, cudaStream_t, Split);
 
 // Tiles of 32 x 8 columns; z-chunks sized so that the grid has about 4 CTAs per SM.
 template <typename T>
@@ -1219,7 +1323,7 @@ cudaError_t launch_sub_mean_p(Dims d, const double *dinv, double *p, const doubl
 
 cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
                               float *r32, double *partials, double *dscal, int scale_in, int scale_out,
-                              cudaStream_t s)
+                              cudaStream_t s, Split sp)
 {
     const unsigned g = red_grid(d.n());
     if (scale_in < 0) {  // first pass: scale from ||b0||
@@ -1228,7 +1332,7 @@ cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, 
         k_scale_from_nb2<<<1, 1, 0, s>>>(dscal, scale_in);
     }
     note_launch();
-    k_resid_cast<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r32, dscal, scale_in, partials);
+    k_resid_cast<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r32, dscal, scale_in, partials, sp.half);
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
     note_launch();
@@ -1237,11 +1341,12 @@ cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, 
 }
 
 cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, double *p, const double *dscal,
-                              int scale_slot, cudaStream_t s)
+                              int scale_slot, cudaStream_t s, Split sp)
 {
     note_launch();
     (void)dinv;
-    k_accumulate<<<red_grid(d.n()), kRedThreads, 0, s>>>((unsigned)d.n(), e32, p, dscal, scale_slot);
+    k_accumulate<<<red_grid(d.n()), kRedThreads, 0, s>>>((unsigned)d.n(), e32, p, dscal, scale_slot, sp.half, d.nx,
+                                                          d.ny);
     return cudaGetLastError();
 }
 
@@ -1299,11 +1404,12 @@ cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, cons
 
 
 cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
-                             double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s)
+                             double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s,
+                             Split sp)
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials);
+    k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials, sp.half);
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
     return cudaGetLastError();
@@ -1336,16 +1442,18 @@ template cudaError_t launch_pcg_dots<float>(size_t, const double *, const float 
                                             int, int, cudaStream_t);
 
 template <typename Z>
-cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s)
+cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s,
+                           Split sp)
 {
+    if (sp.half && sizeof(Z) != 4) return cudaErrorInvalidValue;  // FP64 fields are never split
     note_launch();
-    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, first);
+    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, first, sp.half, sp.nx, sp.ny);
     note_launch();
     k_pcg_shift_rz<<<1, 1, 0, s>>>(dscal);
     return cudaGetLastError();
 }
-template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, cudaStream_t);
-template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, cudaStream_t);
+template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, cudaStream_t, Split);
+template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, cudaStream_t, Split);
 
 cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
                              double *q, double *partials, double *dscal, cudaStream_t s)
@@ -1359,11 +1467,12 @@ cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, c
 }
 
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
-                              double *partials, double *dscal, int scale_slot, cudaStream_t s)
+                              double *partials, double *dscal, int scale_slot, cudaStream_t s, Split sp)
 {
     const unsigned g = red_grid(n);
     note_launch();
-    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, partials);
+    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, partials, sp.half, sp.nx,
+                                           sp.ny);
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, -1);
     return cudaGetLastError();
