@@ -49,9 +49,9 @@ B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
 SWEEP_KERNEL = {0: "k_smooth_split x2 colour passes, colour-split p and b",
                 1: "k_smooth_split x2 colour passes, colour-split p and b",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
-# DRAM bytes of one finest-grid FP32 sweep of the default smoother (two colour passes) from an ncu
-# capture of this workload; None until the current kernel has been captured
-SWEEP_TRAFFIC_256 = None
+# DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split colour
+# passes) from an ncu capture of this workload (profiles/k_smooth_split_256_colour_pass.md)
+SWEEP_TRAFFIC_256 = 268.456960e6 + 26.637056e6 + 268.452352e6 + 27.134208e6
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))
 
