@@ -96,6 +96,10 @@ typedef struct {
     int coarse_graph;     /* 1: replay the coarse-grid part of each V-cycle (all levels below the
                              finest) as one CUDA graph captured on first use on a private stream;
                              0: launch its kernels one by one.  Identical results [1] */
+    int coarse_tail;      /* 1: the smallest levels below the finest (each field of at most a few
+                             thousand cells) are smoothed, restricted and prolonged by one CTA in
+                             two launches around the coarsest solve instead of a launch per pass;
+                             0: a launch per pass.  Identical results [1] */
 } mg_opts;
 
 /* Solve statistics (host struct, filled when non-NULL). */

@@ -71,7 +71,8 @@ struct mg_ctx {
     // conjugate-gradient vectors (krylov = 1): FP64 r, d, q; z, z_old (FP64 cycles) or a
     // second FP32 cycle output (mixed cycles)
     double *kr = nullptr, *kd = nullptr, *kq = nullptr, *kz = nullptr, *kzo = nullptr;
-    double *kdiag = nullptr;  // finest-grid sum of face coefficients (CG operator)
+    // CG operator on the finest grid: h^-2 beta in bx/by/bz and h^-2 sum(beta) in dinv
+    LevelArrays<double> kop;
     float *ke_alt = nullptr;
     // layout of the finest FP32 iterate / right-hand side (L32[0].p, L32[0].b, ke_alt): colour-split
     // for the per-colour smoother in mixed precision, natural otherwise
@@ -353,6 +354,18 @@ inline cudaError_t launch_sweep_tma(Dims, double, const LevelArrays<double> &, c
 template <typename T>
 int coarse_correction_graph(mg_ctx *c, const std::vector<LevelArrays<T>> &L);
 
+// First level of the coarse tail in precision T: the largest level below the finest, above the
+// coarsest, whose six fields (p, b, three face arrays, dinv) fit in an SM's L1; -1 if none.
+constexpr size_t kTailBytes = 200 * 1024;
+template <typename T>
+int tail_start(const mg_ctx *c)
+{
+    if (!c->o.coarse_tail) return -1;
+    for (int l = 1; l + 1 < c->nlev && l - 1 < mg::kTailMaxLevels; l++)
+        if (c->dims[l].n() * 6 * sizeof(T) <= kTailBytes && c->nlev - l <= mg::kTailMaxLevels) return l;
+    return -1;
+}
+
 template <typename T>
 int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T *p)
 {
@@ -360,6 +373,25 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const Dims d = c->dims[l];
     if (l == c->nlev - 1) {
         CK(mg::launch_coarse_solve<T>(c->ncoarse, c->M, b, p, s));
+        return MG_OK;
+    }
+    if (l == tail_start<T>(c)) {  // this level and all below: one CTA, two launches
+        mg::TailArgs<T> a{};
+        a.nlev = c->nlev - l;
+        a.nu1 = c->o.nu1;
+        a.nu2 = c->o.nu2;
+        for (int q = 0; q < a.nlev; q++) {
+            const int lv = l + q;
+            const Dims dl = c->dims[lv];
+            a.lev[q] = mg::TailLevel<T>{dl.nx, dl.ny, dl.nz, (T)(c->hs[lv] * c->hs[lv]),
+                                        (T)(1.0 / (c->hs[lv] * c->hs[lv])), L[lv]};
+        }
+        a.lev[0].L.b = const_cast<T *>(b);
+        a.lev[0].L.p = p;
+        const LevelArrays<T> &Lc = L[c->nlev - 1];
+        CK(mg::launch_tail_down<T>(a, s));
+        CK(mg::launch_coarse_solve<T>(c->ncoarse, c->M, Lc.b, Lc.p, s));
+        CK(mg::launch_tail_up<T>(a, s));
         return MG_OK;
     }
     const T h2 = (T)(c->hs[l] * c->hs[l]);
@@ -569,9 +601,10 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
         if (l > 0)
             CK(mg::launch_restrict_coeffs(c->dims[l - 1], c->L64[l - 1].bx, c->L64[l - 1].by, c->L64[l - 1].bz,
                                           c->L64[l].bx, c->L64[l].by, c->L64[l].bz, s));
-        // the finest level's diagonal (CG operator) comes out of the same pass
-        CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv,
-                                       l == 0 ? c->kdiag : nullptr, s));
+        // the finest level's CG operator (scaled coefficients and diagonal) comes out of the same pass
+        const bool op = l == 0 && c->kop.dinv;
+        CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv, s,
+                                       op ? &c->kop : nullptr, 1.0 / (c->hs[0] * c->hs[0])));
     }
     CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
     // coarsest operator to the host
@@ -680,7 +713,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             it++;
             {
                 ProfScope ps(c, MG_PROF_APPLY, true);
-                CK(mg::launch_pcg_apply(d, ih2, c->L64[0], c->kdiag, c->kd, c->kq, c->partials, c->dscal, s));
+                CK(mg::launch_pcg_apply(d, c->kop, c->kd, c->kq, c->partials, c->dscal, s));
             }
             std::swap(e_cur, e_old);
             std::swap(sc_cur, sc_old);
@@ -748,6 +781,7 @@ void mg_default_opts(mg_opts *o)
     o->smoother = 0;
     o->krylov = 0;
     o->coarse_graph = 1;
+    o->coarse_tail = 1;
 }
 
 const char *mg_last_error(void) { return g_err.c_str(); }
@@ -789,7 +823,8 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
-        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1)
+        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1 ||
+        o.coarse_tail < 0 || o.coarse_tail > 1)
         return fail(MG_ERR_ARG, "mg_setup: invalid options");
 
     mg_ctx *c = new mg_ctx();
@@ -841,7 +876,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (c->o.krylov) {
         const size_t n0 = c->dims[0].n();
         st = c->alloc(&c->kr, n0);
-        if (st == MG_OK) st = c->alloc(&c->kdiag, n0);
+        if (st == MG_OK) st = level_alloc<double>(c, c->kop, n0, false);
         if (st == MG_OK) st = c->alloc(&c->kd, n0);
         if (st == MG_OK) st = c->alloc(&c->kq, n0);
         if (st == MG_OK && c->o.prec == MG_MIXED) st = c->alloc(&c->ke_alt, n0);

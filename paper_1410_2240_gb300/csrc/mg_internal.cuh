@@ -64,11 +64,28 @@ struct Split {
     int nx = 0, ny = 0;
 };
 
+// The coarse tail: levels lev[0] (the largest) .. lev[nlev-1] (the coarsest) of the hierarchy,
+// run by one CTA.  Each level's b and p are the ones a V-cycle on it would receive.
+constexpr int kTailMaxLevels = 8;
+template <typename T>
+struct TailLevel {
+    int nx, ny, nz;
+    T h2, ih2;
+    LevelArrays<T> L;
+};
+template <typename T>
+struct TailArgs {
+    int nlev, nu1, nu2;
+    TailLevel<T> lev[kTailMaxLevels];
+};
+
 // ---- kernel launchers (mg_kernels.cu); all stream-ordered, return cudaError_t of the launch ----
 cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
                                double *bx, double *by, double *bz, cudaStream_t s);
+// op (optional): also write the CG operator's arrays scaled by `scale` (op->dinv = the scaled sum)
 template <typename T>
-cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, T *diag, cudaStream_t s);
+cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s,
+                            const LevelArrays<T> *op = nullptr, T scale = T(1));
 cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s);
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
@@ -96,6 +113,12 @@ template <typename T>
 cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp = {});
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s);
+// the coarse tail's descent (pre-smoothing, restriction down to lev[nlev-1].b) and ascent
+// (prolongation of lev[nlev-1].p, post-smoothing up to lev[0].p); the coarsest solve runs between
+template <typename T>
+cudaError_t launch_tail_down(const TailArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_tail_up(const TailArgs<T> &a, cudaStream_t s);
 
 // reductions and fine-level helpers (FP64)
 cudaError_t launch_count_live(Dims d, const double *dinv, double *partials, double *dscal, cudaStream_t s);
@@ -123,8 +146,9 @@ cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const 
 template <typename Z>
 cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s,
                            Split sp = {});
-cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
-                             double *q, double *partials, double *dscal, cudaStream_t s);
+// op: face coefficients and diagonal pre-scaled by h^-2 (op.dinv holds the scaled diagonal)
+cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double *dv, double *q, double *partials,
+                             double *dscal, cudaStream_t s);
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
                               double *partials, double *dscal, int scale_slot, cudaStream_t s, Split sp = {});
 

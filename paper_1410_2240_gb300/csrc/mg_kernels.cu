@@ -169,10 +169,11 @@ __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__
 }
 
 // dinv = 1 / (sum of the six face coefficients), summed x-, x+, y-, y+, z-, z+; 0 if none is
-// open.  diag (optional) = the sum itself.  kRun cells per thread with the divisor memo above.
+// open.  Optionally (op != null) the CG operator's arrays scaled by `scale` = h^-2: op->dinv =
+// scale * sum, op->bx/by/bz = scale * the faces.  kRun cells per thread with the divisor memo above.
 template <typename T>
 __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, const T *__restrict__ by,
-                           const T *__restrict__ bz, T *__restrict__ dinv, T *__restrict__ diag)
+                           const T *__restrict__ bz, T *__restrict__ dinv, LevelArrays<T> op, T scale)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
@@ -189,8 +190,13 @@ __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, con
         s += (j < ny - 1) ? by[c + nx] : T(0);
         s += bz_lo;
         s += bz_hi;
+        if (op.dinv) {
+            op.dinv[c] = s * scale;
+            op.bx[c] = bx[c] * scale;
+            op.by[c] = by[c] * scale;
+            op.bz[c] = bz_lo * scale;
+        }
         bz_lo = bz_hi;
-        if (diag) diag[c] = s;
         T q = T(0);
         if (s > T(0)) {
             if (!same_bits(s, s_last)) {
@@ -242,13 +248,11 @@ __device__ __forceinline__ T inv_diag(T stored, T bxl, T bxh, T byl, T byh, T bz
 //     p_c = dinv_c * (sum_f beta_f p_nb - h^2 b_c),  sum order x-,x+,y-,y+,z-,z+,
 // products accumulated with fused multiply-adds in that order.
 // ---------------------------------------------------------------------------
+// one cell's update (shared by k_smooth and the coarse tail, so both round alike)
 template <typename T>
-__global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T *__restrict__ b,
-                         T *__restrict__ p, int colour, int z0)
+__device__ __forceinline__ void smooth_cell(int i, int j, int k, int nx, int ny, int nz, T h2, const LevelArrays<T> &L,
+                                            const T *b, T *p)
 {
-    const int j = blockIdx.y, k = blockIdx.z + z0;
-    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
-    if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     T s = T(0);
@@ -262,6 +266,16 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
     if (k > 0) s = fma(bzl, p[c - sxy], s);
     if (k < nz - 1) s = fma(bzh, p[c + sxy], s);
     p[c] = inv_diag<T>(sizeof(T) == 8 ? L.dinv[c] : T(0), bxl, bxh, byl, byh, bzl, bzh) * fma(-h2, b[c], s);
+}
+
+template <typename T>
+__global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T *__restrict__ b,
+                         T *__restrict__ p, int colour, int z0)
+{
+    const int j = blockIdx.y, k = blockIdx.z + z0;
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
+    if (i >= nx) return;
+    smooth_cell<T>(i, j, k, nx, ny, nz, h2, L, b, p);
 }
 
 // Colour-split layout (Split in mg_internal.cuh): slot of natural cell c in a row of parity
@@ -310,8 +324,7 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
 template <typename T>
 __device__ __forceinline__ T residual_at(int i, int j, int k, size_t c, int nx, int ny, int nz, size_t sxy, T ih2,
-                                         const LevelArrays<T> &L, const T *__restrict__ b,
-                                         const T *__restrict__ p)
+                                         const LevelArrays<T> &L, const T *b, const T *p)
 {
     const T pc = p[c];
     T s = T(0);
@@ -345,12 +358,10 @@ __device__ __forceinline__ double residual64_at(int i, int j, int k, size_t c, i
 
 // Residual and cell-centred full weighting: coarse b = mean of the 8 children's residuals.
 template <typename T>
-__global__ void k_resid_restrict(int nx, int ny, int nz, T ih2, LevelArrays<T> L, const T *__restrict__ b,
-                                 const T *__restrict__ p, T *__restrict__ bc)
+__device__ __forceinline__ void restrict_cell(int I, int J, int K, int nx, int ny, int nz, T ih2,
+                                              const LevelArrays<T> &L, const T *b, const T *p, T *bc)
 {
     const int NX = nx / 2, NY = ny / 2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
-    if (I >= NX) return;
     const size_t sxy = (size_t)nx * ny;
     T s = T(0);
 #pragma unroll
@@ -364,6 +375,15 @@ __global__ void k_resid_restrict(int nx, int ny, int nz, T ih2, LevelArrays<T> L
                 s += residual_at<T>(i, j, k, c, nx, ny, nz, sxy, ih2, L, b, p);
             }
     bc[((size_t)K * NY + J) * NX + I] = T(0.125) * s;
+}
+
+template <typename T>
+__global__ void k_resid_restrict(int nx, int ny, int nz, T ih2, LevelArrays<T> L, const T *__restrict__ b,
+                                 const T *__restrict__ p, T *__restrict__ bc)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= nx / 2) return;
+    restrict_cell<T>(I, J, K, nx, ny, nz, ih2, L, b, p, bc);
 }
 
 template <typename T> struct Pair;
@@ -462,6 +482,41 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
 // bound by memory latency).  A child's 8 products w_z w_y w_x e are summed with fma, z outermost
 // and x innermost, the parent before the neighbour on each axis.  p and dinv are aligned to a
 // pair (16-byte aligned arrays, even nx).
+// the trilinear corrections of coarse cell (I,J,K)'s 8 children, corr[dz][dy][dx]
+template <typename T>
+__device__ __forceinline__ void prolong_corr(int I, int J, int K, int NX, int NY, int NZ, const T *ec, T corr[2][2][2])
+{
+    // neighbourhood index 0 = lower neighbour (clamped), 1 = parent, 2 = upper neighbour (clamped)
+    const int Is[3] = {max(I - 1, 0), I, min(I + 1, NX - 1)};
+    const int Js[3] = {max(J - 1, 0), J, min(J + 1, NY - 1)};
+    const int Ks[3] = {max(K - 1, 0), K, min(K + 1, NZ - 1)};
+    T e[3][3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) e[a][bb][d] = ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]];
+    const T w[2] = {T(0.75), T(0.25)};
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                // parent first, then the neighbour on the child's side
+                const int ka[2] = {1, dz ? 2 : 0}, jb[2] = {1, dy ? 2 : 0}, id[2] = {1, dx ? 2 : 0};
+                T s = T(0);
+#pragma unroll
+                for (int a = 0; a < 2; a++)
+#pragma unroll
+                    for (int bb = 0; bb < 2; bb++)
+#pragma unroll
+                        for (int d = 0; d < 2; d++) s = fma(w[a] * w[bb] * w[d], e[ka[a]][jb[bb]][id[d]], s);
+                corr[dz][dy][dx] = s;
+            }
+}
+
 template <typename T, bool SPLIT>
 __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, const T *__restrict__ dinv,
                           T *__restrict__ p, size_t half)
@@ -470,10 +525,6 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
     const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
     if (I >= NX) return;
-    // neighbourhood index 0 = lower neighbour (clamped), 1 = parent, 2 = upper neighbour (clamped)
-    const int Is[3] = {max(I - 1, 0), I, min(I + 1, NX - 1)};
-    const int Js[3] = {max(J - 1, 0), J, min(J + 1, NY - 1)};
-    const int Ks[3] = {max(K - 1, 0), K, min(K + 1, NZ - 1)};
     P2 dv[2][2], pv[2][2];
 #pragma unroll
     for (int dz = 0; dz < 2; dz++)
@@ -490,14 +541,8 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
                 pv[dz][dy] = *reinterpret_cast<const P2 *>(p + c);
             }
         }
-    T e[3][3][3];
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int bb = 0; bb < 3; bb++)
-#pragma unroll
-            for (int d = 0; d < 3; d++) e[a][bb][d] = ec[((size_t)Ks[a] * NY + Js[bb]) * NX + Is[d]];
-    const T w[2] = {T(0.75), T(0.25)};
+    T corr[2][2][2];
+    prolong_corr<T>(I, J, K, NX, NY, NZ, ec, corr);
 #pragma unroll
     for (int dz = 0; dz < 2; dz++)
 #pragma unroll
@@ -505,18 +550,9 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
             T out[2];
 #pragma unroll
             for (int dx = 0; dx < 2; dx++) {
-                // parent first, then the neighbour on the child's side
-                const int ka[2] = {1, dz ? 2 : 0}, jb[2] = {1, dy ? 2 : 0}, id[2] = {1, dx ? 2 : 0};
-                T s = T(0);
-#pragma unroll
-                for (int a = 0; a < 2; a++)
-#pragma unroll
-                    for (int bb = 0; bb < 2; bb++)
-#pragma unroll
-                        for (int d = 0; d < 2; d++) s = fma(w[a] * w[bb] * w[d], e[ka[a]][jb[bb]][id[d]], s);
                 const T dval = dx ? dv[dz][dy].y : dv[dz][dy].x;
                 const T pold = dx ? pv[dz][dy].y : pv[dz][dy].x;
-                out[dx] = zero_bits(dval) ? pold : pold + s;
+                out[dx] = zero_bits(dval) ? pold : pold + corr[dz][dy][dx];
             }
             const size_t c = ((size_t)(2 * K + dz) * ny + (2 * J + dy)) * nx + 2 * I;
             if (SPLIT) {
@@ -656,6 +692,96 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ M, const T *__r
         for (int q = lane; q < n; q += 32) s = fma(row[q], sb[q], s);
         s = warp_sum(s);
         if (lane == 0) e[r] = (T)s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse tail.  On the smallest levels (a few thousand cells) every colour pass, restriction and
+// prolongation is a launch far longer than its work.  One CTA runs them in sequence instead,
+// phases separated by __syncthreads (a level's fields stay in the SM's L1 between phases).  The
+// per-cell arithmetic is the per-pass kernels' own (smooth_cell, restrict_cell, prolong_corr) and
+// every cell of a pass is independent of the others, so the results are identical.  The fields
+// are written and read within the kernel, so they are read through plain pointers (never the
+// read-only path).
+// ---------------------------------------------------------------------------
+constexpr int kTailThreads = 512;
+
+template <typename T>
+__device__ void tail_colour(const TailLevel<T> &v, int colour)
+{
+    const int hx = (v.nx + 1) / 2, total = hx * v.ny * v.nz;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int u = t % hx, jk = t / hx, j = jk % v.ny, k = jk / v.ny;
+        const int i = 2 * u + ((j + k + colour) & 1);
+        if (i < v.nx) smooth_cell<T>(i, j, k, v.nx, v.ny, v.nz, v.h2, v.L, v.L.b, v.L.p);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tail_restrict(const TailLevel<T> &f, T *bc)
+{
+    const int NX = f.nx / 2, NY = f.ny / 2, total = NX * NY * (f.nz / 2);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int I = t % NX, JK = t / NX, J = JK % NY, K = JK / NY;
+        restrict_cell<T>(I, J, K, f.nx, f.ny, f.nz, f.ih2, f.L, f.L.b, f.L.p, bc);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tail_prolong(const TailLevel<T> &f, const T *ec)
+{
+    const int NX = f.nx / 2, NY = f.ny / 2, NZ = f.nz / 2, total = NX * NY * NZ;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int I = t % NX, JK = t / NX, J = JK % NY, K = JK / NY;
+        T corr[2][2][2];
+        prolong_corr<T>(I, J, K, NX, NY, NZ, ec, corr);
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 2; dx++) {
+                    const size_t c = ((size_t)(2 * K + dz) * f.ny + (2 * J + dy)) * f.nx + 2 * I + dx;
+                    if (!zero_bits(f.L.dinv[c])) f.L.p[c] = f.L.p[c] + corr[dz][dy][dx];
+                }
+    }
+    __syncthreads();
+}
+
+// descent: on each level but the coarsest, zero p (below the first), nu1 sweeps red then
+// black, residual restricted to the next level's b
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_tail_down(TailArgs<T> a)
+{
+    for (int l = 0; l < a.nlev - 1; l++) {
+        const TailLevel<T> v = a.lev[l];
+        if (l > 0) {
+            const int n = v.nx * v.ny * v.nz;
+            for (int t = threadIdx.x; t < n; t += blockDim.x) v.L.p[t] = T(0);
+            __syncthreads();
+        }
+        for (int it = 0; it < a.nu1; it++) {
+            tail_colour<T>(v, 0);
+            tail_colour<T>(v, 1);
+        }
+        tail_restrict<T>(v, a.lev[l + 1].L.b);
+    }
+}
+
+// ascent: from the level above the coarsest up, prolong the coarser correction, nu2 sweeps
+// black then red
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_tail_up(TailArgs<T> a)
+{
+    for (int l = a.nlev - 2; l >= 0; l--) {
+        const TailLevel<T> v = a.lev[l];
+        tail_prolong<T>(v, a.lev[l + 1].L.p);
+        for (int it = 0; it < a.nu2; it++) {
+            tail_colour<T>(v, 1);
+            tail_colour<T>(v, 0);
+        }
     }
 }
 
@@ -1035,11 +1161,12 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
 
 __global__ void k_pcg_shift_rz(double *dscal) { dscal[S_RZ] = dscal[S_RZN]; }
 
-// q = A d and <d, q>, with A d = h^-2 (sum_f beta_f d_nb - diag d_c): 8 FP64 operations per cell
-// instead of 14 for the difference form.  Its rounding error is larger for smooth d (relative
-// ~1e-12 at 256^3), which only perturbs the recursive residual; convergence is confirmed on the
-// true residual in difference form.
-__global__ void k_pcg_apply(int nx, int ny, int nz, double ih2, LevelArrays<double> L, const double *__restrict__ diag,
+// q = A d and <d, q>, with A d = sum_f (h^-2 beta_f) d_nb - (h^-2 diag) d_c on arrays pre-scaled
+// by h^-2 (L, diag; exact for a power-of-two h): 8 FP64 operations per cell instead of 15 for the
+// difference form.  Its rounding error is larger for smooth d (relative ~1e-12 at 256^3), which
+// only perturbs the recursive residual; convergence is confirmed on the true residual in
+// difference form.
+__global__ void k_pcg_apply(int nx, int ny, int nz, LevelArrays<double> L, const double *__restrict__ diag,
                             const double *__restrict__ d, double *__restrict__ q, double *__restrict__ partials)
 {
     const unsigned n = (unsigned)nx * ny * nz;
@@ -1056,7 +1183,7 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, double ih2, LevelArrays<doub
         if (j < ny - 1) s = fma(L.by[idx + nx], d[idx + nx], s);
         if (k > 0) s = fma(L.bz[idx], d[idx - sxy], s);
         if (k < nz - 1) s = fma(L.bz[idx + sxy], d[idx + sxy], s);
-        const double qv = s * ih2;
+        const double qv = s;
         q[idx] = qv;
         dq = fma(dc, qv, dq);
     }
@@ -1152,16 +1279,18 @@ cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, 
 }
 
 template <typename T>
-cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, T *diag, cudaStream_t s)
+cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s,
+                            const LevelArrays<T> *op, T scale)
 {
     note_launch();
-    k_diag_inv<T><<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv, diag);
+    k_diag_inv<T><<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv,
+                                                                      op ? *op : LevelArrays<T>{}, scale);
     return cudaGetLastError();
 }
-template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *, double *,
-                                             cudaStream_t);
-template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, float *,
-                                            cudaStream_t);
+template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *,
+                                             cudaStream_t, const LevelArrays<double> *, double);
+template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, cudaStream_t,
+                                            const LevelArrays<float> *, float);
 
 cudaError_t launch_restrict_coeffs(Dims f, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s)
@@ -1275,6 +1404,27 @@ cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaSt
                                                                                                                 e);
     return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_tail_down(const TailArgs<T> &a, cudaStream_t s)
+{
+    if (a.nlev < 2 || a.nlev > kTailMaxLevels) return cudaErrorInvalidValue;
+    note_launch();
+    k_tail_down<T><<<1, kTailThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_tail_up(const TailArgs<T> &a, cudaStream_t s)
+{
+    if (a.nlev < 2 || a.nlev > kTailMaxLevels) return cudaErrorInvalidValue;
+    note_launch();
+    k_tail_up<T><<<1, kTailThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_tail_down<double>(const TailArgs<double> &, cudaStream_t);
+template cudaError_t launch_tail_down<float>(const TailArgs<float> &, cudaStream_t);
+template cudaError_t launch_tail_up<double>(const TailArgs<double> &, cudaStream_t);
+template cudaError_t launch_tail_up<float>(const TailArgs<float> &, cudaStream_t);
+
 template cudaError_t launch_coarse_solve<double>(int, const double *, const double *, double *, cudaStream_t);
 template cudaError_t launch_coarse_solve<float>(int, const double *, const float *, float *, cudaStream_t);
 
@@ -1455,12 +1605,12 @@ cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int s
 template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, cudaStream_t, Split);
 template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, cudaStream_t, Split);
 
-cudaError_t launch_pcg_apply(Dims d, double ih2, const LevelArrays<double> &L, const double *diag, const double *dv,
-                             double *q, double *partials, double *dscal, cudaStream_t s)
+cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double *dv, double *q, double *partials,
+                             double *dscal, cudaStream_t s)
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_pcg_apply<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, diag, dv, q, partials);
+    k_pcg_apply<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, op, op.dinv, dv, q, partials);
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_SIGMA, -1);
     return cudaGetLastError();

@@ -253,6 +253,40 @@ def test_pcg_projection_and_adjoint(mgp):
         assert np.abs(a - b).max() <= 1e-8 * max(np.abs(b).max(), 1.0)
 
 
+TAIL_CASES = {
+    "c2_64": lambda: synth.case_c2(64),
+    "ragged_160x32x32": lambda: synth.small_case(160, 32, 32, solid="ellipsoid", seed=41),
+    "aniso_64x32x16": lambda: synth.small_case(64, 32, 16, solid="ellipsoid", seed=43),
+    "c3_256": lambda: synth.case_c3(256),
+}
+
+
+@pytest.mark.parametrize("name", list(TAIL_CASES))
+def test_coarse_tail_identical_to_launches(mgp, name):
+    """Running the smallest levels in one CTA (two launches around the coarsest solve) gives the
+    same V-cycles (FP64) and the same mixed solves (FP32 cycles, stationary and CG) bit for bit as
+    a launch per pass, with and without the coarse-grid graph."""
+    case = TAIL_CASES[name]()
+    beta = mgp.face_coeffs(dev(case.phi), case.h, None if case.solid is None else dev(case.solid, dtype=torch.uint8),
+                           rho_air=case.lam)
+    rhs = mgp.Context(beta, case.h).divergence(faces_dev(case.u_star))
+    p = {}
+    for tail in (0, 1):
+        ctx = mgp.Context(beta, case.h, coarse_tail=tail)
+        q = torch.zeros_like(rhs)
+        for _ in range(2):
+            ctx.vcycle(rhs - rhs.mean(), q)
+        p[tail] = q
+    assert torch.equal(p[0], p[1])
+    for kw in ({"krylov": 0}, {"krylov": 1, "inner_cycles": 2}, {"krylov": 1, "coarse_graph": 0}):
+        res = []
+        for tail in (0, 1):
+            ctx = mgp.Context(beta, case.h, prec="mixed", coarse_tail=tail, **kw)
+            q, st = ctx.solve(rhs, tol=1e-10)
+            res.append((q, st.cycles))
+        assert res[0][1] == res[1][1] and torch.equal(res[0][0], res[1][0]), kw
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_coarse_graph_identical_to_launches(mgp, prec):
     """Replaying the coarse-grid correction as a CUDA graph changes nothing."""
