@@ -46,12 +46,12 @@ B_VCYCLE32 = 145.0    # V(2,2), all levels, FP32: (4 sweeps x 24 + residual/rest
 B_VCYCLE64 = 322.0    # V(2,2), all levels, FP64
 B_RESID64 = 48.0      # FP64 residual + norm (p, b, bx, by, bz read; dinv mask)
 B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
-SWEEP_KERNEL = {0: "k_smooth_split x2 colour passes, colour-split p and b",
-                1: "k_smooth_split x2 colour passes, colour-split p and b",
+SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
+                1: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
-# DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split colour
-# passes) from an ncu capture of this workload (profiles/k_smooth_split_256_colour_pass.md)
-SWEEP_TRAFFIC_256 = 268.456960e6 + 26.637056e6 + 268.452352e6 + 27.134208e6
+# DRAM bytes of one finest-grid FP32 sweep of the default smoother (two colour passes) from an ncu
+# capture of this workload; None until the current kernel has been captured
+SWEEP_TRAFFIC_256 = None
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))
 

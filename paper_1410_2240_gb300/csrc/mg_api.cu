@@ -77,6 +77,7 @@ struct mg_ctx {
     // layout of the finest FP32 iterate / right-hand side (L32[0].p, L32[0].b, ke_alt): colour-split
     // for the per-colour smoother in mixed precision, natural otherwise
     mg::Split split0;
+    float *urow0 = nullptr;  // uniform-row values of the finest FP32 level (with split0)
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
     double *qbuf = nullptr;     // adjoint solution when the caller passes none
@@ -399,6 +400,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const bool fine = (l == 0);
     const bool fused = use_fused<T>(c, l) && palt_of<T>(c, l) != nullptr;
     const mg::Split sp = (sizeof(T) == 4 && l == 0) ? c->split0 : mg::Split{};
+    const float *urow = (sizeof(T) == 4 && l == 0) ? c->urow0 : nullptr;
     T *cur = p, *alt = palt_of<T>(c, l);
     // one red-black sweep, `first` colour first
     auto sweep = [&](int first) -> int {
@@ -411,8 +413,8 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
             std::swap(cur, alt);
         } else if (sp.half) {
             if constexpr (std::is_same<T, float>::value) {
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s));
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow));
             }
         } else {
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
@@ -424,7 +426,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const LevelArrays<T> &C = L[l + 1];
     {
         ProfScope ps(c, MG_PROF_RESTRICT, fine);
-        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s, sp));
+        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s, sp, urow));
     }
     {
         ProfScope ps(c, MG_PROF_COARSE, fine);
@@ -628,6 +630,8 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
             CK(mg::launch_cast_f32(n, c->L64[l].bz, c->L32[l].bz, s));
             CK(mg::launch_cast_f32(n, c->L64[l].dinv, c->L32[l].dinv, s));
         }
+        if (c->urow0)
+            CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s));
     }
     CK(cudaStreamSynchronize(s));  // M's host staging buffer must outlive the copy
     return MG_OK;
@@ -871,6 +875,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (c->o.prec == MG_MIXED) {
         c->L32.resize(c->nlev);
         for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<float>(c, c->L32[l], c->dims[l].n(), true);
+        if (st == MG_OK && c->split0.half) st = c->alloc(&c->urow0, (size_t)c->dims[0].ny * c->dims[0].nz);
         if (st != MG_OK) return bail(st);
     }
     if (c->o.krylov) {

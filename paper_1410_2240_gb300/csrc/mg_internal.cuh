@@ -93,8 +93,12 @@ cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_
 template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
                           int z0 = 0, int z1 = -1);
-// one colour of a red-black sweep on the colour-split layout (FP32, all dims even)
+// one colour of a red-black sweep on the colour-split layout (FP32, all dims even); urow (optional):
+// the level's uniform-row values (launch_uniform_rows)
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
+                                cudaStream_t s, const float *urow = nullptr);
+// urow[k*ny + j] = v if every face around row (j,k) but its two x-walls equals v, else 0
+cudaError_t launch_uniform_rows(Dims d, const float *bx, const float *by, const float *bz, float *urow,
                                 cudaStream_t s);
 // FP32 fused sweep with TMA-staged planes (mg_sweep_tma.cu)
 bool tma_sweep_supported(Dims d);
@@ -108,7 +112,7 @@ cudaError_t launch_rb_sweep(Dims d, T h2, const LevelArrays<T> &L, const T *b, c
 // b and p of the fine level in the layout sp (FP32 only may be split); bc natural
 template <typename T>
 cudaError_t launch_resid_restrict(Dims fine, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
-                                  cudaStream_t s, Split sp = {});
+                                  cudaStream_t s, Split sp = {}, const float *urow = nullptr);
 template <typename T>
 cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp = {});
 template <typename T>

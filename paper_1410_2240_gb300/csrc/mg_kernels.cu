@@ -291,13 +291,42 @@ __device__ __forceinline__ int row_parity(unsigned c, int nx, int ny)
     return (int)((row % (unsigned)ny + row / (unsigned)ny) & 1u);
 }
 
+// Uniform rows.  Away from the interface and the body, every face coefficient around an x-row of
+// cells holds one value (pure air or pure water).  urow[k*ny + j] = that value v when every face
+// of every cell of row (j,k) except the two x-walls (bx at i = 0 and the high face of i = nx-1,
+// both walls, stored as 0) equals v bitwise, else 0; one warp per row.  A pass that reads urow[r]
+// != 0 takes its face values from it instead of loading them: the same values, so the same results.
+__global__ void k_uniform_rows(int nx, int ny, int nz, const float *__restrict__ bx, const float *__restrict__ by,
+                               const float *__restrict__ bz, float *__restrict__ urow)
+{
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * warps + (threadIdx.x >> 5);
+    if (r >= ny * nz) return;
+    const int j = r % ny, k = r / ny;
+    const size_t sxy = (size_t)nx * ny, c0 = (size_t)r * nx;
+    const float v = by[c0];
+    const int vb = __float_as_int(v);
+    bool ok = v > 0.f && j < ny - 1 && k < nz - 1;
+    if (ok)  // warp-uniform; the loads of a lane's cells are independent of one another
+        for (int i = lane; i < nx; i += 32) {
+            const size_t c = c0 + i;
+            const bool cell = (i == 0 || __float_as_int(bx[c]) == vb) & (__float_as_int(by[c]) == vb) &
+                              (__float_as_int(by[c + nx]) == vb) & (__float_as_int(bz[c]) == vb) &
+                              (__float_as_int(bz[c + sxy]) == vb);
+            ok = ok & cell;
+        }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) urow[r] = ok ? v : 0.f;
+}
+
 // One colour of red-black Gauss-Seidel on the colour-split layout (FP32, all dims even): the
 // cell's six neighbours are the other colour's slots m-1+(i&1), m+(i&1), m -+ nx/2, m -+ nx*ny/2
 // (m = c >> 1), read contiguously; b and the result are the own colour's slot m.  A pass moves
-// the face coefficients, half of p and half of b instead of all of p and b.  Same arithmetic, in
-// the same order, as k_smooth<float>.
+// the face coefficients (none on uniform rows), half of p and half of b instead of all of p and
+// b.  Same arithmetic, in the same order, as k_smooth<float>.  Used where nx % 8 != 0
+// (k_smooth_split4 otherwise).
 __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
-                               float *__restrict__ p, int colour)
+                               float *__restrict__ p, int colour, const float *__restrict__ urow)
 {
     const int j = blockIdx.y, k = blockIdx.z;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
@@ -307,18 +336,114 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
     const size_t m = c >> 1, hx = nx / 2, hxy = sxy / 2;
     const float *__restrict__ o = p + (colour ? 0 : half);  // the other colour
     const int odd = i & 1;
-    float s = 0.f;
-    const float bxl = L.bx[c], bxh = (i < nx - 1) ? L.bx[c + 1] : 0.f;
-    const float byl = L.by[c], byh = (j < ny - 1) ? L.by[c + nx] : 0.f;
-    const float bzl = L.bz[c], bzh = (k < nz - 1) ? L.bz[c + sxy] : 0.f;
-    if (i > 0) s = fmaf(bxl, o[m - 1 + odd], s);
-    if (i < nx - 1) s = fmaf(bxh, o[m + odd], s);
-    if (j > 0) s = fmaf(byl, o[m - hx], s);
-    if (j < ny - 1) s = fmaf(byh, o[m + hx], s);
-    if (k > 0) s = fmaf(bzl, o[m - hxy], s);
-    if (k < nz - 1) s = fmaf(bzh, o[m + hxy], s);
     const size_t own = (colour ? half : 0) + m;
-    p[own] = inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, b[own], s);
+    // the neighbours and b are loaded before the row's uniform value is known, so a uniform row
+    // waits for one memory round trip, not two
+    const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
+    const float pxm = i > 0 ? o[m - 1 + odd] : 0.f, pxp = i < nx - 1 ? o[m + odd] : 0.f;
+    const float pym = j > 0 ? o[m - hx] : 0.f, pyp = j < ny - 1 ? o[m + hx] : 0.f;
+    const float pzm = k > 0 ? o[m - hxy] : 0.f, pzp = k < nz - 1 ? o[m + hxy] : 0.f;
+    const float bv = b[own];
+    float bxl, bxh, byl, byh, bzl, bzh;
+    if (v != 0.f) {  // uniform row: the stored values, x-walls 0
+        bxl = i > 0 ? v : 0.f;
+        bxh = i < nx - 1 ? v : 0.f;
+        byl = byh = bzl = bzh = v;
+    } else {
+        bxl = L.bx[c];
+        bxh = (i < nx - 1) ? L.bx[c + 1] : 0.f;
+        byl = L.by[c];
+        byh = (j < ny - 1) ? L.by[c + nx] : 0.f;
+        bzl = L.bz[c];
+        bzh = (k < nz - 1) ? L.bz[c + sxy] : 0.f;
+    }
+    float s = 0.f;
+    if (i > 0) s = fmaf(bxl, pxm, s);
+    if (i < nx - 1) s = fmaf(bxh, pxp, s);
+    if (j > 0) s = fmaf(byl, pym, s);
+    if (j < ny - 1) s = fmaf(byh, pyp, s);
+    if (k > 0) s = fmaf(bzl, pzm, s);
+    if (k < nz - 1) s = fmaf(bzh, pzp, s);
+    p[own] = inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, bv, s);
+}
+
+// The same colour pass, four consecutive cells of the colour per thread (nx % 8 == 0): the cells'
+// slots mb..mb+3 are float4-aligned in the colour-split arrays, so the x-neighbours (one float4
+// and one scalar), the y and z neighbours, b and the results move as float4; on rows that are not
+// uniform the faces come as float4 pairs from which each cell takes its own.  Four independent
+// updates per thread keep more loads in flight than one, which the pass needs once uniform rows
+// have removed most of its bytes.  Each cell's arithmetic is k_smooth_split's, in its order.
+// OFF = (j + k + colour) & 1, the x offset of the colour in the row (uniform across a warp).
+template <int OFF>
+__device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, const LevelArrays<float> &L,
+                                            const float *__restrict__ b, float *__restrict__ p, int colour, float v,
+                                            int g, int j, int k)
+{
+    const int G = nx / 8;
+    const size_t sxy = (size_t)nx * ny, half = sxy * nz / 2, hx = nx / 2, hxy = sxy / 2;
+    const size_t mb = ((size_t)k * sxy + (size_t)j * nx) / 2 + 4 * g;
+    const float *__restrict__ o = p + (colour ? 0 : half);
+    float *own = p + (colour ? half : 0);
+    const float *bo = b + (colour ? half : 0);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 ox = *reinterpret_cast<const float4 *>(o + mb);
+    const float oxe = OFF ? ((g < G - 1) ? o[mb + 4] : 0.f) : ((g > 0) ? o[mb - 1] : 0.f);
+    const float4 oym = j > 0 ? *reinterpret_cast<const float4 *>(o + mb - hx) : zero4;
+    const float4 oyp = j < ny - 1 ? *reinterpret_cast<const float4 *>(o + mb + hx) : zero4;
+    const float4 ozm = k > 0 ? *reinterpret_cast<const float4 *>(o + mb - hxy) : zero4;
+    const float4 ozp = k < nz - 1 ? *reinterpret_cast<const float4 *>(o + mb + hxy) : zero4;
+    const float4 bv = *reinterpret_cast<const float4 *>(bo + mb);
+    const float xs[6] = {OFF ? 0.f : oxe, ox.x, ox.y, ox.z, ox.w, OFF ? oxe : 0.f};  // slots mb-1 .. mb+4
+    const float oy0[4] = {oym.x, oym.y, oym.z, oym.w}, oy1[4] = {oyp.x, oyp.y, oyp.z, oyp.w};
+    const float oz0[4] = {ozm.x, ozm.y, ozm.z, ozm.w}, oz1[4] = {ozp.x, ozp.y, ozp.z, ozp.w};
+    const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+    const size_t c0 = 2 * mb;
+    float fbx[9], fby[8], fbyh[8], fbz[8], fbzh[8];
+    auto ld8 = [](const float *a, float *d) {
+        const float4 u = *reinterpret_cast<const float4 *>(a), w = *reinterpret_cast<const float4 *>(a + 4);
+        d[0] = u.x; d[1] = u.y; d[2] = u.z; d[3] = u.w; d[4] = w.x; d[5] = w.y; d[6] = w.z; d[7] = w.w;
+    };
+    if (v == 0.f) {
+        ld8(L.bx + c0, fbx);
+        fbx[8] = (OFF && 8 * g + 7 < nx - 1) ? L.bx[c0 + 8] : 0.f;
+        ld8(L.by + c0, fby);
+        if (j < ny - 1) ld8(L.by + c0 + nx, fbyh); else for (int q = 0; q < 8; q++) fbyh[q] = 0.f;
+        ld8(L.bz + c0, fbz);
+        if (k < nz - 1) ld8(L.bz + c0 + sxy, fbzh); else for (int q = 0; q < 8; q++) fbzh[q] = 0.f;
+    }
+    float out[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int i = 8 * g + 2 * t + OFF;
+        const int e = 2 * t + OFF;
+        float bxl, bxh, byl, byh, bzl, bzh;
+        if (v != 0.f) {
+            bxl = i > 0 ? v : 0.f; bxh = i < nx - 1 ? v : 0.f; byl = byh = bzl = bzh = v;
+        } else {
+            bxl = fbx[e]; bxh = i < nx - 1 ? fbx[e + 1] : 0.f;
+            byl = fby[e]; byh = fbyh[e]; bzl = fbz[e]; bzh = fbzh[e];
+        }
+        const float pxm = xs[t + OFF], pxp = xs[t + 1 + OFF];  // slots mb+t-1+OFF, mb+t+OFF
+        float s = 0.f;
+        if (i > 0) s = fmaf(bxl, pxm, s);
+        if (i < nx - 1) s = fmaf(bxh, pxp, s);
+        if (j > 0) s = fmaf(byl, oy0[t], s);
+        if (j < ny - 1) s = fmaf(byh, oy1[t], s);
+        if (k > 0) s = fmaf(bzl, oz0[t], s);
+        if (k < nz - 1) s = fmaf(bzh, oz1[t], s);
+        out[t] = inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, bb[t], s);
+    }
+    *reinterpret_cast<float4 *>(own + mb) = make_float4(out[0], out[1], out[2], out[3]);
+}
+__global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
+                         float *__restrict__ p, int colour, const float *__restrict__ urow)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (g >= nx / 8 || j >= ny) return;
+    const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
+    if ((j + k + colour) & 1) split4_body<1>(nx, ny, nz, h2, L, b, p, colour, v, g, j, k);
+    else split4_body<0>(nx, ny, nz, h2, L, b, p, colour, v, g, j, k);
 }
 
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
@@ -399,7 +524,7 @@ template <> struct Pair<double> { using type = double2; };
 template <bool SPLIT>
 __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelArrays<float> L,
                                        const float *__restrict__ b, const float *__restrict__ p,
-                                       float *__restrict__ bc, size_t half)
+                                       float *__restrict__ bc, size_t half, const float *__restrict__ urow)
 {
     const int NX = nx / 2, NY = ny / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
@@ -423,6 +548,15 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
     float pxm[2][2], pxp[2][2], fxp[2][2];
     float2 fy[2][3], fz[2][3];      // fy[dk][row j0, j0+1, j0+2], fz[dj][plane k0, k0+1, k0+2]
     float2 pym[2], pyp[2], pzm[2], pzp[2];  // pym[dk] = p(j0-1, k0+dk) ...; pzm[dj] = p(j0+dj, k0-1) ...
+    // the four fine rows uniform with one value: every face this cell reads is that value (the
+    // uniform rows' y+ and z+ faces included), x-walls 0
+    float v = 0.f;
+    if (urow) {
+        const float u00 = urow[(size_t)k0 * ny + j0], u10 = urow[(size_t)k0 * ny + j0 + 1];
+        const float u01 = urow[(size_t)(k0 + 1) * ny + j0], u11 = urow[(size_t)(k0 + 1) * ny + j0 + 1];
+        if (u00 != 0.f && u00 == u10 && u00 == u01 && u00 == u11) v = u00;
+    }
+    const float2 v2 = make_float2(v, v);
 #pragma unroll
     for (int dk = 0; dk < 2; dk++)
 #pragma unroll
@@ -431,24 +565,37 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
             const int q = par(j0 + dj, k0 + dk);
             pc[dj][dk] = ldf2(p, c, q);
             bb[dj][dk] = ldf2(b, c, q);
-            fx[dj][dk] = ld2(L.bx, c);
             pxm[dj][dk] = i0 > 0 ? ldf(p, c - 1, q) : 0.f;
             pxp[dj][dk] = xhi ? ldf(p, c + 2, q) : 0.f;
-            fxp[dj][dk] = xhi ? L.bx[c + 2] : 0.f;
+            if (v != 0.f) {
+                fx[dj][dk] = make_float2(i0 > 0 ? v : 0.f, v);
+                fxp[dj][dk] = xhi ? v : 0.f;
+            } else {
+                fx[dj][dk] = ld2(L.bx, c);
+                fxp[dj][dk] = xhi ? L.bx[c + 2] : 0.f;
+            }
         }
 #pragma unroll
     for (int dk = 0; dk < 2; dk++) {
-        fy[dk][0] = ld2(L.by, row(j0, k0 + dk));
-        fy[dk][1] = ld2(L.by, row(j0 + 1, k0 + dk));
-        fy[dk][2] = yhi ? ld2(L.by, row(j0 + 2, k0 + dk)) : zero2;
+        if (v != 0.f) {
+            fy[dk][0] = fy[dk][1] = fy[dk][2] = v2;
+        } else {
+            fy[dk][0] = ld2(L.by, row(j0, k0 + dk));
+            fy[dk][1] = ld2(L.by, row(j0 + 1, k0 + dk));
+            fy[dk][2] = yhi ? ld2(L.by, row(j0 + 2, k0 + dk)) : zero2;
+        }
         pym[dk] = ylo ? ldf2(p, row(j0 - 1, k0 + dk), par(j0 - 1, k0 + dk)) : zero2;
         pyp[dk] = yhi ? ldf2(p, row(j0 + 2, k0 + dk), par(j0 + 2, k0 + dk)) : zero2;
     }
 #pragma unroll
     for (int dj = 0; dj < 2; dj++) {
-        fz[dj][0] = ld2(L.bz, row(j0 + dj, k0));
-        fz[dj][1] = ld2(L.bz, row(j0 + dj, k0 + 1));
-        fz[dj][2] = zhi ? ld2(L.bz, row(j0 + dj, k0 + 2)) : zero2;
+        if (v != 0.f) {
+            fz[dj][0] = fz[dj][1] = fz[dj][2] = v2;
+        } else {
+            fz[dj][0] = ld2(L.bz, row(j0 + dj, k0));
+            fz[dj][1] = ld2(L.bz, row(j0 + dj, k0 + 1));
+            fz[dj][2] = zhi ? ld2(L.bz, row(j0 + dj, k0 + 2)) : zero2;
+        }
         pzm[dj] = zlo ? ldf2(p, row(j0 + dj, k0 - 1), par(j0 + dj, k0 - 1)) : zero2;
         pzp[dj] = zhi ? ldf2(p, row(j0 + dj, k0 + 2), par(j0 + dj, k0 + 2)) : zero2;
     }
@@ -1325,34 +1472,51 @@ template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> 
                                           cudaStream_t, int, int);
 
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s)
+                                cudaStream_t s, const float *urow)
 {
     note_launch();
-    k_smooth_split<<<row_grid(d.nx / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour);
+    if (d.nx % 8 == 0) {  // four cells per thread, blocks of 32 threads x 4 rows
+        const int G = d.nx / 8;
+        k_smooth_split4<<<dim3((G + 31) / 32, (d.ny + 3) / 4, d.nz), dim3(32, 4), 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p,
+                                                                                         colour, urow);
+    } else {
+        k_smooth_split<<<row_grid(d.nx / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour,
+                                                                              urow);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uniform_rows(Dims d, const float *bx, const float *by, const float *bz, float *urow,
+                                cudaStream_t s)
+{
+    const int rows = d.ny * d.nz, warps = 8;
+    note_launch();
+    k_uniform_rows<<<(rows + warps - 1) / warps, 32 * warps, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, urow);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
-                                  cudaStream_t s, Split sp)
+                                  cudaStream_t s, Split sp, const float *urow)
 {
     note_launch();
     const dim3 g = row_grid(f.nx / 2, f.ny / 2, f.nz / 2);
     if constexpr (std::is_same<T, float>::value) {
         if (sp.half)
-            k_resid_restrict_pairs<true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half);
+            k_resid_restrict_pairs<true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half, urow);
         else
-            k_resid_restrict_pairs<false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0);
+            k_resid_restrict_pairs<false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0, urow);
     } else {
+        if (urow) return cudaErrorInvalidValue;  // uniform rows describe FP32 coefficients
         if (sp.half) return cudaErrorInvalidValue;  // FP64 fields are never split
         k_resid_restrict<T><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc);
     }
     return cudaGetLastError();
 }
 template cudaError_t launch_resid_restrict<double>(Dims, double, const LevelArrays<double> &, const double *,
-                                                   const double *, double *, cudaStream_t, Split);
+                                                   const double *, double *, cudaStream_t, Split, const float *);
 template cudaError_t launch_resid_restrict<float>(Dims, float, const LevelArrays<float> &, const float *,
-                                                  const float *, float *, cudaStream_t, Split);
+                                                  const float *, float *, cudaStream_t, Split, const float *);
 
 template <typename T>
 cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp)
