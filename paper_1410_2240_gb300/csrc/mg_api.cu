@@ -362,7 +362,7 @@ template <typename T>
 int tail_start(const mg_ctx *c)
 {
     if (!c->o.coarse_tail) return -1;
-    for (int l = 1; l + 1 < c->nlev && l - 1 < mg::kTailMaxLevels; l++)
+    for (int l = 1; l + 1 < c->nlev; l++)
         if (c->dims[l].n() * 6 * sizeof(T) <= kTailBytes && c->nlev - l <= mg::kTailMaxLevels) return l;
     return -1;
 }
@@ -853,7 +853,8 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     // the finest FP32 fields are colour-split when its sweeps are colour passes; a hierarchy of
     // two or more levels has even dims on the finest
     if (c->o.prec == MG_MIXED && c->o.smoother <= 1 && c->nlev >= 2)
-        c->split0 = mg::Split{c->dims[0].n() / 2, c->dims[0].nx, c->dims[0].ny};
+        c->split0 = mg::Split{c->dims[0].n() / 2, c->dims[0].nx, c->dims[0].ny, mg::make_fastdiv(c->dims[0].nx),
+                              mg::make_fastdiv(c->dims[0].ny)};
     const Dims dc = c->dims.back();
     if ((long long)dc.n() > o.coarse_max_cells)
         return bail(fail(MG_ERR_ARG, "mg_setup: coarsest grid %dx%dx%d has %zu cells > coarse_max_cells=%d", dc.nx,

@@ -55,6 +55,21 @@ void note_kernel_launch();
 // set the message mg_last_error() returns on this thread
 void set_last_error(const char *msg);
 
+// Division of 32-bit unsigned integers by a divisor fixed for a launch: a multiply-high, a
+// subtraction, an addition and two shifts instead of an emulated division (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI 1994, the round-up
+// method; exact for every dividend below 2^32).
+struct FastDiv {
+    unsigned mult = 0, s1 = 0, s2 = 0;
+};
+inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned l = 0;
+    while ((1ull << l) < d) l++;  // l = ceil(log2 d)
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{(unsigned)m, l < 1 ? l : 1u, l > 1 ? l - 1 : 0u};
+}
+
 // Layout of the finest level's FP32 iterate and right-hand side.  half == 0: natural C order.
 // half == n / 2 (all dims even): colour-split, the cells of colour (i + j + k) & 1 == 0 in
 // [0, half) and of colour 1 in [half, n), cell c at slot c >> 1 of its colour's half.  Face
@@ -62,6 +77,7 @@ void set_last_error(const char *msg);
 struct Split {
     size_t half = 0;
     int nx = 0, ny = 0;
+    FastDiv fnx, fny;  // division by nx and ny (the row and plane of a natural index)
 };
 
 // The coarse tail: levels lev[0] (the largest) .. lev[nlev-1] (the coarsest) of the hierarchy,

@@ -284,11 +284,16 @@ __device__ __forceinline__ size_t split_slot(size_t c, int q, size_t half)
 {
     return (((int)(c & 1) ^ q) ? half : 0) + (c >> 1);
 }
-// parity (j + k) & 1 of the row holding natural index c
-__device__ __forceinline__ int row_parity(unsigned c, int nx, int ny)
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
 {
-    const unsigned row = c / (unsigned)nx;
-    return (int)((row % (unsigned)ny + row / (unsigned)ny) & 1u);
+    const unsigned t = __umulhi(n, f.mult);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+// parity (j + k) & 1 of the row holding natural index c
+__device__ __forceinline__ int row_parity(unsigned c, const Split &sp)
+{
+    const unsigned row = fdiv(c, sp.fnx), k = fdiv(row, sp.fny), j = row - k * (unsigned)sp.ny;
+    return (int)((j + k) & 1u);
 }
 
 // Uniform rows.  Away from the interface and the body, every face coefficient around an x-row of
@@ -1052,11 +1057,11 @@ __global__ void k_scale_from_nb2(double *dscal, int slot)
 // p += scale * e32 (the FP32 cycle leaves e32 = 0 on dead cells, so no mask is read); e32 in
 // the layout (half, nx, ny)
 __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *__restrict__ p,
-                             const double *__restrict__ dscal, int scale_slot, size_t half, int nx, int ny)
+                             const double *__restrict__ dscal, int scale_slot, Split sp)
 {
     const double s = dscal[scale_slot];
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const size_t e = half ? split_slot(idx, row_parity(idx, nx, ny), half) : idx;
+        const size_t e = sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx;
         p[idx] = fma(s, (double)e32[e], p[idx]);
     }
 }
@@ -1134,7 +1139,8 @@ __device__ __forceinline__ void adj_face(double b, double pc, double pn, double 
         const double gq = div_h(__dsub_rn(qc, qn), h, inv_h, pow2);
         const double gp = div_h(__dsub_rn(pc, pn), h, inv_h, pow2);
         gu = __dsub_rn(w, gq);
-        gb = __dmul_rn(__dmul_rn(dt, gp), __dsub_rn(gq, w));
+        // (Gq - w) is -gu exactly: a rounded difference changes sign with its operands' order
+        gb = __dmul_rn(__dmul_rn(dt, gp), -gu);
     } else {
         gu = w;
         gb = 0.0;
@@ -1283,7 +1289,7 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
 // d = sz * Z + beta d,  beta = (<r,z> - <r,z_old>) / <r_old, z_old>  (first: beta = 0)
 template <typename Z>
 __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, const double *__restrict__ dscal,
-                          int sz_slot, int first, size_t half, int nx, int ny)
+                          int sz_slot, int first, Split sp)
 {
     const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
     const double beta = first ? 0.0 : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ];
@@ -1291,10 +1297,10 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
     double2 *d2 = reinterpret_cast<double2 *>(d);
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
         size_t i0 = 2 * v, i1 = 2 * v + 1;
-        if (half) {  // colour-split Z: the pair's colours sit at slot v of each half
-            const int q = row_parity(2 * v, nx, ny);
-            i0 = (q ? half : 0) + v;
-            i1 = (q ? 0 : half) + v;
+        if (sp.half) {  // colour-split Z: the pair's colours sit at slot v of each half
+            const int q = row_parity(2 * v, sp);
+            i0 = (q ? sp.half : 0) + v;
+            i1 = (q ? 0 : sp.half) + v;
         }
         const double z0 = (double)z[i0], z1 = (double)z[i1];
         double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
@@ -1345,8 +1351,7 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, LevelArrays<double> L, const
 // scale = RMS of the previous residual (written to scale_slot).  Two elements per iteration.
 __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
                              double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
-                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, size_t half,
-                             int nx, int ny)
+                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, Split sp)
 {
     const double alpha = dscal[S_RZ] / dscal[S_SIGMA];
     double inv_scale = 1.0;
@@ -1375,10 +1380,10 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
         rv2[v] = rv;
         if (r32) {
             const float r0 = (float)rv.x * inv_scale32, r1 = (float)rv.y * inv_scale32;
-            if (half) {  // colour-split r32: the pair's colours at slot v of each half
-                const int qp = row_parity(2 * v, nx, ny);
-                r32[(qp ? half : 0) + v] = r0;
-                r32[(qp ? 0 : half) + v] = r1;
+            if (sp.half) {  // colour-split r32: the pair's colours at slot v of each half
+                const int qp = row_parity(2 * v, sp);
+                r32[(qp ? sp.half : 0) + v] = r0;
+                r32[(qp ? 0 : sp.half) + v] = r1;
             } else {
                 r32v[v] = make_float2(r0, r1);
             }
@@ -1659,8 +1664,7 @@ cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, doub
 {
     note_launch();
     (void)dinv;
-    k_accumulate<<<red_grid(d.n()), kRedThreads, 0, s>>>((unsigned)d.n(), e32, p, dscal, scale_slot, sp.half, d.nx,
-                                                          d.ny);
+    k_accumulate<<<red_grid(d.n()), kRedThreads, 0, s>>>((unsigned)d.n(), e32, p, dscal, scale_slot, sp);
     return cudaGetLastError();
 }
 
@@ -1761,7 +1765,7 @@ cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int s
 {
     if (sp.half && sizeof(Z) != 4) return cudaErrorInvalidValue;  // FP64 fields are never split
     note_launch();
-    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, first, sp.half, sp.nx, sp.ny);
+    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, first, sp);
     note_launch();
     k_pcg_shift_rz<<<1, 1, 0, s>>>(dscal);
     return cudaGetLastError();
@@ -1785,8 +1789,7 @@ cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, doubl
 {
     const unsigned g = red_grid(n);
     note_launch();
-    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, partials, sp.half, sp.nx,
-                                           sp.ny);
+    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, partials, sp);
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, -1);
     return cudaGetLastError();
