@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--pcg-scaling", action="store_true",
+                    help="instead of the benchmark: iterations and solve time of Jacobi-preconditioned CG and of "
+                         "multigrid (stationary, and preconditioning CG) on one geometry at 64^3, 128^3, 256^3")
     ap.add_argument("--no-kernel-times", action="store_true",
                     help="skip the profiled run behind kernel_ms and roofline (for ncu captures)")
     ap.add_argument("--inner", type=int, default=2,
@@ -510,9 +513,43 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def pcg_scaling(args):
+    """The Poisson-solver section's comparison of diagonally preconditioned CG with multigrid:
+    iterations to relative residual 1e-10 and solve time (CUDA events inside the library, the
+    second of two solves) per method and resolution, one JSON line."""
+    import torch
+    import __graft_entry__
+    from paper_1410_2240_gb300 import synth
+    __graft_entry__.build()
+    from paper_1410_2240_gb300 import mgproj
+    dev = lambda a, dt=torch.float64: torch.from_numpy(a).to(device="cuda", dtype=dt)
+    methods = (("jacobi_pcg_fp64", dict(krylov=1, precond=1, max_cycles=200000)),
+               ("mg_vcycles_fp64", dict(krylov=0)),
+               ("mg_pcg_fp64", dict(krylov=1, inner_cycles=1)),
+               ("mg_pcg_mixed", dict(krylov=1, inner_cycles=2, prec="mixed")))
+    rows = []
+    for n in (64, 128, 256):
+        case = synth.case_c2(n, geom_seed=2, field_seed=3)
+        beta = mgproj.face_coeffs(dev(case.phi), case.h, dev(case.solid, torch.uint8), rho_air=case.lam)
+        rhs = mgproj.Context(beta, case.h).divergence(tuple(dev(x) for x in case.u_star))
+        for name, kw in methods:
+            ctx = mgproj.Context(beta, case.h, **kw)
+            for _ in range(2):
+                _, st = ctx.solve(rhs, tol=TOL)
+            rows.append({"n": n, "method": name, "iterations": st.cycles, "solve_ms": st.ms_solve,
+                         "rel_resid": st.rel_resid})
+            del ctx
+            torch.cuda.empty_cache()
+    print(json.dumps({"experiment": "jacobi-preconditioned CG vs multigrid, iterations and solve time",
+                      "workload": "unit cube, 4-mode free surface + ellipsoid (the 256^3 benchmark geometry), "
+                                  "rho_air/rho_water 1e-3", "tol": TOL, "rows": rows}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.pcg_scaling:
+        pcg_scaling(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

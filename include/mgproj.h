@@ -100,6 +100,10 @@ typedef struct {
                              thousand cells) are smoothed, restricted and prolonged by one CTA in
                              two launches around the coarsest solve instead of a launch per pass;
                              0: a launch per pass.  Identical results [1] */
+    int precond;          /* preconditioner of the conjugate gradients (krylov = 1): 0 inner_cycles
+                             multigrid V-cycles; 1 Jacobi (the inverse diagonal, z = D^-1 r; MG_FP64
+                             only), the diagonally preconditioned CG the Poisson-solver section
+                             compares multigrid with [0] */
 } mg_opts;
 
 /* Solve statistics (host struct, filled when non-NULL). */

@@ -663,9 +663,12 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
     int it = 0, status = MG_OK, nhist = 0;
     double rel = 0.0, nb2 = 0.0;
     bool done = false, zeroed = false;
-    // precondition: z = M r (FP64) or e_cur = M (r / scale) (mixed)
+    // precondition: z = M r (FP64) or e_cur = M (r / scale) (mixed); M = V-cycles, or the inverse
+    // diagonal of A (Jacobi: -h^2 dinv)
     auto precondition = [&]() -> int {
-        if (mixed) {
+        if (c->o.precond == 1) {
+            CK(mg::launch_jacobi(n, -c->hs[0] * c->hs[0], c->L64[0].dinv, c->kr, z, s));
+        } else if (mixed) {
             CK(cudaMemsetAsync(e_cur, 0, n * sizeof(float), s));
             for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, e_cur));
         } else {
@@ -786,6 +789,7 @@ void mg_default_opts(mg_opts *o)
     o->krylov = 0;
     o->coarse_graph = 1;
     o->coarse_tail = 1;
+    o->precond = 0;
 }
 
 const char *mg_last_error(void) { return g_err.c_str(); }
@@ -828,7 +832,8 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
         o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1 ||
-        o.coarse_tail < 0 || o.coarse_tail > 1)
+        o.coarse_tail < 0 || o.coarse_tail > 1 || o.precond < 0 || o.precond > 1 ||
+        (o.precond == 1 && (o.krylov != 1 || o.prec != MG_FP64)))
         return fail(MG_ERR_ARG, "mg_setup: invalid options");
 
     mg_ctx *c = new mg_ctx();

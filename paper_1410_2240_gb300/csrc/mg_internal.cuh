@@ -163,6 +163,8 @@ cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, 
                             int sz_slot, int so_slot, cudaStream_t s);
 cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const float *zo, double *partials,
                               double *dscal, int sr_slot, int sz_slot, int so_slot, cudaStream_t s);
+// z = scale * dinv * r (the Jacobi preconditioner of the CG)
+cudaError_t launch_jacobi(size_t n, double scale, const double *dinv, const double *r, double *z, cudaStream_t s);
 template <typename Z>
 cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s,
                            Split sp = {});

@@ -1314,6 +1314,14 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
 
 __global__ void k_pcg_shift_rz(double *dscal) { dscal[S_RZ] = dscal[S_RZN]; }
 
+// Jacobi preconditioner: z = (scale * dinv) * r, dead cells 0
+__global__ void k_jacobi(unsigned n, double scale, const double *__restrict__ dinv, const double *__restrict__ r,
+                         double *__restrict__ z)
+{
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        z[idx] = (scale * dinv[idx]) * r[idx];
+}
+
 // q = A d and <d, q>, with A d = sum_f (h^-2 beta_f) d_nb - (h^-2 diag) d_c on arrays pre-scaled
 // by h^-2 (L, diag; exact for a power-of-two h): 8 FP64 operations per cell instead of 15 for the
 // difference form.  Its rounding error is larger for smooth d (relative ~1e-12 at 256^3), which
@@ -1427,6 +1435,13 @@ cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, 
     note_launch();
     k_face_coeffs<<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, phi, solid, rho_a, drho, bx, by,
                                                                       bz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(size_t n, double scale, const double *dinv, const double *r, double *z, cudaStream_t s)
+{
+    note_launch();
+    k_jacobi<<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, scale, dinv, r, z);
     return cudaGetLastError();
 }
 

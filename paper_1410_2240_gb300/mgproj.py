@@ -42,7 +42,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("coarse_max_cells", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("profile", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("coarse_graph", ctypes.c_int), ("coarse_tail", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("coarse_graph", ctypes.c_int), ("coarse_tail", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

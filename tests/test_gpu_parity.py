@@ -301,3 +301,36 @@ def test_coarse_graph_identical_to_launches(mgp, prec):
         assert torch.equal(p, p2)
         out.append((p, st.cycles))
     assert out[0][1] == out[1][1] and torch.equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_64"])
+def test_jacobi_pcg_matches_oracle(mgp, name):
+    """Diagonally preconditioned CG (the comparison solver of the Poisson-solver section): the
+    oracle's iteration count within 3 at the same tolerance, and its solution to 1e-9."""
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case, krylov=1, precond=1, max_cycles=100000)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = case_rhs(case, beta_o)
+    p_o, it_o = O.cg_solve(beta_o, rhs, case.h, tol=1e-10, max_it=100000)
+    p_ref, _, _ = O.MG(beta_o, case.h, max_coarse=4096).solve(rhs, tol=1e-12, max_cycles=300)
+    p_g, st = ctx.solve(dev(rhs), tol=1e-10)
+    assert it_o > 0 and abs(st.cycles - it_o) <= 3, (st.cycles, it_o)
+    assert rel(host(p_g), p_ref) <= 1e-9
+
+
+def test_jacobi_pcg_grows_with_n_multigrid_does_not(mgp):
+    """The scaling the Poisson-solver section reports: on one geometry at 32^3 and 64^3, the
+    diagonally preconditioned CG needs about twice the iterations at twice the resolution, the
+    multigrid-preconditioned CG about the same number."""
+    its = {}
+    for n in (32, 64):
+        case = synth.case_c2(n)
+        beta = mgp.face_coeffs(dev(case.phi), case.h, dev(case.solid, dtype=torch.uint8), rho_air=case.lam)
+        rhs = mgp.Context(beta, case.h).divergence(faces_dev(case.u_star))
+        for method, kw in (("jacobi", dict(precond=1, max_cycles=100000)), ("mg", dict(inner_cycles=1))):
+            ctx = mgp.Context(beta, case.h, krylov=1, **kw)
+            _, st = ctx.solve(rhs, tol=1e-10)
+            its[method, n] = st.cycles
+    assert its["jacobi", 64] >= 1.5 * its["jacobi", 32], its
+    assert abs(its["mg", 64] - its["mg", 32]) <= 2, its
+    assert its["jacobi", 32] > 3 * its["mg", 32], its
