@@ -113,6 +113,10 @@ def _load(path: Optional[str] = None):
             lib.orc_face_scale.argtypes = [sz, _D, _D, _D, _D, _D, _D, _D, _D, _D]
             lib.orc_gradient.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, _D, _D]
             lib.orc_phi_grad.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, _D, _D]
+            lib.orc_face_open.argtypes = [d, d, d, d]
+            lib.orc_face_open.restype = d
+            lib.orc_face_areas.argtypes = [i, i, i, _D, _D, _D, _D]
+            lib.orc_divergence_area.argtypes = [i, i, i, d, d] + [_D] * 10
             _lib = lib
     return _lib
 
@@ -383,6 +387,81 @@ def project_adjoint(beta, p, w, h, dt=1.0, lam=1e-3, tol=1e-12, method="mg"):
     grad_u = tuple(np.where(b > 0, x - g, x) for b, x, g in zip(beta, w, gq))
     grad_beta = tuple(np.where(b > 0, dt * a * (g - x), 0.0) for b, a, g, x in zip(beta, gp, gq, w))
     grad_phi = phi_grad(beta, grad_beta, lam)
+    return grad_u, grad_beta, grad_phi
+
+
+# ---------------------------------------------------------------------------
+# Fractional face areas (Body Boundary Conditions section, Eq. integral2)
+# ---------------------------------------------------------------------------
+
+def face_open(f00, f10, f01, f11):
+    """Open fraction of one face from its corner values of psi (orc_face_open)."""
+    lib = _load()
+    return lib.orc_face_open(float(f00), float(f10), float(f01), float(f11))
+
+
+def face_areas(psi_nodes):
+    """Open fractions (ax, ay, az) of the low faces from psi at the nodes ((nz+1, ny+1, nx+1)),
+    psi > 0 outside the body; wall faces 0."""
+    lib = _load()
+    psi = _f64(psi_nodes)
+    nz, ny, nx = (s - 1 for s in psi.shape)
+    out = [np.empty((nz, ny, nx)) for _ in range(3)]
+    lib.orc_face_areas(nx, ny, nz, _p(psi), *[_p(o) for o in out])
+    return tuple(out)
+
+
+def area_coeffs(areas, beta):
+    """Operator coefficients of Eq. integral2: area fraction times 1/rho on each face (one rounded
+    product; 0 where the area is 0)."""
+    return tuple(np.where(a > 0, a * b, 0.0) for a, b in zip(areas, beta))
+
+
+def open_mask(areas, beta):
+    """1/rho on the faces with an open area, 0 elsewhere (the correction's coefficient)."""
+    return tuple(np.where(a > 0, b, 0.0) for a, b in zip(areas, beta))
+
+
+def divergence_area(areas, u, h, dt=1.0, v=None):
+    """b = D_a (u - v) / dt (orc_divergence_area); v = None: a static body."""
+    lib = _load()
+    nx, ny, nz = _dims(areas[0])
+    out = np.empty((nz, ny, nx))
+    vv = [None, None, None] if v is None else [_p(_f64(x)) for x in v]
+    lib.orc_divergence_area(nx, ny, nz, h, dt, *[_p(_f64(a)) for a in areas], *[_p(_f64(x)) for x in u],
+                            *vv, _p(out))
+    return out
+
+
+def project_area(phi, areas, u_star, h, dt=1.0, lam=1e-3, tol=1e-12, v=None):
+    """Forward projection with fractional face areas: the operator on area * 1/rho, the
+    right-hand side D_a (u* - v)/dt, the correction with 1/rho on faces of open area.
+    Returns (u, p, beta (1/rho, no solid mask), rhs)."""
+    beta = face_coeffs(phi, None, lam)
+    ce = area_coeffs(areas, beta)
+    rhs = divergence_area(areas, u_star, h, dt, v)
+    p = solve(ce, rhs, h, tol=tol)
+    u = correct(open_mask(areas, beta), p, u_star, h, dt)
+    return u, p, beta, rhs
+
+
+def project_adjoint_area(beta, areas, p, w, h, dt=1.0, lam=1e-3, tol=1e-12):
+    """Backward of project_area for the loss sum(w * u): with B = diag(1/rho), D_a = D diag(a),
+    A = D_a B G, G = -D^T on open faces,
+        grad_u*  = w - a (G q),                 A q = D (B w)
+        grad_beta = dt (G p) (a (G q) - w)      (faces of open area; 0 elsewhere)
+        grad_phi  as for binary faces, from grad_beta.
+    Returns (grad_u_star, grad_beta, grad_phi)."""
+    bo = open_mask(areas, beta)
+    ce = area_coeffs(areas, beta)
+    bw = tuple(b * x for b, x in zip(bo, w))
+    c = divergence(bo, bw, h, 1.0)
+    q = solve(ce, c, h, tol=tol)
+    gq = gradient(bo, q, h)
+    gp = gradient(bo, p, h)
+    grad_u = tuple(np.where(a > 0, x - a * g, x) for a, x, g in zip(areas, w, gq))
+    grad_beta = tuple(np.where(a > 0, dt * gpp * (a * g - x), 0.0) for a, gpp, g, x in zip(areas, gp, gq, w))
+    grad_phi = phi_grad(bo, grad_beta, lam)
     return grad_u, grad_beta, grad_phi
 
 

@@ -11,6 +11,7 @@ import tempfile
 import pytest
 
 import oracle as O
+import test_oracle_areas as T3
 import test_oracle_operator as T1
 import test_oracle_solver as T2
 
@@ -62,6 +63,18 @@ MUTANTS = [
      [lambda: T2.test_pcg_matches_dense_pseudoinverse(1)]),
     ("component search ignores upper z faces", "if (k < nz - 1) { nb[m] = IX(i, j, k + 1); fb[m++] = bz[IX(i, j, k + 1)]; }", "",
      [T1.test_components_counts]),
+    ("triangle open fraction not squared", "return (f * f) / ((f - g1) * (f - g2));", "return f / ((f - g1) * (f - g2));",
+     [T3.test_face_open_closed_forms, T3.test_face_open_matches_brute_force]),
+    ("x-face area takes a corner of the next x plane",
+     "ax[c] = i == 0 ? 0.0 : orc_face_open(PSI(i, j, k), PSI(i, j + 1, k), PSI(i, j, k + 1), PSI(i, j + 1, k + 1));",
+     "ax[c] = i == 0 ? 0.0 : orc_face_open(PSI(i, j, k), PSI(i, j + 1, k), PSI(i + 1, j, k + 1), PSI(i, j + 1, k + 1));",
+     [T3.test_plane_areas_exact, T3.test_sphere_cross_sections]),
+    ("area divergence drops the area of the low x face", "if (ax[c] > 0.0) d -= FLUX(ax, ux, vx, c);",
+     "if (ax[c] > 0.0) d -= ux[c];", [T3.test_area_divergence_composes_with_plain_divergence]),
+    ("area divergence ignores the body velocity",
+     "#define FLUX(arr_a, arr_u, arr_v, idx) ((arr_a)[idx] * ((arr_u)[idx] - ((arr_v) ? (arr_v)[idx] : 0.0)))",
+     "#define FLUX(arr_a, arr_u, arr_v, idx) ((arr_a)[idx] * (arr_u)[idx])",
+     [T3.test_area_divergence_composes_with_plain_divergence]),
 ]
 
 
