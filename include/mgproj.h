@@ -165,6 +165,46 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
 int mg_update(mg_ctx *c, const double *const face_coeffs[3]);
 
 /*
+ * Open-area fractions of the faces from a body given by a signed distance psi
+ * (Body Boundary Conditions section: psi > 0 outside the body, < 0 inside),
+ * the fractional areas of Eq. integral2.  psi_nodes: device, the
+ * (nz+1) x (ny+1) x (nx+1) grid nodes in C order, node (i,j,k) at (i h, j h,
+ * k h).  The paper takes the area calculation from a cited reference; here
+ * each face is split into four triangles about its centre (psi there = the
+ * mean of its four corners), psi is taken as linear on each triangle, and the
+ * face's fraction is the mean of the triangles' areas where psi > 0 (a closed
+ * form per triangle; exact for a planar body).  area_out: device, the three
+ * low-face arrays (layout as for face coefficients), values in [0, 1]; wall
+ * faces 0.  Errors: MG_ERR_ARG for a bad grid or null/unaligned arrays.
+ */
+int mg_face_areas(const mg_grid *g, const double *psi_nodes, double *const area_out[3], void *stream);
+
+/*
+ * Fractional face areas for a context (Eq. integral2 solved by the method of
+ * fractional areas): the face coefficients given to mg_setup / mg_update are
+ * then 1/rho_f, and the operator uses area_f * (1/rho_f) on the finest faces
+ * (the product the Poisson-solver section moves to the coarse grids); a face
+ * is open where that product is > 0.  mg_divergence weights each open face's
+ * flux by its area; mg_correct updates the velocity of open faces with
+ * 1/rho_f; mg_project_adjoint uses the areas in its gradients.  area: device,
+ * three low-face arrays in [0, 1] (mg_face_areas), copied; NULL returns to
+ * whole faces.  Rebuilds the hierarchy (as mg_update).  Cells are not merged:
+ * a cut cell of small open area stays a cell of small coefficients.
+ */
+int mg_set_face_areas(mg_ctx *c, const double *const area[3]);
+
+/*
+ * Body velocity v* on the faces (Eq. bc2), for the body term of Eq. integral2:
+ * mg_divergence and mg_project use u - v on every open face.  For a body
+ * velocity of zero divergence (a rigid motion, sampled at the face centres),
+ * its flux through the body surface inside a cut cell is minus its flux
+ * through the cell's open face parts (Gauss's theorem), so this adds the body
+ * term; in cells the body does not cut, the discrete divergence of a rigid
+ * motion is zero.  v: device, three face arrays, copied; NULL: a static body.
+ */
+int mg_set_body_velocity(mg_ctx *c, const double *const v[3]);
+
+/*
  * Solve A p = b to ||b - A p|| / ||b|| <= tol (multigrid of the Poisson-solver
  * section).  rhs: device, read only; its mean over the fluid cells is removed
  * first (compatibility of the Neumann problem) and isolated cells are ignored.

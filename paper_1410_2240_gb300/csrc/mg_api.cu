@@ -77,6 +77,11 @@ struct mg_ctx {
     // layout of the finest FP32 iterate / right-hand side (L32[0].p, L32[0].b, ke_alt): colour-split
     // for the per-colour smoother in mixed precision, natural otherwise
     mg::Split split0;
+    // fractional face areas (mg_set_face_areas): the open fractions, and 1/rho on the faces as given
+    // to mg_setup / mg_update (the operator then uses area * 1/rho); the body velocity on the faces
+    // (mg_set_body_velocity)
+    bool has_area = false, has_vb = false;
+    LevelArrays<double> karea, kbeta, kvb;
     float *urow0 = nullptr;  // uniform-row values of the finest FP32 level (with split0)
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
@@ -596,9 +601,17 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
     const Dims dc = c->dims.back();
     const size_t n0 = c->dims[0].n();
     CK(cudaMemsetAsync(c->dscal, 0, mg::S_COUNT * sizeof(double), s));
-    CK(cudaMemcpyAsync(c->L64[0].bx, face_coeffs[0], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(c->L64[0].by, face_coeffs[1], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(c->L64[0].bz, face_coeffs[2], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (c->has_area) {  // keep 1/rho; the operator's coefficient is area * 1/rho
+        double *kb[3] = {c->kbeta.bx, c->kbeta.by, c->kbeta.bz};
+        for (int a = 0; a < 3; a++)
+            if (face_coeffs[a] != kb[a])
+                CK(cudaMemcpyAsync(kb[a], face_coeffs[a], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(mg::launch_area_coeffs(n0, c->karea, c->kbeta, c->L64[0], s));
+    } else {
+        CK(cudaMemcpyAsync(c->L64[0].bx, face_coeffs[0], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->L64[0].by, face_coeffs[1], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->L64[0].bz, face_coeffs[2], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     for (int l = 0; l < c->nlev; l++) {
         if (l > 0)
             CK(mg::launch_restrict_coeffs(c->dims[l - 1], c->L64[l - 1].bx, c->L64[l - 1].by, c->L64[l - 1].bz,
@@ -966,7 +979,16 @@ int mg_divergence(mg_ctx *c, const double *const u[3], double dt, double *rhs)
     if (!(dt > 0.0)) return fail(MG_ERR_ARG, "mg_divergence: dt must be > 0");
     if (!aligned16({u[0], u[1], u[2], rhs})) return fail(MG_ERR_ARG, "mg_divergence: arrays must be 16-byte aligned");
     const LevelArrays<double> &L = c->L64[0];
-    CK(mg::launch_divergence(c->dims[0], 1.0 / (dt * c->g.h), L.bx, L.by, L.bz, u[0], u[1], u[2], rhs, c->s));
+    if (c->has_area || c->has_vb) {
+        LevelArrays<double> uu{};
+        uu.bx = const_cast<double *>(u[0]);
+        uu.by = const_cast<double *>(u[1]);
+        uu.bz = const_cast<double *>(u[2]);
+        CK(mg::launch_divergence_area(c->dims[0], 1.0 / (dt * c->g.h), L, c->has_area ? c->karea : LevelArrays<double>{},
+                                      uu, c->has_vb ? c->kvb : LevelArrays<double>{}, rhs, c->s));
+    } else {
+        CK(mg::launch_divergence(c->dims[0], 1.0 / (dt * c->g.h), L.bx, L.by, L.bz, u[0], u[1], u[2], rhs, c->s));
+    }
     return MG_OK;
 }
 
@@ -980,7 +1002,79 @@ int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double
         return fail(MG_ERR_ARG, "mg_correct: arrays must be 16-byte aligned");
     const LevelArrays<double> &L = c->L64[0];
     CK(mg::launch_correct(c->dims[0], dt, c->g.h, L.bx, L.by, L.bz, p, u_star[0], u_star[1], u_star[2], u[0], u[1],
-                          u[2], c->s));
+                          u[2], c->s, c->has_area ? &c->kbeta : nullptr));
+    return MG_OK;
+}
+
+int mg_face_areas(const mg_grid *g, const double *psi_nodes, double *const area_out[3], void *stream)
+{
+    g_err.clear();
+    if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_face_areas: bad grid");
+    if (!psi_nodes || !area_out || !area_out[0] || !area_out[1] || !area_out[2])
+        return fail(MG_ERR_ARG, "mg_face_areas: null pointer");
+    if (!aligned16({psi_nodes, area_out[0], area_out[1], area_out[2]}))
+        return fail(MG_ERR_ARG, "mg_face_areas: arrays must be 16-byte aligned");
+    CK(mg::launch_face_areas(Dims{g->nx, g->ny, g->nz}, psi_nodes, area_out[0], area_out[1], area_out[2],
+                             (cudaStream_t)stream));
+    return MG_OK;
+}
+
+int mg_set_face_areas(mg_ctx *c, const double *const area[3])
+{
+    g_err.clear();
+    if (!c) return fail(MG_ERR_ARG, "mg_set_face_areas: null context");
+    const size_t n0 = c->dims[0].n();
+    if (!area) {
+        if (!c->has_area) return MG_OK;
+        c->has_area = false;
+        const double *kb[3] = {c->kbeta.bx, c->kbeta.by, c->kbeta.bz};
+        return compute_hierarchy(c, kb);
+    }
+    if (!area[0] || !area[1] || !area[2]) return fail(MG_ERR_ARG, "mg_set_face_areas: null face array");
+    if (!aligned16({area[0], area[1], area[2]}))
+        return fail(MG_ERR_ARG, "mg_set_face_areas: arrays must be 16-byte aligned");
+    if (!c->karea.bx) {
+        CKS(c->alloc(&c->karea.bx, n0));
+        CKS(c->alloc(&c->karea.by, n0));
+        CKS(c->alloc(&c->karea.bz, n0));
+        CKS(c->alloc(&c->kbeta.bx, n0));
+        CKS(c->alloc(&c->kbeta.by, n0));
+        CKS(c->alloc(&c->kbeta.bz, n0));
+    }
+    cudaStream_t s = c->s;
+    if (!c->has_area) {  // the coefficients given so far are 1/rho
+        CK(cudaMemcpyAsync(c->kbeta.bx, c->L64[0].bx, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->kbeta.by, c->L64[0].by, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->kbeta.bz, c->L64[0].bz, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaMemcpyAsync(c->karea.bx, area[0], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->karea.by, area[1], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->karea.bz, area[2], n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    c->has_area = true;
+    const double *kb[3] = {c->kbeta.bx, c->kbeta.by, c->kbeta.bz};
+    return compute_hierarchy(c, kb);
+}
+
+int mg_set_body_velocity(mg_ctx *c, const double *const v[3])
+{
+    g_err.clear();
+    if (!c) return fail(MG_ERR_ARG, "mg_set_body_velocity: null context");
+    if (!v) {
+        c->has_vb = false;
+        return MG_OK;
+    }
+    if (!v[0] || !v[1] || !v[2]) return fail(MG_ERR_ARG, "mg_set_body_velocity: null face array");
+    if (!aligned16({v[0], v[1], v[2]})) return fail(MG_ERR_ARG, "mg_set_body_velocity: arrays must be 16-byte aligned");
+    const size_t n0 = c->dims[0].n();
+    if (!c->kvb.bx) {
+        CKS(c->alloc(&c->kvb.bx, n0));
+        CKS(c->alloc(&c->kvb.by, n0));
+        CKS(c->alloc(&c->kvb.bz, n0));
+    }
+    CK(cudaMemcpyAsync(c->kvb.bx, v[0], n0 * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaMemcpyAsync(c->kvb.by, v[1], n0 * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaMemcpyAsync(c->kvb.bz, v[2], n0 * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    c->has_vb = true;
     return MG_OK;
 }
 
@@ -1027,8 +1121,10 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
         CK(cudaMemsetAsync(q, 0, n * sizeof(double), c->s));
     }
     const LevelArrays<double> &L = c->L64[0];
-    // beta * w into grad_u (used as scratch), then c = D(beta w)
-    CK(mg::launch_face_mul(n, L.bx, L.by, L.bz, w[0], w[1], w[2], grad_u[0], grad_u[1], grad_u[2], c->s));
+    // beta * w into grad_u (used as scratch), then c = D(beta w); beta = 1/rho (with fractional areas
+    // the operator's coefficient is area * 1/rho, and D sums the open faces without their areas)
+    const LevelArrays<double> &B = c->has_area ? c->kbeta : L;
+    CK(mg::launch_face_mul(n, B.bx, B.by, B.bz, w[0], w[1], w[2], grad_u[0], grad_u[1], grad_u[2], c->s));
     CK(mg::launch_divergence(c->dims[0], 1.0 / c->g.h, L.bx, L.by, L.bz, grad_u[0], grad_u[1], grad_u[2], c->rhs_tmp,
                              c->s));
     const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, q, tol, stats) : solve_impl(c, c->rhs_tmp, q, tol, stats);
@@ -1038,7 +1134,7 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
     if (grad_beta)
         for (int a = 0; a < 3; a++) gb[a] = grad_beta[a];
     CK(mg::launch_adjoint_faces(c->dims[0], c->g.h, dt, L.bx, L.by, L.bz, p, q, w[0], w[1], w[2], grad_u[0],
-                                grad_u[1], grad_u[2], gb[0], gb[1], gb[2], c->s));
+                                grad_u[1], grad_u[2], gb[0], gb[1], gb[2], c->s, c->has_area ? &c->karea : nullptr));
     g_err = keep;
     return st;
 }

@@ -177,16 +177,27 @@ cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, doubl
 // projection and adjoint
 cudaError_t launch_divergence(Dims d, double scale, const double *bx, const double *by, const double *bz,
                               const double *ux, const double *uy, const double *uz, double *rhs, cudaStream_t s);
+// the face is open where b > 0; val (optional): its coefficient (1/rho) when b holds area * 1/rho
 cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const double *by, const double *bz,
                            const double *p, const double *ux0, const double *uy0, const double *uz0, double *ux,
-                           double *uy, double *uz, cudaStream_t s);
+                           double *uy, double *uz, cudaStream_t s, const LevelArrays<double> *val = nullptr);
+// fractional face areas (open fractions of the low faces) from psi at the (nx+1)(ny+1)(nz+1) nodes
+cudaError_t launch_face_areas(Dims d, const double *psi, double *ax, double *ay, double *az, cudaStream_t s);
+// out = area * beta on faces of open area, 0 elsewhere (bx/by/bz of each)
+cudaError_t launch_area_coeffs(size_t n, const LevelArrays<double> &area, const LevelArrays<double> &beta,
+                               const LevelArrays<double> &out, cudaStream_t s);
+// rhs = scale * sum over open faces (mask > 0) of +-area (u - v); area or v null: 1 or 0
+cudaError_t launch_divergence_area(Dims d, double scale, const LevelArrays<double> &mask,
+                                   const LevelArrays<double> &area, const LevelArrays<double> &u,
+                                   const LevelArrays<double> &v, double *rhs, cudaStream_t s);
 cudaError_t launch_face_mul(size_t n, const double *bx, const double *by, const double *bz, const double *wx,
                             const double *wy, const double *wz, double *ox, double *oy, double *oz,
                             cudaStream_t s);
 cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, const double *by,
                                  const double *bz, const double *p, const double *q, const double *wx,
                                  const double *wy, const double *wz, double *gux, double *guy, double *guz,
-                                 double *gbx, double *gby, double *gbz, cudaStream_t s);
+                                 double *gbx, double *gby, double *gbz, cudaStream_t s,
+                                 const LevelArrays<double> *area = nullptr);
 cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, const double *by, const double *bz,
                             const double *gbx, const double *gby, const double *gbz, double *gphi,
                             cudaStream_t s);

@@ -1088,6 +1088,87 @@ __global__ void k_divergence(int nx, int ny, int nz, double scale, const double 
     rhs[c] = scale * d;
 }
 
+// ---------------------------------------------------------------------------
+// Fractional face areas (Body Boundary Conditions section, Eq. integral2).  psi is given at the
+// nodes ((nz+1) x (ny+1) x (nx+1), > 0 outside the body).  A face is split into four triangles
+// about its centre (psi there = the mean of the four corners), psi is linear on each, and the open
+// fraction is the mean of the triangles' fractions where psi > 0; a triangle with one corner f > 0
+// and two g1, g2 <= 0 has f^2 / ((f - g1)(f - g2)), one with two corners > 0 and one g <= 0 has
+// 1 - g^2 / ((g - f1)(g - f2)).  Each operation rounded separately.
+// ---------------------------------------------------------------------------
+__device__ double tri_open(double a, double b, double c)
+{
+    const bool pa = pos_bits(a), pb = pos_bits(b), pc = pos_bits(c);
+    const int np = (int)pa + (int)pb + (int)pc;
+    if (np == 0) return 0.0;
+    if (np == 3) return 1.0;
+    if (np == 1) {
+        const double f = pa ? a : (pb ? b : c);
+        const double g1 = pa ? b : a, g2 = pc ? b : c;
+        return div_call(__dmul_rn(f, f), __dmul_rn(__dsub_rn(f, g1), __dsub_rn(f, g2)));
+    }
+    const double g = !pa ? a : (!pb ? b : c);
+    const double f1 = !pa ? b : a, f2 = !pc ? b : c;
+    return __dsub_rn(1.0, div_call(__dmul_rn(g, g), __dmul_rn(__dsub_rn(g, f1), __dsub_rn(g, f2))));
+}
+
+// corners in cyclic order around the face: f00, f10, f11, f01
+__device__ double face_open(double f00, double f10, double f01, double f11)
+{
+    const double fc = __dmul_rn(__dadd_rn(__dadd_rn(f00, f10), __dadd_rn(f01, f11)), 0.25);
+    const double t0 = tri_open(f00, f10, fc), t1 = tri_open(f10, f11, fc);
+    const double t2 = tri_open(f11, f01, fc), t3 = tri_open(f01, f00, fc);
+    return __dmul_rn(__dadd_rn(__dadd_rn(__dadd_rn(t0, t1), t2), t3), 0.25);
+}
+
+// open fractions of the low faces of every cell; wall faces 0
+__global__ void k_face_areas(int nx, int ny, int nz, const double *__restrict__ psi, double *__restrict__ ax,
+                             double *__restrict__ ay, double *__restrict__ az)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t NX = (size_t)nx + 1, NXY = NX * ((size_t)ny + 1);
+    auto P = [&](int ii, int jj, int kk) { return psi[(size_t)kk * NXY + (size_t)jj * NX + (size_t)ii]; };
+    const size_t c = ((size_t)k * ny + j) * nx + i;
+    ax[c] = i == 0 ? 0.0 : face_open(P(i, j, k), P(i, j + 1, k), P(i, j, k + 1), P(i, j + 1, k + 1));
+    ay[c] = j == 0 ? 0.0 : face_open(P(i, j, k), P(i + 1, j, k), P(i, j, k + 1), P(i + 1, j, k + 1));
+    az[c] = k == 0 ? 0.0 : face_open(P(i, j, k), P(i + 1, j, k), P(i, j + 1, k), P(i + 1, j + 1, k));
+}
+
+// the operator's coefficient of a face: area * 1/rho where the area is > 0, else 0
+__global__ void k_area_coeffs(size_t n, LevelArrays<double> area, LevelArrays<double> beta, LevelArrays<double> out)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        out.bx[c] = pos_bits(area.bx[c]) ? __dmul_rn(area.bx[c], beta.bx[c]) : 0.0;
+        out.by[c] = pos_bits(area.by[c]) ? __dmul_rn(area.by[c], beta.by[c]) : 0.0;
+        out.bz[c] = pos_bits(area.bz[c]) ? __dmul_rn(area.bz[c], beta.bz[c]) : 0.0;
+    }
+}
+
+// b = scale * sum over the open faces (mask > 0) of +-w_f (u_f - v_f), order x+, x-, y+, y-, z+, z-;
+// w = the face's area (or 1 without areas), v = the body velocity (or none)
+__global__ void k_divergence_area(int nx, int ny, int nz, double scale, LevelArrays<double> mask,
+                                  LevelArrays<double> area, LevelArrays<double> u, LevelArrays<double> v,
+                                  double *__restrict__ rhs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    auto flux = [&](const double *a, const double *uu, const double *vv, size_t f) {
+        const double du = vv ? __dsub_rn(uu[f], vv[f]) : uu[f];
+        return a ? __dmul_rn(a[f], du) : du;
+    };
+    double d = 0.0;
+    if (i < nx - 1 && pos_bits(mask.bx[c + 1])) d = __dadd_rn(d, flux(area.bx, u.bx, v.bx, c + 1));
+    if (pos_bits(mask.bx[c])) d = __dsub_rn(d, flux(area.bx, u.bx, v.bx, c));
+    if (j < ny - 1 && pos_bits(mask.by[c + nx])) d = __dadd_rn(d, flux(area.by, u.by, v.by, c + nx));
+    if (pos_bits(mask.by[c])) d = __dsub_rn(d, flux(area.by, u.by, v.by, c));
+    if (k < nz - 1 && pos_bits(mask.bz[c + sxy])) d = __dadd_rn(d, flux(area.bz, u.bz, v.bz, c + sxy));
+    if (pos_bits(mask.bz[c])) d = __dsub_rn(d, flux(area.bz, u.bz, v.bz, c));
+    rhs[c] = __dmul_rn(scale, d);
+}
+
 // u_f = u*_f - dt beta_f (p_c - p_nb) / h on open low faces; closed faces copy u*.
 // x / h, rounded once: a multiply by 1/h when h is a power of two (then x * (1/h) is exact and
 // equal to the quotient), an IEEE division otherwise
@@ -1096,26 +1177,30 @@ __device__ __forceinline__ double div_h(double x, double h, double inv_h, bool p
     return pow2 ? __dmul_rn(x, inv_h) : div_call(x, h);
 }
 
+// The face is open where b > 0; its coefficient is val (1/rho when b holds area * 1/rho), or b
+// itself when val is null.
 __global__ void k_correct(int nx, int ny, int nz, double dt, double h, double inv_h, int pow2,
                           const double *__restrict__ bx, const double *__restrict__ by, const double *__restrict__ bz,
                           const double *__restrict__ p, const double *ux0, const double *uy0, const double *uz0,
-                          double *ux, double *uy, double *uz)
+                          double *ux, double *uy, double *uz, LevelArrays<double> val)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     const double pc = p[c];
-    double b = bx[c], u = ux0[c];
-    if (i > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
+    double b = bx[c], u = ux0[c], bv = val.bx ? val.bx[c] : b;
+    if (i > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
     ux[c] = u;
     b = by[c];
     u = uy0[c];
-    if (j > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - nx])), h, inv_h, pow2));
+    bv = val.by ? val.by[c] : b;
+    if (j > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - nx])), h, inv_h, pow2));
     uy[c] = u;
     b = bz[c];
     u = uz0[c];
-    if (k > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, b), __dsub_rn(pc, p[c - sxy])), h, inv_h, pow2));
+    bv = val.bz ? val.bz[c] : b;
+    if (k > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - sxy])), h, inv_h, pow2));
     uz[c] = u;
 }
 
@@ -1132,12 +1217,15 @@ __global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double
 }
 
 // grad_u = w - G q (open faces) / w (closed);  grad_beta = dt (G p)((G q) - w) (open) / 0 (closed)
+// a: the face's open area (fractional areas), or null
 __device__ __forceinline__ void adj_face(double b, double pc, double pn, double qc, double qn, double w, double h,
-                                         double inv_h, bool pow2, double dt, double &gu, double &gb)
+                                         double inv_h, bool pow2, double dt, const double *a, size_t c, double &gu,
+                                         double &gb)
 {
     if (pos_bits(b)) {
-        const double gq = div_h(__dsub_rn(qc, qn), h, inv_h, pow2);
+        double gq = div_h(__dsub_rn(qc, qn), h, inv_h, pow2);
         const double gp = div_h(__dsub_rn(pc, pn), h, inv_h, pow2);
+        if (a) gq = __dmul_rn(a[c], gq);
         gu = __dsub_rn(w, gq);
         // (Gq - w) is -gu exactly: a rounded difference changes sign with its operands' order
         gb = __dmul_rn(__dmul_rn(dt, gp), -gu);
@@ -1153,7 +1241,7 @@ __global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double inv_h, 
                                 const double *__restrict__ p, const double *__restrict__ q,
                                 const double *__restrict__ wx, const double *__restrict__ wy,
                                 const double *__restrict__ wz, double *gux, double *guy, double *guz, double *gbx,
-                                double *gby, double *gbz)
+                                double *gby, double *gbz, LevelArrays<double> area)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
@@ -1161,13 +1249,16 @@ __global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double inv_h, 
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     const double pc = p[c], qc = q[c];
     double gu, gb;
-    adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, inv_h, pow2, dt, gu, gb);
+    adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, inv_h, pow2, dt, area.bx, c, gu,
+             gb);
     gux[c] = gu;
     if (gbx) gbx[c] = gb;
-    adj_face(by[c], pc, j > 0 ? p[c - nx] : 0.0, qc, j > 0 ? q[c - nx] : 0.0, wy[c], h, inv_h, pow2, dt, gu, gb);
+    adj_face(by[c], pc, j > 0 ? p[c - nx] : 0.0, qc, j > 0 ? q[c - nx] : 0.0, wy[c], h, inv_h, pow2, dt, area.by, c,
+             gu, gb);
     guy[c] = gu;
     if (gby) gby[c] = gb;
-    adj_face(bz[c], pc, k > 0 ? p[c - sxy] : 0.0, qc, k > 0 ? q[c - sxy] : 0.0, wz[c], h, inv_h, pow2, dt, gu, gb);
+    adj_face(bz[c], pc, k > 0 ? p[c - sxy] : 0.0, qc, k > 0 ? q[c - sxy] : 0.0, wz[c], h, inv_h, pow2, dt, area.bz,
+             c, gu, gb);
     guz[c] = gu;
     if (gbz) gbz[c] = gb;
 }
@@ -1694,13 +1785,39 @@ cudaError_t launch_divergence(Dims d, double scale, const double *bx, const doub
 
 cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const double *by, const double *bz,
                            const double *p, const double *ux0, const double *uy0, const double *uz0, double *ux,
-                           double *uy, double *uz, cudaStream_t s)
+                           double *uy, double *uz, cudaStream_t s, const LevelArrays<double> *val)
 {
     note_launch();
     int ex;
     const bool pow2 = std::frexp(h, &ex) == 0.5;
     k_correct<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, dt, h, 1.0 / h, pow2, bx, by, bz, p,
-                                                                  ux0, uy0, uz0, ux, uy, uz);
+                                                                  ux0, uy0, uz0, ux, uy, uz,
+                                                                  val ? *val : LevelArrays<double>{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_areas(Dims d, const double *psi, double *ax, double *ay, double *az, cudaStream_t s)
+{
+    note_launch();
+    k_face_areas<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, psi, ax, ay, az);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_area_coeffs(size_t n, const LevelArrays<double> &area, const LevelArrays<double> &beta,
+                               const LevelArrays<double> &out, cudaStream_t s)
+{
+    note_launch();
+    k_area_coeffs<<<red_grid(n), kRedThreads, 0, s>>>(n, area, beta, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divergence_area(Dims d, double scale, const LevelArrays<double> &mask,
+                                   const LevelArrays<double> &area, const LevelArrays<double> &u,
+                                   const LevelArrays<double> &v, double *rhs, cudaStream_t s)
+{
+    note_launch();
+    k_divergence_area<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, scale, mask, area, u, v,
+                                                                         rhs);
     return cudaGetLastError();
 }
 
@@ -1715,14 +1832,14 @@ cudaError_t launch_face_mul(size_t n, const double *bx, const double *by, const 
 cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, const double *by, const double *bz,
                                  const double *p, const double *q, const double *wx, const double *wy,
                                  const double *wz, double *gux, double *guy, double *guz, double *gbx, double *gby,
-                                 double *gbz, cudaStream_t s)
+                                 double *gbz, cudaStream_t s, const LevelArrays<double> *area)
 {
     note_launch();
     int ex;
     const bool pow2 = std::frexp(h, &ex) == 0.5;
     k_adjoint_faces<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h, 1.0 / h, pow2, dt, bx, by,
                                                                         bz, p, q, wx, wy, wz, gux, guy, guz, gbx, gby,
-                                                                        gbz);
+                                                                        gbz, area ? *area : LevelArrays<double>{});
     return cudaGetLastError();
 }
 

@@ -75,6 +75,9 @@ _lib.mg_num_levels.argtypes = [_vp]
 _lib.mg_level_dims.argtypes = [_vp, ctypes.c_int, ctypes.c_int * 3]
 _lib.mg_level_array.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp]
 _lib.mg_update.argtypes = [_vp, _PP]
+_lib.mg_face_areas.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _vp]
+_lib.mg_set_face_areas.argtypes = [_vp, _PP]
+_lib.mg_set_body_velocity.argtypes = [_vp, _PP]
 _lib.mg_kernel_launches.restype = ctypes.c_uint64
 _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.mg_profile_reset.argtypes = [_vp]
@@ -92,7 +95,8 @@ def kernel_launches() -> int:
 EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_solve", "mg_vcycle", "mg_divergence",
            "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
            "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset",
-           "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error"]
+           "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error", "mg_face_areas", "mg_set_face_areas",
+           "mg_set_body_velocity"]
 
 
 class MGError(RuntimeError):
@@ -162,6 +166,19 @@ def face_coeffs(phi: torch.Tensor, h: float, solid: Optional[torch.Tensor] = Non
     return out
 
 
+def face_areas(psi_nodes: torch.Tensor, h: float, out=None, stream=None):
+    """mg_face_areas: open-area fractions (ax, ay, az) of the faces from psi at the grid nodes
+    (shape (nz+1, ny+1, nx+1), psi > 0 outside the body)."""
+    nz1, ny1, nx1 = psi_nodes.shape
+    shape = (nz1 - 1, ny1 - 1, nx1 - 1)
+    g = Grid(nx1 - 1, ny1 - 1, nz1 - 1, h)
+    if out is None:
+        out = tuple(torch.empty(shape, dtype=torch.float64, device=psi_nodes.device) for _ in range(3))
+    _check(_lib.mg_face_areas(ctypes.byref(g), _dev(psi_nodes, psi_nodes.shape, name="psi_nodes"),
+                              _faces(out, shape, "area_out"), _stream(stream)))
+    return out
+
+
 def phi_grad(beta: Sequence[torch.Tensor], grad_beta: Sequence[torch.Tensor], h: float, rho_air=1e-3,
              rho_water=1.0, out=None, stream=None):
     """mg_phi_grad: chain rule from face coefficients to phi."""
@@ -206,6 +223,15 @@ class Context:
     def update(self, beta):
         """mg_update: rebuild the hierarchy for new face coefficients (same grid, no allocation)."""
         _check(_lib.mg_update(self._c, _faces(beta, self.shape, "beta")))
+
+    def set_face_areas(self, areas):
+        """mg_set_face_areas: fractional open areas of the faces (None: whole faces); the face
+        coefficients of this context are then 1/rho and the operator uses area * 1/rho."""
+        _check(_lib.mg_set_face_areas(self._c, None if areas is None else _faces(areas, self.shape, "area")))
+
+    def set_body_velocity(self, v):
+        """mg_set_body_velocity: the body velocity on the faces (None: a static body)."""
+        _check(_lib.mg_set_body_velocity(self._c, None if v is None else _faces(v, self.shape, "v")))
 
     def profile_read(self, group):
         n = ctypes.c_int()
