@@ -122,6 +122,17 @@ def ellipsoid_mask(nx, ny, nz, h, centre=(0.5, 0.5, 0.5), semi=(0.3, 0.06, 0.05)
     return np.ascontiguousarray((q <= 1.0).astype(np.uint8))
 
 
+def ellipsoid_psi_nodes(nx, ny, nz, h, centre=(0.5, 0.5, 0.5), semi=(0.3, 0.06, 0.05)) -> np.ndarray:
+    """Level-set of the same ellipsoid at the grid nodes ((nz+1, ny+1, nx+1), node (i,j,k) at
+    (i h, j h, k h)): > 0 outside, < 0 inside, (sqrt(q) - 1) * min(semi) (the distance to the surface
+    near it, up to the ellipsoid's aspect)."""
+    x = (np.arange(nx + 1) * h)[None, None, :]
+    y = (np.arange(ny + 1) * h)[None, :, None]
+    z = (np.arange(nz + 1) * h)[:, None, None]
+    q = ((x - centre[0]) / semi[0]) ** 2 + ((y - centre[1]) / semi[1]) ** 2 + ((z - centre[2]) / semi[2]) ** 2
+    return np.ascontiguousarray((np.sqrt(q) - 1.0) * min(semi))
+
+
 # ---------------------------------------------------------------------------
 # The five workloads
 # ---------------------------------------------------------------------------
