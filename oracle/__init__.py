@@ -117,6 +117,7 @@ def _load(path: Optional[str] = None):
             lib.orc_face_open.restype = d
             lib.orc_face_areas.argtypes = [i, i, i, _D, _D, _D, _D]
             lib.orc_divergence_area.argtypes = [i, i, i, d, d] + [_D] * 10
+            lib.orc_stretched_metrics.argtypes = [i, i, i] + [_D] * 15
             _lib = lib
     return _lib
 
@@ -463,6 +464,38 @@ def project_adjoint_area(beta, areas, p, w, h, dt=1.0, lam=1e-3, tol=1e-12):
     grad_beta = tuple(np.where(a > 0, dt * gpp * (a * g - x), 0.0) for a, gpp, g, x in zip(areas, gp, gq, w))
     grad_phi = phi_grad(bo, grad_beta, lam)
     return grad_u, grad_beta, grad_phi
+
+
+# ---------------------------------------------------------------------------
+# Stretched grids: the index-grid form (unit spacing) of Eq. integral2 times the cell volume
+# ---------------------------------------------------------------------------
+
+def stretched_metrics(hx, hy, hz, beta, frac=None):
+    """(beta_idx, area) of every low face for cell widths hx (nx), hy (ny), hz (nz):
+    beta_idx = beta / (distance between the cell centres), area = the face's two widths times
+    the open fraction (frac, or 1); walls 0.  With these and unit spacing, the operator is
+    area * beta_idx, the divergence the cell volume times b, the correction the physical one."""
+    lib = _load()
+    nx, ny, nz = len(hx), len(hy), len(hz)
+    ob = [np.empty((nz, ny, nx)) for _ in range(3)]
+    ar = [np.empty((nz, ny, nx)) for _ in range(3)]
+    ff = [None, None, None] if frac is None else [_p(_f64(f)) for f in frac]
+    lib.orc_stretched_metrics(nx, ny, nz, _p(_f64(hx)), _p(_f64(hy)), _p(_f64(hz)), *[_p(_f64(b)) for b in beta],
+                              *ff, *[_p(o) for o in ob], *[_p(a) for a in ar])
+    return tuple(ob), tuple(ar)
+
+
+def project_stretched(phi, hx, hy, hz, u_star, dt=1.0, lam=1e-3, tol=1e-12, frac=None, v=None):
+    """Forward projection on a stretched grid: the fractional-area projection on the index grid
+    (unit spacing) with the metrics above.  Returns (u, p, beta_idx, area, rhs) with rhs = the
+    cell volume times b."""
+    beta = face_coeffs(phi, None, lam)
+    bi, area = stretched_metrics(hx, hy, hz, beta, frac)
+    ce = area_coeffs(area, bi)
+    rhs = divergence_area(area, u_star, 1.0, dt, v)
+    p = solve(ce, rhs, 1.0, tol=tol)
+    u = correct(open_mask(area, bi), p, u_star, 1.0, dt)
+    return u, p, bi, area, rhs
 
 
 # ---------------------------------------------------------------------------

@@ -781,6 +781,48 @@ void orc_divergence_area(int nx, int ny, int nz, double h, double dt, const doub
             }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Stretched grids (grids stretched along the Cartesian axes, Numerical      */
+/* efficiency / parallel-computing sections).  Cell widths hx[i], hy[j],      */
+/* hz[k].  Multiplying Eq. integral2 by the cell volume puts it on the index  */
+/* grid (unit spacing) with, for each low face,                               */
+/*   beta_idx = beta / d   (d: distance between the two cell centres)         */
+/*   area     = (the face's two widths) * open fraction (1 without a body)    */
+/* so that the operator is area * beta_idx (the product moved to the coarse   */
+/* grids), the divergence sum(+-area u)/dt is the cell volume times b, and    */
+/* the correction u - dt beta_idx (p_R - p_L) is the physical one.  Wall      */
+/* faces: area 0, beta_idx 0.                                                 */
+/* ------------------------------------------------------------------------- */
+void orc_stretched_metrics(int nx, int ny, int nz, const double *hx, const double *hy, const double *hz,
+                           const double *bx, const double *by, const double *bz, const double *fx, const double *fy,
+                           const double *fz, double *obx, double *oby, double *obz, double *ax, double *ay, double *az)
+{
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t c = IX(i, j, k);
+                if (i == 0) { obx[c] = 0.0; ax[c] = 0.0; }
+                else {
+                    double d = 0.5 * (hx[i - 1] + hx[i]);
+                    obx[c] = bx[c] / d;
+                    ax[c] = (hy[j] * hz[k]) * (fx ? fx[c] : 1.0);
+                }
+                if (j == 0) { oby[c] = 0.0; ay[c] = 0.0; }
+                else {
+                    double d = 0.5 * (hy[j - 1] + hy[j]);
+                    oby[c] = by[c] / d;
+                    ay[c] = (hx[i] * hz[k]) * (fy ? fy[c] : 1.0);
+                }
+                if (k == 0) { obz[c] = 0.0; az[c] = 0.0; }
+                else {
+                    double d = 0.5 * (hz[k - 1] + hz[k]);
+                    obz[c] = bz[c] / d;
+                    az[c] = (hx[i] * hy[j]) * (fz ? fz[c] : 1.0);
+                }
+            }
+}
+
 /* u_f = u*_f - dt beta_f (p_R - p_L) / h on open faces; closed faces keep u*. */
 void orc_correct(int nx, int ny, int nz, double h, double dt, const double *bx, const double *by,
                  const double *bz, const double *p, const double *ux0, const double *uy0,

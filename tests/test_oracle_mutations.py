@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 import test_oracle_areas as T3
+import test_oracle_stretched as T4
 import test_oracle_operator as T1
 import test_oracle_solver as T2
 
@@ -75,6 +76,10 @@ MUTANTS = [
      "#define FLUX(arr_a, arr_u, arr_v, idx) ((arr_a)[idx] * ((arr_u)[idx] - ((arr_v) ? (arr_v)[idx] : 0.0)))",
      "#define FLUX(arr_a, arr_u, arr_v, idx) ((arr_a)[idx] * (arr_u)[idx])",
      [T3.test_area_divergence_composes_with_plain_divergence]),
+    ("stretched z distance is one width", "double d = 0.5 * (hz[k - 1] + hz[k]);", "double d = hz[k];",
+     [T4.test_linear_pressure_face_gradients_exact, T4.test_layered_problem_matches_1d_finite_volumes]),
+    ("stretched z-face area from the wrong widths", "az[c] = (hx[i] * hy[j]) * (fz ? fz[c] : 1.0);",
+     "az[c] = (hx[i] * hz[k]) * (fz ? fz[c] : 1.0);", [T4.test_linear_pressure_face_gradients_exact]),
 ]
 
 
