@@ -205,6 +205,26 @@ int mg_set_face_areas(mg_ctx *c, const double *const area[3]);
 int mg_set_body_velocity(mg_ctx *c, const double *const v[3]);
 
 /*
+ * Stretched grids (grids stretched along the Cartesian axes, as in the
+ * paper's runs): cell widths hx[nx], hy[ny], hz[nz] (device).  Multiplying
+ * Eq. integral2 by the cell volume puts it on the index grid of unit spacing,
+ * with per low face
+ *     beta_out = beta / d   (d: the distance between the two cell centres),
+ *     area_out = the face's two widths * frac (frac: open fractions, or NULL
+ *                for whole faces).
+ * A context built on beta_out with h = 1 and given area_out by
+ * mg_set_face_areas then solves the stretched problem: mg_divergence returns
+ * the cell volume times b, the pressure and mg_correct's velocity are the
+ * physical ones, and the adjoint's face gradient is with respect to beta_out
+ * (divide by d for 1/rho).  g->h is ignored.  beta, frac: device face arrays
+ * (layout as for face coefficients); beta_out, area_out: device, written;
+ * wall faces 0.  Errors: MG_ERR_ARG for a bad grid or null/unaligned arrays.
+ */
+int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, const double *hz,
+                         const double *const beta[3], const double *const frac[3], double *const beta_out[3],
+                         double *const area_out[3], void *stream);
+
+/*
  * Solve A p = b to ||b - A p|| / ||b|| <= tol (multigrid of the Poisson-solver
  * section).  rhs: device, read only; its mean over the fluid cells is removed
  * first (compatibility of the Neumann problem) and isolated cells are ignored.

@@ -1019,6 +1019,35 @@ int mg_face_areas(const mg_grid *g, const double *psi_nodes, double *const area_
     return MG_OK;
 }
 
+int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, const double *hz,
+                         const double *const beta[3], const double *const frac[3], double *const beta_out[3],
+                         double *const area_out[3], void *stream)
+{
+    g_err.clear();
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1 || (double)g->nx * g->ny * g->nz >= 2147483647.0)
+        return fail(MG_ERR_ARG, "mg_stretched_metrics: bad grid");
+    if (!hx || !hy || !hz || !beta || !beta_out || !area_out) return fail(MG_ERR_ARG, "mg_stretched_metrics: null pointer");
+    for (int a = 0; a < 3; a++)
+        if (!beta[a] || !beta_out[a] || !area_out[a] || (frac && !frac[a]))
+            return fail(MG_ERR_ARG, "mg_stretched_metrics: null face array");
+    if (!aligned16({hx, hy, hz, beta[0], beta[1], beta[2], beta_out[0], beta_out[1], beta_out[2], area_out[0],
+                    area_out[1], area_out[2]}) ||
+        (frac && !aligned16({frac[0], frac[1], frac[2]})))
+        return fail(MG_ERR_ARG, "mg_stretched_metrics: arrays must be 16-byte aligned");
+    auto view = [](const double *const x[3]) {
+        LevelArrays<double> v{};
+        if (x) {
+            v.bx = const_cast<double *>(x[0]);
+            v.by = const_cast<double *>(x[1]);
+            v.bz = const_cast<double *>(x[2]);
+        }
+        return v;
+    };
+    CK(mg::launch_stretched_metrics(Dims{g->nx, g->ny, g->nz}, hx, hy, hz, view(beta), view(frac),
+                                    view(beta_out), view(area_out), (cudaStream_t)stream));
+    return MG_OK;
+}
+
 int mg_set_face_areas(mg_ctx *c, const double *const area[3])
 {
     g_err.clear();

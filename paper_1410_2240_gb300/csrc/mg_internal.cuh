@@ -183,6 +183,10 @@ cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const 
                            double *uy, double *uz, cudaStream_t s, const LevelArrays<double> *val = nullptr);
 // fractional face areas (open fractions of the low faces) from psi at the (nx+1)(ny+1)(nz+1) nodes
 cudaError_t launch_face_areas(Dims d, const double *psi, double *ax, double *ay, double *az, cudaStream_t s);
+// stretched-grid metrics: bout = beta / (centre distance), aout = face widths * frac (frac null: 1)
+cudaError_t launch_stretched_metrics(Dims d, const double *hx, const double *hy, const double *hz,
+                                    const LevelArrays<double> &beta, const LevelArrays<double> &frac,
+                                    const LevelArrays<double> &bout, const LevelArrays<double> &aout, cudaStream_t s);
 // out = area * beta on faces of open area, 0 elsewhere (bx/by/bz of each)
 cudaError_t launch_area_coeffs(size_t n, const LevelArrays<double> &area, const LevelArrays<double> &beta,
                                const LevelArrays<double> &out, cudaStream_t s);

@@ -1135,6 +1135,44 @@ __global__ void k_face_areas(int nx, int ny, int nz, const double *__restrict__ 
     az[c] = k == 0 ? 0.0 : face_open(P(i, j, k), P(i + 1, j, k), P(i, j + 1, k), P(i + 1, j + 1, k));
 }
 
+// Stretched grids: cell widths hx[i], hy[j], hz[k].  Eq. integral2 times the cell volume on the
+// index grid (unit spacing): beta_idx = beta / d with d the distance between the two cell centres,
+// area = the face's two widths times the open fraction (frac, or 1); walls 0.  Each operation
+// rounded separately.
+__global__ void k_stretched_metrics(int nx, int ny, int nz, const double *__restrict__ hx,
+                                    const double *__restrict__ hy, const double *__restrict__ hz,
+                                    LevelArrays<double> beta, LevelArrays<double> frac, LevelArrays<double> bout,
+                                    LevelArrays<double> aout)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t c = ((size_t)k * ny + j) * nx + i;
+    if (i == 0) {
+        bout.bx[c] = 0.0;
+        aout.bx[c] = 0.0;
+    } else {
+        const double d = __dmul_rn(0.5, __dadd_rn(hx[i - 1], hx[i]));
+        bout.bx[c] = div_call(beta.bx[c], d);
+        aout.bx[c] = __dmul_rn(__dmul_rn(hy[j], hz[k]), frac.bx ? frac.bx[c] : 1.0);
+    }
+    if (j == 0) {
+        bout.by[c] = 0.0;
+        aout.by[c] = 0.0;
+    } else {
+        const double d = __dmul_rn(0.5, __dadd_rn(hy[j - 1], hy[j]));
+        bout.by[c] = div_call(beta.by[c], d);
+        aout.by[c] = __dmul_rn(__dmul_rn(hx[i], hz[k]), frac.by ? frac.by[c] : 1.0);
+    }
+    if (k == 0) {
+        bout.bz[c] = 0.0;
+        aout.bz[c] = 0.0;
+    } else {
+        const double d = __dmul_rn(0.5, __dadd_rn(hz[k - 1], hz[k]));
+        bout.bz[c] = div_call(beta.bz[c], d);
+        aout.bz[c] = __dmul_rn(__dmul_rn(hx[i], hy[j]), frac.bz ? frac.bz[c] : 1.0);
+    }
+}
+
 // the operator's coefficient of a face: area * 1/rho where the area is > 0, else 0
 __global__ void k_area_coeffs(size_t n, LevelArrays<double> area, LevelArrays<double> beta, LevelArrays<double> out)
 {
@@ -1800,6 +1838,16 @@ cudaError_t launch_face_areas(Dims d, const double *psi, double *ax, double *ay,
 {
     note_launch();
     k_face_areas<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, psi, ax, ay, az);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stretched_metrics(Dims d, const double *hx, const double *hy, const double *hz,
+                                    const LevelArrays<double> &beta, const LevelArrays<double> &frac,
+                                    const LevelArrays<double> &bout, const LevelArrays<double> &aout, cudaStream_t s)
+{
+    note_launch();
+    k_stretched_metrics<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, hx, hy, hz, beta, frac,
+                                                                           bout, aout);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ _lib.mg_update.argtypes = [_vp, _PP]
 _lib.mg_face_areas.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _vp]
 _lib.mg_set_face_areas.argtypes = [_vp, _PP]
 _lib.mg_set_body_velocity.argtypes = [_vp, _PP]
+_lib.mg_stretched_metrics.argtypes = [ctypes.POINTER(Grid), _vp, _vp, _vp, _PP, _PP, _PP, _PP, _vp]
 _lib.mg_kernel_launches.restype = ctypes.c_uint64
 _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.mg_profile_reset.argtypes = [_vp]
@@ -96,7 +97,7 @@ EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_sol
            "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
            "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset",
            "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error", "mg_face_areas", "mg_set_face_areas",
-           "mg_set_body_velocity"]
+           "mg_set_body_velocity", "mg_stretched_metrics"]
 
 
 class MGError(RuntimeError):
@@ -177,6 +178,21 @@ def face_areas(psi_nodes: torch.Tensor, h: float, out=None, stream=None):
     _check(_lib.mg_face_areas(ctypes.byref(g), _dev(psi_nodes, psi_nodes.shape, name="psi_nodes"),
                               _faces(out, shape, "area_out"), _stream(stream)))
     return out
+
+
+def stretched_metrics(hx: torch.Tensor, hy: torch.Tensor, hz: torch.Tensor, beta, frac=None, stream=None):
+    """mg_stretched_metrics: (beta / centre distance, face widths * frac) of every low face for cell
+    widths hx, hy, hz; a context on the first with h = 1 and the second as face areas solves the
+    stretched problem."""
+    shape = (hz.numel(), hy.numel(), hx.numel())
+    g = Grid(shape[2], shape[1], shape[0], 1.0)
+    bo = tuple(torch.empty(shape, dtype=torch.float64, device=hx.device) for _ in range(3))
+    ao = tuple(torch.empty(shape, dtype=torch.float64, device=hx.device) for _ in range(3))
+    _check(_lib.mg_stretched_metrics(ctypes.byref(g), _dev(hx, hx.shape, name="hx"), _dev(hy, hy.shape, name="hy"),
+                                     _dev(hz, hz.shape, name="hz"), _faces(beta, shape, "beta"),
+                                     None if frac is None else _faces(frac, shape, "frac"), _faces(bo, shape, "beta_out"),
+                                     _faces(ao, shape, "area_out"), _stream(stream)))
+    return bo, ao
 
 
 def phi_grad(beta: Sequence[torch.Tensor], grad_beta: Sequence[torch.Tensor], h: float, rho_air=1e-3,
