@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--pcg-scaling", action="store_true",
                     help="instead of the benchmark: iterations and solve time of Jacobi-preconditioned CG and of "
                          "multigrid (stationary, and preconditioning CG) on one geometry at 64^3, 128^3, 256^3")
+    ap.add_argument("--stretched", action="store_true",
+                    help="the 256^3 workload's arrays on a grid stretched in z (widths 3.5:1, finest at z = 0.5)")
     ap.add_argument("--cut-cells", action="store_true",
                     help="the 256^3 workload's ellipsoid as fractional face areas from a level set (no binary mask)")
     ap.add_argument("--no-kernel-times", action="store_true",
@@ -85,7 +87,7 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_name(n, workload="c3", cut_cells=False):
+def workload_name(n, workload="c3", cut_cells=False, stretched=False):
     step = (f"step = face coeffs + hierarchy + projection + adjoint projection + phi chain rule "
             f"(2 solves to rel. resid {TOL:g})")
     if workload == "c4":
@@ -96,11 +98,13 @@ def workload_name(n, workload="c3", cut_cells=False):
                 "0.4x0.05x0.04 with rounded bow, rho ratio 1e-3, u*/w FP32 seed 5 promoted to FP64; " + step)
     body = ("piercing ellipsoid (0.3,0.06,0.05) as fractional face areas from a level set at the nodes"
             if cut_cells else "piercing ellipsoid (0.3,0.06,0.05)")
+    grid = "; grid stretched in z (widths 3.5:1, finest at z = 0.5), no phi chain rule" if stretched else ""
     return (f"{n}^3 unit cube, 4-mode free surface (amp 0.08, seed 2) + {body}, "
-            f"rho_air/rho_water 1e-3, u*~N(0,0.1) seed 3, w~N(0,1); " + step)
+            f"rho_air/rho_water 1e-3, u*~N(0,0.1) seed 3, w~N(0,1); " + step + grid)
 
 
 def make_case(args):
+    import numpy as np
     from paper_1410_2240_gb300 import synth
     if args.workload == "c4":
         return synth.case_c4()
@@ -110,6 +114,8 @@ def make_case(args):
     if getattr(args, "cut_cells", False):  # the ellipsoid as fractional face areas, no binary mask
         case.psi_nodes = synth.ellipsoid_psi_nodes(args.n, args.n, args.n, case.h)
         case.solid = None
+    if getattr(args, "stretched", False):  # the same arrays on a grid stretched in z, finest at 0.5
+        case.widths = (np.full(args.n, case.h), np.full(args.n, case.h), synth.stretched_widths(args.n, 3.5, 0.5))
     return case
 
 
@@ -215,6 +221,7 @@ class Step:
     """All device buffers of one projection step; run() launches it on the current stream."""
 
     def __init__(self, case, prec, profile, **opts):
+        import numpy as np
         import torch
         from paper_1410_2240_gb300 import mgproj
         self.mg = mgproj
@@ -225,7 +232,14 @@ class Step:
         self.u_star = tuple(dev(x) for x in case.u_star)
         self.w = tuple(dev(x) for x in case.w)
         self.beta = mgproj.face_coeffs(self.phi, case.h, self.solid, rho_air=case.lam)
-        self.ctx = mgproj.Context(self.beta, case.h, prec=prec, profile=profile, **opts)
+        self.widths = None
+        if getattr(case, "widths", None) is not None:  # stretched: the index grid of unit spacing
+            self.widths = tuple(dev(np.asarray(w)) for w in case.widths)
+            bidx, area = mgproj.stretched_metrics(*self.widths, self.beta)
+            self.ctx = mgproj.Context(bidx, 1.0, prec=prec, profile=profile, **opts)
+            self.ctx.set_face_areas(area)
+        else:
+            self.ctx = mgproj.Context(self.beta, case.h, prec=prec, profile=profile, **opts)
         psi = getattr(case, "psi_nodes", None)
         if psi is not None:  # a static body: its face areas once, kept by the context
             self.ctx.set_face_areas(mgproj.face_areas(dev(psi), case.h))
@@ -241,13 +255,18 @@ class Step:
     def run(self):
         mg, c = self.mg, self.case
         mg.face_coeffs(self.phi, c.h, self.solid, rho_air=c.lam, out=self.beta)
-        self.ctx.update(self.beta)
+        if self.widths is not None:
+            bidx, _ = mg.stretched_metrics(*self.widths, self.beta)
+            self.ctx.update(bidx)
+        else:
+            self.ctx.update(self.beta)
         self.p.zero_()
         _, _, st = self.ctx.project(self.u_star, p=self.p, tol=TOL, out=self.u)
         c1, t1 = st.cycles, st.ms_solve
         self.q.zero_()
         _, _, st = self.ctx.project_adjoint(self.w, self.p, tol=TOL, grad_u=self.gu, grad_beta=self.gb, q=self.q)
-        mg.phi_grad(self.beta, self.gb, c.h, rho_air=c.lam, out=self.gphi)
+        if self.widths is None:  # (stretched: the face gradient is with respect to beta / d)
+            mg.phi_grad(self.beta, self.gb, c.h, rho_air=c.lam, out=self.gphi)
         self.cycles.append((c1, st.cycles))
         self.solve_ms.append(t1 + st.ms_solve)
 
@@ -443,7 +462,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.n, args.workload, args.cut_cells), "cells": n, "precision": "mixed (FP32 V-cycles, FP64 "
+        "config": {"workload": workload_name(args.n, args.workload, args.cut_cells, args.stretched), "cells": n, "precision": "mixed (FP32 V-cycles, FP64 "
                    "residual/accumulation/coarsest solve)", "tol": TOL, "solves_per_step": 2,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: each FP64 fine array is %.0f MB, ~1.5 GB touched per step" % (8 * n / 1e6)},

@@ -122,6 +122,14 @@ def ellipsoid_mask(nx, ny, nz, h, centre=(0.5, 0.5, 0.5), semi=(0.3, 0.06, 0.05)
     return np.ascontiguousarray((q <= 1.0).astype(np.uint8))
 
 
+def stretched_widths(n: int, ratio: float = 3.5, finest: float = 0.5) -> np.ndarray:
+    """Cell widths of an axis of unit length stretched smoothly: the narrowest cells at `finest`,
+    the widest a factor `ratio` wider (the spread of the paper's grid, 0.002 to 0.007)."""
+    t = (np.arange(n) + 0.5) / n
+    w = 1.0 + (ratio - 1.0) * (0.5 - 0.5 * np.cos(2 * np.pi * (t - finest + 0.5)))
+    return np.ascontiguousarray(w / w.sum())
+
+
 def ellipsoid_psi_nodes(nx, ny, nz, h, centre=(0.5, 0.5, 0.5), semi=(0.3, 0.06, 0.05)) -> np.ndarray:
     """Level-set of the same ellipsoid at the grid nodes ((nz+1, ny+1, nx+1), node (i,j,k) at
     (i h, j h, k h)): > 0 outside, < 0 inside, (sqrt(q) - 1) * min(semi) (the distance to the surface
