@@ -118,6 +118,7 @@ def _load(path: Optional[str] = None):
             lib.orc_face_areas.argtypes = [i, i, i, _D, _D, _D, _D]
             lib.orc_divergence_area.argtypes = [i, i, i, d, d] + [_D] * 10
             lib.orc_stretched_metrics.argtypes = [i, i, i] + [_D] * 15
+            lib.orc_vof_upwind.argtypes = [i, i, i, d, d] + [_D] * 8
             _lib = lib
     return _lib
 
@@ -496,6 +497,50 @@ def project_stretched(phi, hx, hy, hz, u_star, dt=1.0, lam=1e-3, tol=1e-12, frac
     p = solve(ce, rhs, 1.0, tol=tol)
     u = correct(open_mask(area, bi), p, u_star, 1.0, dt)
     return u, p, bi, area, rhs
+
+
+# ---------------------------------------------------------------------------
+# The time step (Numerical Time Integration section): two projections, Eq. poisson1 / runge1 and
+# Eq. poisson2 / runge2, and the VOF operator
+# ---------------------------------------------------------------------------
+
+def vof_upwind(beta, u, phi, h, dt):
+    """VOF(u, phi, dt) of orc_vof_upwind (first-order upwind fluxes through the open faces)."""
+    lib = _load()
+    nx, ny, nz = _dims(beta[0])
+    out = np.empty((nz, ny, nx))
+    lib.orc_vof_upwind(nx, ny, nz, h, dt, *[_p(_f64(b)) for b in beta], *[_p(_f64(x)) for x in u], _p(_f64(phi)),
+                       _p(out))
+    return out
+
+
+def body_force(beta, g):
+    """R of the momentum equations kept here: the hydrostatic term -g (g = 1/Fr^2) on the open
+    z-faces, 0 on every other face."""
+    return (np.zeros_like(beta[0]), np.zeros_like(beta[1]), np.where(beta[2] > 0, -g, 0.0))
+
+
+def rk2_step(phi, solid, u, h, dt, g, lam=1e-3, tol=1e-12):
+    """One step of the second-order Runge-Kutta scheme:
+        u~  = u^k + dt R;  P* from Eq. poisson1 with rho(phi^k);  u* = u~ - dt B G P*   (Eq. runge1)
+        phi* = phi^k - VOF(u^k, phi^k, dt)
+        u~~ = u* + u^k + dt R;  P from Eq. poisson2 with rho(phi*);
+        u^{k+1} = (u~~ - dt B* G P) / 2                                                  (Eq. runge2)
+        phi^{k+1} = phi^k - VOF((u* + u^k)/2, phi^k, dt)
+    R = the body force.  Returns (u^{k+1}, phi^{k+1}, P)."""
+    beta = face_coeffs(phi, solid, lam)
+    R = body_force(beta, g)
+    ut = tuple(a + dt * r for a, r in zip(u, R))
+    us = correct(beta, solve(beta, divergence(beta, ut, h, dt), h, tol=tol), ut, h, dt)
+    phis = phi - vof_upwind(beta, u, phi, h, dt)
+    beta2 = face_coeffs(phis, solid, lam)
+    R2 = body_force(beta2, g)
+    ut2 = tuple((a + b) + dt * r for a, b, r in zip(us, u, R2))
+    P = solve(beta2, divergence(beta2, ut2, h, dt), h, tol=tol)
+    u1 = tuple(0.5 * x for x in correct(beta2, P, ut2, h, dt))
+    uh = tuple(0.5 * (a + b) for a, b in zip(us, u))
+    phi1 = phi - vof_upwind(beta, uh, phi, h, dt)
+    return u1, phi1, P
 
 
 # ---------------------------------------------------------------------------

@@ -823,6 +823,36 @@ void orc_stretched_metrics(int nx, int ny, int nz, const double *hx, const doubl
             }
 }
 
+/* ------------------------------------------------------------------------- */
+/* VOF operator of the time integration (Eq. vof with Q = 0, Numerical Time  */
+/* Integration section): VOF(u, phi, dt) = dt * h^-1 * sum over the open     */
+/* faces of the cell of +-u_f phi_up(f), phi_up the value of the cell the    */
+/* face velocity comes from (first-order upwind, unsplit); closed faces and  */
+/* walls carry no flux.  The paper cites its VOF scheme; this is the simplest */
+/* conservative one.  Face order x+, x-, y+, y-, z+, z-.                      */
+/* ------------------------------------------------------------------------- */
+void orc_vof_upwind(int nx, int ny, int nz, double h, double dt, const double *bx, const double *by, const double *bz,
+                    const double *ux, const double *uy, const double *uz, const double *phi, double *out)
+{
+    double s = dt / h;
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t c = IX(i, j, k), f;
+                double d = 0.0;
+#define UPW(u, lo, hi) ((u) > 0.0 ? (u) * phi[lo] : (u) * phi[hi])
+                if (i < nx - 1 && bx[f = IX(i + 1, j, k)] > 0.0) d += UPW(ux[f], c, f);
+                if (bx[c] > 0.0) d -= UPW(ux[c], IX(i - 1, j, k), c);
+                if (j < ny - 1 && by[f = IX(i, j + 1, k)] > 0.0) d += UPW(uy[f], c, f);
+                if (by[c] > 0.0) d -= UPW(uy[c], IX(i, j - 1, k), c);
+                if (k < nz - 1 && bz[f = IX(i, j, k + 1)] > 0.0) d += UPW(uz[f], c, f);
+                if (bz[c] > 0.0) d -= UPW(uz[c], IX(i, j, k - 1), c);
+#undef UPW
+                out[c] = s * d;
+            }
+}
+
 /* u_f = u*_f - dt beta_f (p_R - p_L) / h on open faces; closed faces keep u*. */
 void orc_correct(int nx, int ny, int nz, double h, double dt, const double *bx, const double *by,
                  const double *bz, const double *p, const double *ux0, const double *uy0,

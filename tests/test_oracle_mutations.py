@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 import test_oracle_areas as T3
+import test_oracle_rk2 as T5
 import test_oracle_stretched as T4
 import test_oracle_operator as T1
 import test_oracle_solver as T2
@@ -80,6 +81,8 @@ MUTANTS = [
      [T4.test_linear_pressure_face_gradients_exact, T4.test_layered_problem_matches_1d_finite_volumes]),
     ("stretched z-face area from the wrong widths", "az[c] = (hx[i] * hy[j]) * (fz ? fz[c] : 1.0);",
      "az[c] = (hx[i] * hz[k]) * (fz ? fz[c] : 1.0);", [T4.test_linear_pressure_face_gradients_exact]),
+    ("VOF takes the downwind cell", "#define UPW(u, lo, hi) ((u) > 0.0 ? (u) * phi[lo] : (u) * phi[hi])",
+     "#define UPW(u, lo, hi) ((u) > 0.0 ? (u) * phi[hi] : (u) * phi[lo])", [T5.test_vof_upwind_hand_example]),
 ]
 
 
