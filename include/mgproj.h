@@ -220,6 +220,28 @@ int mg_set_body_velocity(mg_ctx *c, const double *const v[3]);
  * (layout as for face coefficients); beta_out, area_out: device, written;
  * wall faces 0.  Errors: MG_ERR_ARG for a bad grid or null/unaligned arrays.
  */
+/*
+ * One step of the second-order Runge-Kutta time integration (Numerical Time
+ * Integration section) around the projection:
+ *   stage 1: beta from phi^k (Eq. density); u~ = u^k + dt R; P* from
+ *            Eq. poisson1; u* = u~ - dt beta G P* (Eq. runge1);
+ *            phi* = phi^k - VOF(u^k, phi^k, dt)
+ *   stage 2: beta from phi*; u~~ = (u* + u^k) + dt R; P from Eq. poisson2;
+ *            u^{k+1} = (u~~ - dt beta G P) / 2 (Eq. runge2);
+ *            phi^{k+1} = phi^k - VOF((u* + u^k)/2, phi^k, dt)
+ * R is the body force of the momentum equations, -g (g = 1/Fr^2) on the open
+ * z-faces; the convective, viscous and sub-grid terms are not modelled.  VOF
+ * is the conservative first-order upwind flux form of Eq. vof (Q = 0)
+ * through the open faces.  The two projections use the context's solver
+ * options (and its face areas and body velocity, if set).  phi, solid_mask:
+ * as for mg_face_coeffs; u: device face arrays, u^k on entry, u^{k+1} on
+ * return; phi_out: device, phi^{k+1} (must not alias phi); p_out: device, P
+ * of the second stage.  stats: of the second projection.  Errors: as for
+ * mg_project.
+ */
+int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water, double g,
+                double dt, double *const u[3], double *phi_out, double *p_out, double tol, mg_stats *stats);
+
 int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, const double *hz,
                          const double *const beta[3], const double *const frac[3], double *const beta_out[3],
                          double *const area_out[3], void *stream);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -82,6 +83,9 @@ struct mg_ctx {
     // (mg_set_body_velocity)
     bool has_area = false, has_vb = false;
     LevelArrays<double> karea, kbeta, kvb;
+    // the time step's scratch (mg_rk2_step): face coefficients of the two stages, u~, u*, phi*
+    LevelArrays<double> rk_b1, rk_b2, rk_ut, rk_us;
+    double *rk_phis = nullptr;
     float *urow0 = nullptr;  // uniform-row values of the finest FP32 level (with split0)
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
@@ -1045,6 +1049,76 @@ int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, c
     };
     CK(mg::launch_stretched_metrics(Dims{g->nx, g->ny, g->nz}, hx, hy, hz, view(beta), view(frac),
                                     view(beta_out), view(area_out), (cudaStream_t)stream));
+    return MG_OK;
+}
+
+int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water, double g,
+                double dt, double *const u[3], double *phi_out, double *p_out, double tol, mg_stats *stats)
+{
+    g_err.clear();
+    if (!c || !phi || !u || !u[0] || !u[1] || !u[2] || !phi_out || !p_out)
+        return fail(MG_ERR_ARG, "mg_rk2_step: null argument");
+    if (!(dt > 0.0) || !(tol > 0.0) || !(rho_air > 0.0) || !(rho_water > 0.0) || !std::isfinite(g))
+        return fail(MG_ERR_ARG, "mg_rk2_step: dt, tol and the densities must be > 0, g finite");
+    if (!aligned16({phi, solid_mask, u[0], u[1], u[2], phi_out, p_out}))
+        return fail(MG_ERR_ARG, "mg_rk2_step: arrays must be 16-byte aligned");
+    if (phi_out == phi) return fail(MG_ERR_ARG, "mg_rk2_step: phi_out must not alias phi");
+    const size_t n = c->dims[0].n();
+    const Dims d = c->dims[0];
+    cudaStream_t s = c->s;
+    if (!c->rk_phis) {
+        for (LevelArrays<double> *L : {&c->rk_b1, &c->rk_b2, &c->rk_ut, &c->rk_us}) {
+            CKS(c->alloc(&L->bx, n));
+            CKS(c->alloc(&L->by, n));
+            CKS(c->alloc(&L->bz, n));
+        }
+        CKS(c->alloc(&c->rk_phis, n));
+    }
+    LevelArrays<double> uk{};
+    uk.bx = u[0];
+    uk.by = u[1];
+    uk.bz = u[2];
+    const LevelArrays<double> none{};
+    const double drho = rho_water - rho_air, s_dt_h = dt / c->g.h;
+    auto faces = [](const LevelArrays<double> &L) {
+        return std::array<double *, 3>{L.bx, L.by, L.bz};
+    };
+    // stage 1: rho(phi^k); u~ = u^k + dt R; u* = u~ - dt B G P*  (Eq. poisson1, runge1)
+    CK(mg::launch_face_coeffs(d, phi, solid_mask, rho_air, drho, c->rk_b1.bx, c->rk_b1.by, c->rk_b1.bz, s));
+    {
+        const auto b1 = faces(c->rk_b1);
+        const double *cb1[3] = {b1[0], b1[1], b1[2]};
+        CKS(compute_hierarchy(c, cb1));
+    }
+    CK(mg::launch_rk_combine(n, uk, none, c->rk_b1.bz, dt, g, c->rk_ut, s));
+    CK(cudaMemsetAsync(p_out, 0, n * sizeof(double), s));
+    {
+        const double *ut[3] = {c->rk_ut.bx, c->rk_ut.by, c->rk_ut.bz};
+        double *us[3] = {c->rk_us.bx, c->rk_us.by, c->rk_us.bz};
+        const int st = mg_project(c, ut, us, p_out, dt, tol, stats);
+        if (st != MG_OK) return st;
+    }
+    // phi* = phi^k - VOF(u^k, phi^k, dt)
+    CK(mg::launch_vof_upwind(d, s_dt_h, c->rk_b1, uk, phi, c->rk_phis, s));
+    // stage 2: rho(phi*); u~~ = (u* + u^k) + dt R; u^{k+1} = (u~~ - dt B* G P) / 2  (Eq. poisson2, runge2)
+    CK(mg::launch_face_coeffs(d, c->rk_phis, solid_mask, rho_air, drho, c->rk_b2.bx, c->rk_b2.by, c->rk_b2.bz, s));
+    {
+        const auto b2 = faces(c->rk_b2);
+        const double *cb2[3] = {b2[0], b2[1], b2[2]};
+        CKS(compute_hierarchy(c, cb2));
+    }
+    CK(mg::launch_rk_combine(n, c->rk_us, uk, c->rk_b2.bz, dt, g, c->rk_ut, s));
+    // (u* + u^k) / 2 for the second VOF, kept in u* (u^k is overwritten below)
+    CK(mg::launch_half(n, c->rk_us, uk, c->rk_us, s));
+    // phi^{k+1} = phi^k - VOF((u* + u^k)/2, phi^k, dt), with the first stage's face mask
+    CK(mg::launch_vof_upwind(d, s_dt_h, c->rk_b1, c->rk_us, phi, phi_out, s));
+    CK(cudaMemsetAsync(p_out, 0, n * sizeof(double), s));
+    {
+        const double *ut[3] = {c->rk_ut.bx, c->rk_ut.by, c->rk_ut.bz};
+        const int st = mg_project(c, ut, u, p_out, dt, tol, stats);
+        if (st != MG_OK) return st;
+    }
+    CK(mg::launch_half(n, uk, none, uk, s));
     return MG_OK;
 }
 

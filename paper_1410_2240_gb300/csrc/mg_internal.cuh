@@ -187,6 +187,14 @@ cudaError_t launch_face_areas(Dims d, const double *psi, double *ax, double *ay,
 cudaError_t launch_stretched_metrics(Dims d, const double *hx, const double *hy, const double *hz,
                                     const LevelArrays<double> &beta, const LevelArrays<double> &frac,
                                     const LevelArrays<double> &bout, const LevelArrays<double> &aout, cudaStream_t s);
+// time step pieces: out = (a + b) + dt R with R = -g on open z-faces (b null: a + dt R);
+// out = 0.5 (a + b); phi_out = phi - (dt/h) sum +-u phi_upwind over open faces
+cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b, const double *bz,
+                              double dt, double g, const LevelArrays<double> &out, cudaStream_t s);
+cudaError_t launch_half(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b,
+                        const LevelArrays<double> &out, cudaStream_t s);
+cudaError_t launch_vof_upwind(Dims d, double s_dt_h, const LevelArrays<double> &mask, const LevelArrays<double> &u,
+                              const double *phi, double *phi_out, cudaStream_t s);
 // out = area * beta on faces of open area, 0 elsewhere (bx/by/bz of each)
 cudaError_t launch_area_coeffs(size_t n, const LevelArrays<double> &area, const LevelArrays<double> &beta,
                                const LevelArrays<double> &out, cudaStream_t s);

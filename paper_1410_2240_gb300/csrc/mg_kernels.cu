@@ -1173,6 +1173,55 @@ __global__ void k_stretched_metrics(int nx, int ny, int nz, const double *__rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// The Runge-Kutta time step (Numerical Time Integration section).  R = the body force, -g on the
+// open z-faces (beta_z > 0), 0 elsewhere; each operation rounded separately in the order written.
+// ---------------------------------------------------------------------------
+// out = (a + b) + dt R   (b null: a + dt R)
+__global__ void k_rk_combine(size_t n, LevelArrays<double> a, LevelArrays<double> b, const double *__restrict__ bz,
+                             double dt, double g, LevelArrays<double> out)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const double rz = pos_bits(bz[c]) ? -g : 0.0;
+        const double sx = b.bx ? __dadd_rn(a.bx[c], b.bx[c]) : a.bx[c];
+        const double sy = b.by ? __dadd_rn(a.by[c], b.by[c]) : a.by[c];
+        const double sz = b.bz ? __dadd_rn(a.bz[c], b.bz[c]) : a.bz[c];
+        out.bx[c] = __dadd_rn(sx, __dmul_rn(dt, 0.0));
+        out.by[c] = __dadd_rn(sy, __dmul_rn(dt, 0.0));
+        out.bz[c] = __dadd_rn(sz, __dmul_rn(dt, rz));
+    }
+}
+
+// out = 0.5 (a + b)   (b null: 0.5 a)
+__global__ void k_half(size_t n, LevelArrays<double> a, LevelArrays<double> b, LevelArrays<double> out)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        out.bx[c] = __dmul_rn(0.5, b.bx ? __dadd_rn(a.bx[c], b.bx[c]) : a.bx[c]);
+        out.by[c] = __dmul_rn(0.5, b.by ? __dadd_rn(a.by[c], b.by[c]) : a.by[c]);
+        out.bz[c] = __dmul_rn(0.5, b.bz ? __dadd_rn(a.bz[c], b.bz[c]) : a.bz[c]);
+    }
+}
+
+// phi_out = phi - s * sum over open faces of +-u_f phi_up(f)  (s = dt / h; first-order upwind, the
+// order x+, x-, y+, y-, z+, z-; closed faces carry no flux)
+__global__ void k_vof_upwind(int nx, int ny, int nz, double s, LevelArrays<double> mask, LevelArrays<double> u,
+                             const double *__restrict__ phi, double *__restrict__ phi_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const size_t sxy = (size_t)nx * ny;
+    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    auto upw = [&](double uf, size_t lo, size_t hi) { return __dmul_rn(uf, pos_bits(uf) ? phi[lo] : phi[hi]); };
+    double d = 0.0;
+    if (i < nx - 1 && pos_bits(mask.bx[c + 1])) d = __dadd_rn(d, upw(u.bx[c + 1], c, c + 1));
+    if (pos_bits(mask.bx[c])) d = __dsub_rn(d, upw(u.bx[c], c - 1, c));
+    if (j < ny - 1 && pos_bits(mask.by[c + nx])) d = __dadd_rn(d, upw(u.by[c + nx], c, c + nx));
+    if (pos_bits(mask.by[c])) d = __dsub_rn(d, upw(u.by[c], c - nx, c));
+    if (k < nz - 1 && pos_bits(mask.bz[c + sxy])) d = __dadd_rn(d, upw(u.bz[c + sxy], c, c + sxy));
+    if (pos_bits(mask.bz[c])) d = __dsub_rn(d, upw(u.bz[c], c - sxy, c));
+    phi_out[c] = __dsub_rn(phi[c], __dmul_rn(s, d));
+}
+
 // the operator's coefficient of a face: area * 1/rho where the area is > 0, else 0
 __global__ void k_area_coeffs(size_t n, LevelArrays<double> area, LevelArrays<double> beta, LevelArrays<double> out)
 {
@@ -1848,6 +1897,30 @@ cudaError_t launch_stretched_metrics(Dims d, const double *hx, const double *hy,
     note_launch();
     k_stretched_metrics<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, hx, hy, hz, beta, frac,
                                                                            bout, aout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b, const double *bz,
+                              double dt, double g, const LevelArrays<double> &out, cudaStream_t s)
+{
+    note_launch();
+    k_rk_combine<<<red_grid(n), kRedThreads, 0, s>>>(n, a, b, bz, dt, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_half(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b,
+                        const LevelArrays<double> &out, cudaStream_t s)
+{
+    note_launch();
+    k_half<<<red_grid(n), kRedThreads, 0, s>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vof_upwind(Dims d, double s_dt_h, const LevelArrays<double> &mask, const LevelArrays<double> &u,
+                              const double *phi, double *phi_out, cudaStream_t s)
+{
+    note_launch();
+    k_vof_upwind<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, s_dt_h, mask, u, phi, phi_out);
     return cudaGetLastError();
 }
 

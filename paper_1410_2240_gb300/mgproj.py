@@ -78,6 +78,8 @@ _lib.mg_update.argtypes = [_vp, _PP]
 _lib.mg_face_areas.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _vp]
 _lib.mg_set_face_areas.argtypes = [_vp, _PP]
 _lib.mg_set_body_velocity.argtypes = [_vp, _PP]
+_lib.mg_rk2_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _PP,
+                              _vp, _vp, ctypes.c_double, ctypes.POINTER(Stats)]
 _lib.mg_stretched_metrics.argtypes = [ctypes.POINTER(Grid), _vp, _vp, _vp, _PP, _PP, _PP, _PP, _vp]
 _lib.mg_kernel_launches.restype = ctypes.c_uint64
 _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -97,7 +99,7 @@ EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_sol
            "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
            "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset",
            "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error", "mg_face_areas", "mg_set_face_areas",
-           "mg_set_body_velocity", "mg_stretched_metrics"]
+           "mg_set_body_velocity", "mg_stretched_metrics", "mg_rk2_step"]
 
 
 class MGError(RuntimeError):
@@ -244,6 +246,19 @@ class Context:
         """mg_set_face_areas: fractional open areas of the faces (None: whole faces); the face
         coefficients of this context are then 1/rho and the operator uses area * 1/rho."""
         _check(_lib.mg_set_face_areas(self._c, None if areas is None else _faces(areas, self.shape, "area")))
+
+    def rk2_step(self, phi, u, dt, g, solid=None, rho_air=1e-3, rho_water=1.0, tol=1e-10, phi_out=None, p=None):
+        """mg_rk2_step: one Runge-Kutta step (u updated in place); returns (phi_new, p, stats)."""
+        if phi_out is None:
+            phi_out = torch.empty_like(phi)
+        if p is None:
+            p = torch.empty_like(phi)
+        st = Stats()
+        sp = _vp(0) if solid is None else _dev(solid, self.shape, torch.uint8, "solid")
+        _check(_lib.mg_rk2_step(self._c, _dev(phi, self.shape, name="phi"), sp, rho_air, rho_water, g, dt,
+                                _faces(u, self.shape, "u"), _dev(phi_out, self.shape, name="phi_out"),
+                                _dev(p, self.shape, name="p"), tol, ctypes.byref(st)))
+        return phi_out, p, st
 
     def set_body_velocity(self, v):
         """mg_set_body_velocity: the body velocity on the faces (None: a static body)."""
