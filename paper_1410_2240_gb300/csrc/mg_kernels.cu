@@ -102,6 +102,24 @@ __device__ __noinline__ T div_call(T a, T b)
     return a / b;
 }
 
+// float -> double on the integer pipe.  The hardware conversion issues on the FP64 unit, which
+// bounds the CG kernels that widen an FP32 field per cell.  From the IEEE 754 binary32 and binary64
+// layouts: the sign is kept, the exponent rebiased (127 -> 1023), the 23-bit fraction shifted into
+// the top of the 52-bit one; zeros, infinities and NaNs map field by field.  Subnormal floats (never
+// produced by the scaled cycles, but possible) take the hardware conversion.  Exact: every float is
+// a double.
+__device__ __noinline__ double f2d_slow(float x) { return (double)x; }
+__device__ __forceinline__ double widen(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+    if (e == 0u) return m ? f2d_slow(x) : __longlong_as_double((long long)sgn);
+    const unsigned long long ee = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e + 896u);
+    return __longlong_as_double((long long)(sgn | (ee << 52) | ((unsigned long long)m << 29)));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // x > 0 and x == 0 decided on the integer pipe (an FP64 comparison occupies the FP64 unit, the
 // limiting resource of the FP64 passes).  pos_bits(x) equals x > 0 for every x but a NaN with a
 // clear sign bit; the coefficients, inverse diagonals and live masks it is applied to are never
@@ -1062,7 +1080,7 @@ __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *
     const double s = dscal[scale_slot];
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const size_t e = sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx;
-        p[idx] = fma(s, (double)e32[e], p[idx]);
+        p[idx] = fma(s, widen(e32[e]), p[idx]);
     }
 }
 
@@ -1480,14 +1498,14 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
             i0 = (q ? sp.half : 0) + v;
             i1 = (q ? 0 : sp.half) + v;
         }
-        const double z0 = (double)z[i0], z1 = (double)z[i1];
+        const double z0 = widen(z[i0]), z1 = widen(z[i1]);
         double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
         dv.x = fma(beta, dv.x, sz * z0);
         dv.y = fma(beta, dv.y, sz * z1);
         d2[v] = dv;
     }
     for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride)
-        d[idx] = fma(beta, first ? 0.0 : d[idx], sz * (double)z[idx]);
+        d[idx] = fma(beta, first ? 0.0 : d[idx], sz * widen(z[idx]));
 }
 
 __global__ void k_pcg_shift_rz(double *dscal) { dscal[S_RZ] = dscal[S_RZN]; }
