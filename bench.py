@@ -318,15 +318,29 @@ def e2e_leg(case, K, W):
     o_gu = tuple(torch.empty_like(x).pin_memory() for x in h_u)
     o_gphi = torch.empty_like(h_phi).pin_memory()
 
+    # the loss weights w are uploaded while the forward solve runs, and the projected
+    # velocity is read back while the backward solve runs, on a second stream
+    side = torch.cuda.Stream()
+
     def one():
+        main = torch.cuda.current_stream()
         phi = h_phi.to("cuda", non_blocking=True).requires_grad_(True)
         solid = h_solid.to("cuda", non_blocking=True) if h_solid is not None else None
         u = tuple(x.to("cuda", non_blocking=True).requires_grad_(True) for x in h_u)
-        w = tuple(x.to("cuda", non_blocking=True) for x in h_w)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            w = tuple(x.to("cuda", non_blocking=True) for x in h_w)
+        for x in w:
+            x.record_stream(main)
+        w_ready = side.record_event()
         (ux, uy, uz), p = project(u, phi, case.h, solid=solid, rho_air=case.lam, tol=TOL, precision="mixed")
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            for o, x in zip(o_u, (ux, uy, uz)):
+                o.copy_(x.detach(), non_blocking=True)
+                x.record_stream(side)
+        main.wait_event(w_ready)
         torch.autograd.backward((ux, uy, uz), w)
-        for o, x in zip(o_u, (ux, uy, uz)):
-            o.copy_(x.detach(), non_blocking=True)
         for o, x in zip(o_gu, u):
             o.copy_(x.grad, non_blocking=True)
         o_gphi.copy_(phi.grad, non_blocking=True)

@@ -3,9 +3,9 @@
 ``project(u_star, phi)`` returns the divergence-free velocity u = u* - dt beta grad p
 (Eq. runge1) and the pressure p.  Its backward is the adjoint projection of the C ABI
 (mg_project_adjoint: one more solve with the same self-adjoint operator) followed by
-the chain rule to phi (mg_phi_grad).  Saved for backward: phi (an input), the solid
-mask (an input) and p; the face coefficients and the multigrid hierarchy are rebuilt
-in backward from phi (into a cached context, see ``clear_cache``).
+the chain rule to phi (mg_phi_grad).  Saved for backward: the face coefficients and p.
+The multigrid hierarchy lives in a cached context (see ``clear_cache``); backward
+rebuilds it only when another forward has rebuilt that context since this one.
 """
 from __future__ import annotations
 
@@ -20,7 +20,10 @@ from . import mgproj
 _CONTEXTS = {}
 
 
-def _context(beta, h, prec):
+def _context(beta, h, prec, token):
+    """The cached context for this grid, its hierarchy built from ``beta``.  ``token`` names
+    the forward call that ``beta`` belongs to: a context whose hierarchy was last built for
+    the same token is returned as it is."""
     key = (tuple(beta[0].shape), float(h), int(prec), beta[0].device.index, torch.cuda.current_stream().cuda_stream)
     mg = _CONTEXTS.get(key)
     if mg is None:
@@ -29,8 +32,9 @@ def _context(beta, h, prec):
         # CG preconditioned by V-cycles: 2 cycles per application with FP32 cycles, 1 with FP64
         mg = _CONTEXTS[key] = mgproj.Context(beta, h, prec=prec, krylov=1,
                                              inner_cycles=2 if prec == mgproj.MG_MIXED else 1)
-    else:
+    elif getattr(mg, "built_for", None) is not token:
         mg.update(beta)
+    mg.built_for = token
     return mg
 
 
@@ -44,24 +48,22 @@ class _Project(torch.autograd.Function):
     @staticmethod
     def forward(ctx, ux, uy, uz, phi, solid, h, dt, rho_air, rho_water, tol, prec):
         beta = mgproj.face_coeffs(phi, h, solid, rho_air, rho_water)
-        mg = _context(beta, h, prec)
+        ctx.token = object()
+        mg = _context(beta, h, prec, ctx.token)
         p = torch.zeros_like(phi)
         u, p, st = mg.project((ux, uy, uz), p=p, dt=dt, tol=tol)
-        ctx.save_for_backward(phi, p, solid if solid is not None else torch.empty(0, device=phi.device))
-        ctx.has_solid = solid is not None
+        ctx.save_for_backward(p, *beta)
         ctx.cfg = (h, dt, rho_air, rho_water, tol, prec)
         ctx.mark_non_differentiable(p)
         return u[0], u[1], u[2], p
 
     @staticmethod
     def backward(ctx, gux, guy, guz, gp):
-        phi, p, solid = ctx.saved_tensors
-        solid = solid if ctx.has_solid else None
+        p, *beta = ctx.saved_tensors
         h, dt, rho_air, rho_water, tol, prec = ctx.cfg
-        w = tuple((g if g is not None else torch.zeros_like(phi)).contiguous() for g in (gux, guy, guz))
-        beta = mgproj.face_coeffs(phi, h, solid, rho_air, rho_water)
-        mg = _context(beta, h, prec)
-        grad_u, grad_beta, _ = mg.project_adjoint(w, p, dt=dt, tol=tol, q=torch.zeros_like(phi))
+        w = tuple((g if g is not None else torch.zeros_like(p)).contiguous() for g in (gux, guy, guz))
+        mg = _context(beta, h, prec, ctx.token)
+        grad_u, grad_beta, _ = mg.project_adjoint(w, p, dt=dt, tol=tol, q=torch.zeros_like(p))
         gphi = mgproj.phi_grad(beta, grad_beta, h, rho_air, rho_water) if ctx.needs_input_grad[3] else None
         return grad_u[0], grad_u[1], grad_u[2], gphi, None, None, None, None, None, None, None
 
