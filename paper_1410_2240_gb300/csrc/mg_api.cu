@@ -394,7 +394,10 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
             const int lv = l + q;
             const Dims dl = c->dims[lv];
             a.lev[q] = mg::TailLevel<T>{dl.nx, dl.ny, dl.nz, (T)(c->hs[lv] * c->hs[lv]),
-                                        (T)(1.0 / (c->hs[lv] * c->hs[lv])), L[lv]};
+                                        (T)(1.0 / (c->hs[lv] * c->hs[lv])), L[lv],
+                                        mg::make_fastdiv((unsigned)(dl.nx + 1) / 2), mg::make_fastdiv((unsigned)dl.ny),
+                                        mg::make_fastdiv((unsigned)std::max(dl.nx / 2, 1)),
+                                        mg::make_fastdiv((unsigned)std::max(dl.ny / 2, 1))};
         }
         a.lev[0].L.b = const_cast<T *>(b);
         a.lev[0].L.p = p;
@@ -645,7 +648,9 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
             CK(mg::launch_cast_f32(n, c->L64[l].bx, c->L32[l].bx, s));
             CK(mg::launch_cast_f32(n, c->L64[l].by, c->L32[l].by, s));
             CK(mg::launch_cast_f32(n, c->L64[l].bz, c->L32[l].bz, s));
-            CK(mg::launch_cast_f32(n, c->L64[l].dinv, c->L32[l].dinv, s));
+            // 1/sum of the FP32 coefficients, the value the FP32 smoothers form on the fly
+            CK(mg::launch_diag_inv<float>(c->dims[l], c->L32[l].bx, c->L32[l].by, c->L32[l].bz, c->L32[l].dinv, s,
+                                          nullptr, 1.0f));
         }
         if (c->urow0)
             CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s));

@@ -88,6 +88,7 @@ struct TailLevel {
     int nx, ny, nz;
     T h2, ih2;
     LevelArrays<T> L;
+    FastDiv fhx, fny, fcx, fcy;  // division by (nx + 1) / 2, ny, nx / 2 and ny / 2
 };
 template <typename T>
 struct TailArgs {

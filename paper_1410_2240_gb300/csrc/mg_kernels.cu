@@ -266,8 +266,9 @@ __device__ __forceinline__ T inv_diag(T stored, T bxl, T bxh, T byl, T byh, T bz
 //     p_c = dinv_c * (sum_f beta_f p_nb - h^2 b_c),  sum order x-,x+,y-,y+,z-,z+,
 // products accumulated with fused multiply-adds in that order.
 // ---------------------------------------------------------------------------
-// one cell's update (shared by k_smooth and the coarse tail, so both round alike)
-template <typename T>
+// one cell's update (shared by k_smooth and the coarse tail, so both round alike).  STORED: take
+// 1/sum from L.dinv also in FP32, where the hierarchy stores exactly inv_diag's value
+template <typename T, bool STORED = false>
 __device__ __forceinline__ void smooth_cell(int i, int j, int k, int nx, int ny, int nz, T h2, const LevelArrays<T> &L,
                                             const T *b, T *p)
 {
@@ -283,7 +284,8 @@ __device__ __forceinline__ void smooth_cell(int i, int j, int k, int nx, int ny,
     if (j < ny - 1) s = fma(byh, p[c + nx], s);
     if (k > 0) s = fma(bzl, p[c - sxy], s);
     if (k < nz - 1) s = fma(bzh, p[c + sxy], s);
-    p[c] = inv_diag<T>(sizeof(T) == 8 ? L.dinv[c] : T(0), bxl, bxh, byl, byh, bzl, bzh) * fma(-h2, b[c], s);
+    const T d = (STORED || sizeof(T) == 8) ? L.dinv[c] : inv_diag<T>(T(0), bxl, bxh, byl, byh, bzl, bzh);
+    p[c] = d * fma(-h2, b[c], s);
 }
 
 template <typename T>
@@ -293,7 +295,7 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
     const int j = blockIdx.y, k = blockIdx.z + z0;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
     if (i >= nx) return;
-    smooth_cell<T>(i, j, k, nx, ny, nz, h2, L, b, p);
+    smooth_cell<T, true>(i, j, k, nx, ny, nz, h2, L, b, p);
 }
 
 // Colour-split layout (Split in mg_internal.cuh): slot of natural cell c in a row of parity
@@ -426,6 +428,9 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
         const float4 u = *reinterpret_cast<const float4 *>(a), w = *reinterpret_cast<const float4 *>(a + 4);
         d[0] = u.x; d[1] = u.y; d[2] = u.z; d[3] = u.w; d[4] = w.x; d[5] = w.y; d[6] = w.z; d[7] = w.w;
     };
+    // on a uniform row the diagonal is 6v, or 5v at an x-wall (the sums of inv_diag, in its
+    // order: 0 + v = v + 0 = v), so two divisions serve the thread's four cells
+    float inv6 = 0.f, inv5 = 0.f;
     if (v == 0.f) {
         ld8(L.bx + c0, fbx);
         fbx[8] = (OFF && 8 * g + 7 < nx - 1) ? L.bx[c0 + 8] : 0.f;
@@ -433,6 +438,10 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
         if (j < ny - 1) ld8(L.by + c0 + nx, fbyh); else for (int q = 0; q < 8; q++) fbyh[q] = 0.f;
         ld8(L.bz + c0, fbz);
         if (k < nz - 1) ld8(L.bz + c0 + sxy, fbzh); else for (int q = 0; q < 8; q++) fbzh[q] = 0.f;
+    } else {
+        const float s5 = (((v + v) + v) + v) + v;
+        inv6 = 1.f / (s5 + v);
+        inv5 = 1.f / s5;
     }
     float out[4];
 #pragma unroll
@@ -454,7 +463,9 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
         if (j < ny - 1) s = fmaf(byh, oy1[t], s);
         if (k > 0) s = fmaf(bzl, oz0[t], s);
         if (k < nz - 1) s = fmaf(bzh, oz1[t], s);
-        out[t] = inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, bb[t], s);
+        const float dinv = v != 0.f ? ((i > 0 && i < nx - 1) ? inv6 : inv5)
+                                    : inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh);
+        out[t] = dinv * fmaf(-h2, bb[t], s);
     }
     *reinterpret_cast<float4 *>(own + mb) = make_float4(out[0], out[1], out[2], out[3]);
 }
@@ -874,16 +885,18 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ M, const T *__r
 // are written and read within the kernel, so they are read through plain pointers (never the
 // read-only path).
 // ---------------------------------------------------------------------------
-constexpr int kTailThreads = 512;
+// threads of the descent (its residual-restriction needs more registers) and of the ascent
+constexpr int kTailDownThreads = 512, kTailUpThreads = 1024;
 
 template <typename T>
 __device__ void tail_colour(const TailLevel<T> &v, int colour)
 {
     const int hx = (v.nx + 1) / 2, total = hx * v.ny * v.nz;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int u = t % hx, jk = t / hx, j = jk % v.ny, k = jk / v.ny;
+        const int jk = (int)fdiv(t, v.fhx), k = (int)fdiv(jk, v.fny);
+        const int u = t - jk * hx, j = jk - k * v.ny;
         const int i = 2 * u + ((j + k + colour) & 1);
-        if (i < v.nx) smooth_cell<T>(i, j, k, v.nx, v.ny, v.nz, v.h2, v.L, v.L.b, v.L.p);
+        if (i < v.nx) smooth_cell<T, true>(i, j, k, v.nx, v.ny, v.nz, v.h2, v.L, v.L.b, v.L.p);
     }
     __syncthreads();
 }
@@ -893,7 +906,8 @@ __device__ void tail_restrict(const TailLevel<T> &f, T *bc)
 {
     const int NX = f.nx / 2, NY = f.ny / 2, total = NX * NY * (f.nz / 2);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int I = t % NX, JK = t / NX, J = JK % NY, K = JK / NY;
+        const int JK = (int)fdiv(t, f.fcx), K = (int)fdiv(JK, f.fcy);
+        const int I = t - JK * NX, J = JK - K * NY;
         restrict_cell<T>(I, J, K, f.nx, f.ny, f.nz, f.ih2, f.L, f.L.b, f.L.p, bc);
     }
     __syncthreads();
@@ -904,7 +918,8 @@ __device__ void tail_prolong(const TailLevel<T> &f, const T *ec)
 {
     const int NX = f.nx / 2, NY = f.ny / 2, NZ = f.nz / 2, total = NX * NY * NZ;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int I = t % NX, JK = t / NX, J = JK % NY, K = JK / NY;
+        const int JK = (int)fdiv(t, f.fcx), K = (int)fdiv(JK, f.fcy);
+        const int I = t - JK * NX, J = JK - K * NY;
         T corr[2][2][2];
         prolong_corr<T>(I, J, K, NX, NY, NZ, ec, corr);
 #pragma unroll
@@ -923,7 +938,7 @@ __device__ void tail_prolong(const TailLevel<T> &f, const T *ec)
 // descent: on each level but the coarsest, zero p (below the first), nu1 sweeps red then
 // black, residual restricted to the next level's b
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_tail_down(TailArgs<T> a)
+__global__ void __launch_bounds__(kTailDownThreads) k_tail_down(TailArgs<T> a)
 {
     for (int l = 0; l < a.nlev - 1; l++) {
         const TailLevel<T> v = a.lev[l];
@@ -943,7 +958,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_down(TailArgs<T> a)
 // ascent: from the level above the coarsest up, prolong the coarser correction, nu2 sweeps
 // black then red
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_tail_up(TailArgs<T> a)
+__global__ void __launch_bounds__(kTailUpThreads) k_tail_up(TailArgs<T> a)
 {
     for (int l = a.nlev - 2; l >= 0; l--) {
         const TailLevel<T> v = a.lev[l];
@@ -1789,7 +1804,7 @@ cudaError_t launch_tail_down(const TailArgs<T> &a, cudaStream_t s)
 {
     if (a.nlev < 2 || a.nlev > kTailMaxLevels) return cudaErrorInvalidValue;
     note_launch();
-    k_tail_down<T><<<1, kTailThreads, 0, s>>>(a);
+    k_tail_down<T><<<1, kTailDownThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename T>
@@ -1797,7 +1812,7 @@ cudaError_t launch_tail_up(const TailArgs<T> &a, cudaStream_t s)
 {
     if (a.nlev < 2 || a.nlev > kTailMaxLevels) return cudaErrorInvalidValue;
     note_launch();
-    k_tail_up<T><<<1, kTailThreads, 0, s>>>(a);
+    k_tail_up<T><<<1, kTailUpThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 template cudaError_t launch_tail_down<double>(const TailArgs<double> &, cudaStream_t);
