@@ -87,6 +87,12 @@ struct mg_ctx {
     LevelArrays<double> rk_b1, rk_b2, rk_ut, rk_us;
     double *rk_phis = nullptr;
     float *urow0 = nullptr;  // uniform-row values of the finest FP32 level (with split0)
+    // banded-row records of the finest FP32 level (with split0 and nx % 8 == 0), the two row
+    // counts of the last hierarchy build, and whether its sweeps use the records (more banded
+    // rows than uniform ones: a stretched grid)
+    float4 *arow0 = nullptr;
+    unsigned *rowcnt = nullptr;
+    bool banded = false;
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
     double *qbuf = nullptr;     // adjoint solution when the caller passes none
@@ -413,6 +419,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const bool fused = use_fused<T>(c, l) && palt_of<T>(c, l) != nullptr;
     const mg::Split sp = (sizeof(T) == 4 && l == 0) ? c->split0 : mg::Split{};
     const float *urow = (sizeof(T) == 4 && l == 0) ? c->urow0 : nullptr;
+    const float4 *arow = (sizeof(T) == 4 && l == 0 && c->banded) ? c->arow0 : nullptr;
     T *cur = p, *alt = palt_of<T>(c, l);
     // one red-black sweep, `first` colour first
     auto sweep = [&](int first) -> int {
@@ -425,8 +432,8 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
             std::swap(cur, alt);
         } else if (sp.half) {
             if constexpr (std::is_same<T, float>::value) {
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow));
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow, arow));
             }
         } else {
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
@@ -652,10 +659,17 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
             CK(mg::launch_diag_inv<float>(c->dims[l], c->L32[l].bx, c->L32[l].by, c->L32[l].bz, c->L32[l].dinv, s,
                                           nullptr, 1.0f));
         }
+        if (c->rowcnt) CK(cudaMemsetAsync(c->rowcnt, 0, 2 * sizeof(unsigned), s));
         if (c->urow0)
-            CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s));
+            CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s, c->arow0,
+                                       c->rowcnt));
     }
     CK(cudaStreamSynchronize(s));  // M's host staging buffer must outlive the copy
+    if (c->rowcnt) {
+        unsigned cnt[2] = {0, 0};
+        CK(cudaMemcpy(cnt, c->rowcnt, sizeof cnt, cudaMemcpyDeviceToHost));
+        c->banded = cnt[1] > cnt[0];
+    }
     return MG_OK;
 }
 
@@ -904,6 +918,10 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
         c->L32.resize(c->nlev);
         for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<float>(c, c->L32[l], c->dims[l].n(), true);
         if (st == MG_OK && c->split0.half) st = c->alloc(&c->urow0, (size_t)c->dims[0].ny * c->dims[0].nz);
+        if (st == MG_OK && c->split0.half && c->dims[0].nx % 8 == 0) {
+            st = c->alloc(&c->arow0, (size_t)c->dims[0].ny * c->dims[0].nz);
+            if (st == MG_OK) st = c->alloc(&c->rowcnt, 2);
+        }
         if (st != MG_OK) return bail(st);
     }
     if (c->o.krylov) {

@@ -111,12 +111,16 @@ template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
                           int z0 = 0, int z1 = -1);
 // one colour of a red-black sweep on the colour-split layout (FP32, all dims even); urow (optional):
-// the level's uniform-row values (launch_uniform_rows)
+// the level's uniform-row values, arow (optional, nx % 8 == 0, replaces urow in the sweep): its
+// banded-row records (launch_uniform_rows)
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s, const float *urow = nullptr);
-// urow[k*ny + j] = v if every face around row (j,k) but its two x-walls equals v, else 0
+                                cudaStream_t s, const float *urow = nullptr, const float4 *arow = nullptr);
+// urow[k*ny + j] = v if every face around row (j,k) but its two x-walls equals v, else 0; arow
+// (optional) = {vx, vy, vzl, vzh} if the row's x-, y-, low z- and high z-faces hold one value
+// each, else zeros; count (optional, two counters, incremented): uniform rows, banded rows that
+// are not uniform
 cudaError_t launch_uniform_rows(Dims d, const float *bx, const float *by, const float *bz, float *urow,
-                                cudaStream_t s);
+                                cudaStream_t s, float4 *arow = nullptr, unsigned *count = nullptr);
 // FP32 fused sweep with TMA-staged planes (mg_sweep_tma.cu)
 bool tma_sweep_supported(Dims d);
 cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, const float *b, const float *p_old,

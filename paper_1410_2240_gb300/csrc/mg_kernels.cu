@@ -321,27 +321,40 @@ __device__ __forceinline__ int row_parity(unsigned c, const Split &sp)
 // of every cell of row (j,k) except the two x-walls (bx at i = 0 and the high face of i = nx-1,
 // both walls, stored as 0) equals v bitwise, else 0; one warp per row.  A pass that reads urow[r]
 // != 0 takes its face values from it instead of loading them: the same values, so the same results.
+// On a grid stretched in z the metric factors differ per axis, and a row away from the interface
+// holds four values instead: vx on its x-faces, vy on its low and high y-faces, vzl on its low and
+// vzh on its high z-faces.  arow[r] (optional) = {vx, vy, vzl, vzh} for such a "banded" row, else
+// zeros; count[0] and count[1] (optional) receive the numbers of uniform rows and of banded rows
+// that are not uniform.
 __global__ void k_uniform_rows(int nx, int ny, int nz, const float *__restrict__ bx, const float *__restrict__ by,
-                               const float *__restrict__ bz, float *__restrict__ urow)
+                               const float *__restrict__ bz, float *__restrict__ urow, float4 *__restrict__ arow,
+                               unsigned *__restrict__ count)
 {
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     if (r >= ny * nz) return;
     const int j = r % ny, k = r / ny;
     const size_t sxy = (size_t)nx * ny, c0 = (size_t)r * nx;
-    const float v = by[c0];
-    const int vb = __float_as_int(v);
-    bool ok = v > 0.f && j < ny - 1 && k < nz - 1;
+    const bool inner = j < ny - 1 && k < nz - 1;
+    const float vy = by[c0], vx = nx > 1 ? bx[c0 + 1] : vy, vzl = bz[c0], vzh = inner ? bz[c0 + sxy] : 0.f;
+    const int bxv = __float_as_int(vx), byv = __float_as_int(vy), bzl = __float_as_int(vzl),
+              bzh = __float_as_int(vzh);
+    bool ok = inner && vx > 0.f && vy > 0.f && vzl > 0.f && vzh > 0.f;
     if (ok)  // warp-uniform; the loads of a lane's cells are independent of one another
         for (int i = lane; i < nx; i += 32) {
             const size_t c = c0 + i;
-            const bool cell = (i == 0 || __float_as_int(bx[c]) == vb) & (__float_as_int(by[c]) == vb) &
-                              (__float_as_int(by[c + nx]) == vb) & (__float_as_int(bz[c]) == vb) &
-                              (__float_as_int(bz[c + sxy]) == vb);
+            const bool cell = (i == 0 || __float_as_int(bx[c]) == bxv) & (__float_as_int(by[c]) == byv) &
+                              (__float_as_int(by[c + nx]) == byv) & (__float_as_int(bz[c]) == bzl) &
+                              (__float_as_int(bz[c + sxy]) == bzh);
             ok = ok & cell;
         }
     ok = __all_sync(0xffffffffu, ok);
-    if (lane == 0) urow[r] = ok ? v : 0.f;
+    if (lane == 0) {
+        const bool uni = ok && bxv == byv && bzl == byv && bzh == byv;
+        urow[r] = uni ? vy : 0.f;
+        if (arow) arow[r] = ok ? make_float4(vx, vy, vzl, vzh) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (count && ok) atomicAdd(&count[uni ? 0 : 1], 1u);
+    }
 }
 
 // One colour of red-black Gauss-Seidel on the colour-split layout (FP32, all dims even): the
@@ -399,11 +412,14 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
 // updates per thread keep more loads in flight than one, which the pass needs once uniform rows
 // have removed most of its bytes.  Each cell's arithmetic is k_smooth_split's, in its order.
 // OFF = (j + k + colour) & 1, the x offset of the colour in the row (uniform across a warp).
-template <int OFF>
+// BAND: the row's record is {vx, vy, vzl, vzh} of a banded row (all four equal on a uniform row,
+// zeros elsewhere), else {v, v, v, v} from urow.
+template <int OFF, bool BAND>
 __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, const LevelArrays<float> &L,
-                                            const float *__restrict__ b, float *__restrict__ p, int colour, float v,
+                                            const float *__restrict__ b, float *__restrict__ p, int colour, float4 rv,
                                             int g, int j, int k)
 {
+    const float v = rv.x;
     const int G = nx / 8;
     const size_t sxy = (size_t)nx * ny, half = sxy * nz / 2, hx = nx / 2, hxy = sxy / 2;
     const size_t mb = ((size_t)k * sxy + (size_t)j * nx) / 2 + 4 * g;
@@ -429,7 +445,9 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
         d[0] = u.x; d[1] = u.y; d[2] = u.z; d[3] = u.w; d[4] = w.x; d[5] = w.y; d[6] = w.z; d[7] = w.w;
     };
     // on a uniform row the diagonal is 6v, or 5v at an x-wall (the sums of inv_diag, in its
-    // order: 0 + v = v + 0 = v), so two divisions serve the thread's four cells
+    // order: 0 + v = v + 0 = v), so two divisions serve the thread's four cells; on a banded row
+    // the same with vx, vy, vzl, vzh in their places
+    const float vx = BAND ? rv.x : v, vy = BAND ? rv.y : v, vzl = BAND ? rv.z : v, vzh = BAND ? rv.w : v;
     float inv6 = 0.f, inv5 = 0.f;
     if (v == 0.f) {
         ld8(L.bx + c0, fbx);
@@ -438,6 +456,9 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
         if (j < ny - 1) ld8(L.by + c0 + nx, fbyh); else for (int q = 0; q < 8; q++) fbyh[q] = 0.f;
         ld8(L.bz + c0, fbz);
         if (k < nz - 1) ld8(L.bz + c0 + sxy, fbzh); else for (int q = 0; q < 8; q++) fbzh[q] = 0.f;
+    } else if (BAND) {
+        inv6 = 1.f / ((((((vx + vx) + vy) + vy) + vzl) + vzh));
+        inv5 = 1.f / ((((vx + vy) + vy) + vzl) + vzh);
     } else {
         const float s5 = (((v + v) + v) + v) + v;
         inv6 = 1.f / (s5 + v);
@@ -450,7 +471,7 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
         const int e = 2 * t + OFF;
         float bxl, bxh, byl, byh, bzl, bzh;
         if (v != 0.f) {
-            bxl = i > 0 ? v : 0.f; bxh = i < nx - 1 ? v : 0.f; byl = byh = bzl = bzh = v;
+            bxl = i > 0 ? vx : 0.f; bxh = i < nx - 1 ? vx : 0.f; byl = byh = vy; bzl = vzl; bzh = vzh;
         } else {
             bxl = fbx[e]; bxh = i < nx - 1 ? fbx[e + 1] : 0.f;
             byl = fby[e]; byh = fbyh[e]; bzl = fbz[e]; bzh = fbzh[e];
@@ -469,15 +490,23 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
     }
     *reinterpret_cast<float4 *>(own + mb) = make_float4(out[0], out[1], out[2], out[3]);
 }
+template <bool BAND>
 __global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
-                         float *__restrict__ p, int colour, const float *__restrict__ urow)
+                                float *__restrict__ p, int colour, const float *__restrict__ urow,
+                                const float4 *__restrict__ arow)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     if (g >= nx / 8 || j >= ny) return;
-    const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
-    if ((j + k + colour) & 1) split4_body<1>(nx, ny, nz, h2, L, b, p, colour, v, g, j, k);
-    else split4_body<0>(nx, ny, nz, h2, L, b, p, colour, v, g, j, k);
+    float4 rv;
+    if (BAND) {
+        rv = arow[(size_t)k * ny + j];
+    } else {
+        const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
+        rv = make_float4(v, v, v, v);
+    }
+    if ((j + k + colour) & 1) split4_body<1, BAND>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
+    else split4_body<0, BAND>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
 }
 
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
@@ -1703,13 +1732,16 @@ template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> 
                                           cudaStream_t, int, int);
 
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s, const float *urow)
+                                cudaStream_t s, const float *urow, const float4 *arow)
 {
     note_launch();
     if (d.nx % 8 == 0) {  // four cells per thread, blocks of 32 threads x 4 rows
         const int G = d.nx / 8;
-        k_smooth_split4<<<dim3((G + 31) / 32, (d.ny + 3) / 4, d.nz), dim3(32, 4), 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p,
-                                                                                         colour, urow);
+        const dim3 grid((G + 31) / 32, (d.ny + 3) / 4, d.nz), block(32, 4);
+        if (arow)
+            k_smooth_split4<true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow);
+        else
+            k_smooth_split4<false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, nullptr);
     } else {
         k_smooth_split<<<row_grid(d.nx / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour,
                                                                               urow);
@@ -1718,11 +1750,12 @@ cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, c
 }
 
 cudaError_t launch_uniform_rows(Dims d, const float *bx, const float *by, const float *bz, float *urow,
-                                cudaStream_t s)
+                                cudaStream_t s, float4 *arow, unsigned *count)
 {
     const int rows = d.ny * d.nz, warps = 8;
     note_launch();
-    k_uniform_rows<<<(rows + warps - 1) / warps, 32 * warps, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, urow);
+    k_uniform_rows<<<(rows + warps - 1) / warps, 32 * warps, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, urow, arow,
+                                                                      count);
     return cudaGetLastError();
 }
 

@@ -79,3 +79,51 @@ def test_uniform_widths_match_uniform_context(mgp):
     assert np.linalg.norm(host(p_s) - pu) <= 1e-9 * np.linalg.norm(pu)
     for a, b in zip(faces_host(u_s), faces_host(u_u)):
         assert np.abs(a - b).max() <= 1e-9 * max(np.abs(b).max(), 1.0)
+
+
+def _row_kinds(bx, by, bz):
+    """Numbers of uniform and of banded-but-not-uniform interior rows (every x-face but the wall,
+    the low and high y-faces, the low and the high z-faces each holding one positive value)."""
+    nz, ny, nx = bx.shape
+    uni = band = 0
+    for k in range(nz - 1):
+        for j in range(ny - 1):
+            vx, vy, vzl, vzh = bx[k, j, 1], by[k, j, 0], bz[k, j, 0], bz[k + 1, j, 0]
+            ok = (vx > 0 and vy > 0 and vzl > 0 and vzh > 0 and np.all(bx[k, j, 1:] == vx)
+                  and np.all(by[k, j] == vy) and np.all(by[k, j + 1] == vy) and np.all(bz[k, j] == vzl)
+                  and np.all(bz[k + 1, j] == vzh))
+            if ok and vx == vy == vzl == vzh:
+                uni += 1
+            elif ok:
+                band += 1
+    return uni, band
+
+
+def test_z_stretched_banded_rows_bit_identical_to_fused_sweeps(mgp):
+    """On a grid stretched in z alone the rows away from the interface hold four face values (x,
+    y, low z, high z); the colour passes take them from per-row records instead of loading the
+    faces.  The mixed projection (stationary refinement: CG's FP32 dot products would sum the
+    colour-split and the natural layout in different orders) must equal, bit for bit, the one whose
+    fused sweeps load every face."""
+    # a level interface (the face values of a row then depend on its plane alone) and a body, so
+    # that both banded rows and rows whose faces are loaded occur
+    case = synth.small_case(32, 32, 32, seed=7, solid="ellipsoid", interface="flat")
+    h = case.h
+    hx = np.full(32, h)
+    hy = np.full(32, h)
+    hz = _widths(32, 3.5, 0.2)
+    beta = O.face_coeffs(case.phi, case.solid, case.lam)
+    bo, ao = mgp.stretched_metrics(dev(hx), dev(hy), dev(hz), faces_dev(beta))
+    coef = [(a * b).astype(np.float32) for a, b in zip(faces_host(ao), faces_host(bo))]
+    uni, band = _row_kinds(*coef)
+    assert band > uni and band < 31 * 31, (uni, band)
+    out = []
+    for sm in (1, 2):
+        ctx = mgp.Context(bo, 1.0, prec="mixed", smoother=sm, coarse_max_cells=2048)
+        ctx.set_face_areas(ao)
+        u_g, p_g, st = ctx.project(faces_dev(case.u_star), tol=1e-10)
+        out.append((p_g, u_g, st.cycles))
+    assert out[0][2] == out[1][2]
+    assert torch.equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert torch.equal(a, b)
