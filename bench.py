@@ -25,6 +25,7 @@ independent replica of the workload (the projection is a single-GPU problem here
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -51,7 +52,7 @@ SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p and b, unif
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
 # DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split4 colour
 # passes) from an ncu capture of this workload (profiles/k_smooth_split4_256_colour_pass.md)
-SWEEP_TRAFFIC_256 = 119.531520e6 + 18.950400e6 + 119.533056e6 + 18.479616e6
+SWEEP_TRAFFIC_256 = 119.535104e6 + 18.796544e6 + 119.535360e6 + 18.866944e6
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))
 
@@ -305,6 +306,15 @@ def time_steps(step, K, W, world):
     return ms, step.mg.kernel_launches() - launches0
 
 
+def release():
+    """Free the device memory of the legs already timed now: a context left to a later garbage
+    collection would release its buffers (and synchronize the device) inside another leg's timing."""
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
 def e2e_leg(case, K, W):
     """The same step through the public autograd API with pinned host buffers."""
     import torch
@@ -433,7 +443,7 @@ def run_ours(args):
     solve_ms_total = sum(step.solve_ms)  # the solves alone (CUDA events inside the library)
     p_mixed = step.p.detach().cpu().numpy() if rank == 0 else None
     del step
-    torch.cuda.empty_cache()
+    release()
     # per-kernel times from a second context that records CUDA events around every finest-grid
     # kernel (kept out of the headline timing above)
     prof, Kp, sweep_ms, achieved = {}, 0, None, None
@@ -447,7 +457,7 @@ def run_ours(args):
         achieved = B_SWEEP32 * n / (sweep_ms / 1e3) / 1e9
         prof = {g: pstep.ctx.profile_read(i) for g, i in PROF_GROUPS}
         del pstep
-        torch.cuda.empty_cache()
+        release()
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -476,7 +486,7 @@ def run_ours(args):
                 "kernel_ms": {g: dict(zip(("launches", "ms"), s64.ctx.profile_read(i))) for g, i in PROF_GROUPS}}
         p64 = s64.p.detach().cpu().numpy() if rank == 0 else None
         del s64
-        torch.cuda.empty_cache()
+        release()
     else:
         p64 = None
 
