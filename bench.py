@@ -86,6 +86,8 @@ def parse_args():
                     help="V-cycles per preconditioner application (krylov 1) or per refinement step (krylov 0)")
     ap.add_argument("--inner64", type=int, default=1, help="the same for the plain FP64 comparison solve")
     ap.add_argument("--smoother", type=int, default=0, help="0 auto, 1 per colour, 2 fused, 3 fused + TMA")
+    ap.add_argument("--coarse-tail", type=int, default=1,
+                    help="smallest levels: 0 a launch per pass, 1 one CTA (coarse_tail option)")
     ap.add_argument("--krylov", type=int, default=1,
                     help="1: conjugate gradients preconditioned by the V-cycle (default); 0: stationary V-cycles")
     return ap.parse_args()
@@ -425,7 +427,8 @@ def run_ours(args):
     K, W = args.steps, max(args.warmup, 3)
 
     # ---- mixed (headline) ----
-    opts = {"inner_cycles": args.inner, "smoother": args.smoother, "krylov": args.krylov, "krylov": args.krylov}
+    opts = {"inner_cycles": args.inner, "smoother": args.smoother, "krylov": args.krylov,
+            "coarse_tail": args.coarse_tail}
     step = Step(case, "mixed", profile=0, **opts)
     dev_uuid = None
     try:
@@ -471,7 +474,8 @@ def run_ours(args):
     # ---- plain FP64 on the same step ----
     fp64 = None
     if not args.no_fp64:
-        s64 = Step(case, "fp64", profile=1, smoother=args.smoother, krylov=args.krylov, inner_cycles=args.inner64)
+        s64 = Step(case, "fp64", profile=1, smoother=args.smoother, krylov=args.krylov, inner_cycles=args.inner64,
+                   coarse_tail=args.coarse_tail)
         K64 = max(2, K // 2)
         ms64, _ = time_steps(s64, K64, 3, world)
         sps64, ms64 = replica_throughput(ms64, 2 * K64, world)
