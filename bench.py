@@ -47,6 +47,13 @@ B_VCYCLE32 = 145.0    # V(2,2), all levels, FP32: (4 sweeps x 24 + residual/rest
 B_VCYCLE64 = 322.0    # V(2,2), all levels, FP64
 B_RESID64 = 48.0      # FP64 residual + norm (p, b, bx, by, bz read; dinv mask)
 B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
+B_CG_ITER = 48.0 + 52.0 + 20.0 + 12.0  # one CG iteration's vectors: q = A d, p/r/r32 update, direction, dots
+
+
+def iteration_bytes(inner, vcycle_bytes, krylov, resid_bytes):
+    """Algorithmic bytes per finest cell of one outer iteration: `inner` V-cycles plus the CG vector
+    work (krylov) or the refinement step's residual and accumulation."""
+    return inner * vcycle_bytes + (B_CG_ITER if krylov else resid_bytes)
 SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
                 1: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
@@ -73,6 +80,10 @@ def parse_args():
     ap.add_argument("--pcg-scaling", action="store_true",
                     help="instead of the benchmark: iterations and solve time of Jacobi-preconditioned CG and of "
                          "multigrid (stationary, and preconditioning CG) on one geometry at 64^3, 128^3, 256^3")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="instead of the benchmark: the CPU oracle's full solve to 1e-10 on the 32^3, 128^3 and "
+                         "256^3 workloads, on all host cores and on one (a child process each)")
+    ap.add_argument("--oracle-solve", default=None, help=argparse.SUPPRESS)  # child of --oracle-timing
     ap.add_argument("--rk2", action="store_true",
                     help="instead of the benchmark: Runge-Kutta time steps (two projections, gravity, upwind VOF) "
                          "per second on the 256^3 workload, from the same state each step")
@@ -330,20 +341,24 @@ def e2e_leg(case, K, W):
     o_gu = tuple(torch.empty_like(x).pin_memory() for x in h_u)
     o_gphi = torch.empty_like(h_phi).pin_memory()
 
-    # the loss weights w are uploaded while the forward solve runs, and the projected
-    # velocity is read back while the backward solve runs, on a second stream
+    # the inputs go into device buffers allocated once; the loss weights w are uploaded while the
+    # forward solve runs, and the projected velocity is read back while the backward solve runs,
+    # on a second stream
     side = torch.cuda.Stream()
+    d_phi = torch.empty_like(h_phi, device="cuda")
+    d_solid = torch.empty_like(h_solid, device="cuda") if h_solid is not None else None
+    d_u = tuple(torch.empty_like(x, device="cuda") for x in h_u)
+    d_w = tuple(torch.empty_like(x, device="cuda") for x in h_w)
 
     def one():
         main = torch.cuda.current_stream()
-        phi = h_phi.to("cuda", non_blocking=True).requires_grad_(True)
-        solid = h_solid.to("cuda", non_blocking=True) if h_solid is not None else None
-        u = tuple(x.to("cuda", non_blocking=True).requires_grad_(True) for x in h_u)
+        d_phi.copy_(h_phi, non_blocking=True)
+        phi = d_phi.detach().requires_grad_(True)
+        solid = d_solid.copy_(h_solid, non_blocking=True) if h_solid is not None else None
+        u = tuple(d.copy_(x, non_blocking=True).detach().requires_grad_(True) for d, x in zip(d_u, h_u))
         side.wait_stream(main)
         with torch.cuda.stream(side):
-            w = tuple(x.to("cuda", non_blocking=True) for x in h_w)
-        for x in w:
-            x.record_stream(main)
+            w = tuple(d.copy_(x, non_blocking=True) for d, x in zip(d_w, h_w))
         w_ready = side.record_event()
         (ux, uy, uz), p = project(u, phi, case.h, solid=solid, rho_air=case.lam, tol=TOL, precision="mixed")
         side.wait_stream(main)
@@ -468,7 +483,8 @@ def run_ours(args):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    mixed_vcycle_gbs = (B_VCYCLE32 + B_REFINE) * n * steps_total / (solve_ms_total / 1e3) / 1e9
+    mixed_vcycle_gbs = (iteration_bytes(args.inner, B_VCYCLE32, args.krylov, B_REFINE) * n * steps_total
+                        / (solve_ms_total / 1e3) / 1e9)
 
 
     # ---- plain FP64 on the same step ----
@@ -485,7 +501,8 @@ def run_ours(args):
         tot64 = sum(a + b for a, b in s64.cycles)
         fp64 = {"solves_per_s": sps64, "ms_per_step": ms64 / K64, "inner_cycles": args.inner64,
                 "cycles_fwd_bwd": list(cyc64),
-                "vcycle_hbm_gbs": (B_VCYCLE64 + B_RESID64) * n * tot64 / (sum(s64.solve_ms) / 1e3) / 1e9,
+                "vcycle_hbm_gbs": (iteration_bytes(args.inner64, B_VCYCLE64, args.krylov, B_RESID64) * n * tot64
+                                   / (sum(s64.solve_ms) / 1e3) / 1e9),
                 "fine_sweep_ms": sweep64, "fine_sweep_gbs": B_SWEEP64 * n / (sweep64 / 1e3) / 1e9,
                 "kernel_ms": {g: dict(zip(("launches", "ms"), s64.ctx.profile_read(i))) for g, i in PROF_GROUPS}}
         p64 = s64.p.detach().cpu().numpy() if rank == 0 else None
@@ -517,6 +534,10 @@ def run_ours(args):
         "clocks": clk,
     }
     out["projections_per_s"] = value / 2.0  # one projection step = forward + adjoint
+    # fine-cell V-cycles per second (all V-cycles of the timed steps over the solves' own time)
+    # and smoother cell updates per second (cells / time of one finest-grid sweep)
+    out["fine_cell_vcycles_per_s"] = n * args.inner * steps_total / (solve_ms_total / 1e3)
+    out["smoother_cell_updates_per_s"] = n / (sweep_ms / 1e3) if sweep_ms else None
     out["kernel_gbs"] = kernel_gbs(out["kernel_ms"], n)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_leg(case, max(4, K // 2), 3)
@@ -660,9 +681,54 @@ def rk2_bench(args):
                                  "dt": dt, "g": g, "precision": "mixed"}}))
 
 
+ORACLE_CASES = {"c1_32": "32^3, gently waved interface, no solid, rhs ~ N(0,1)",
+                "c2_128": "128^3, 4-mode free surface + piercing ellipsoid, rhs = D u*",
+                "c3_256": "256^3, as 128^3 (the benchmark's workload)"}
+
+
+def oracle_solve(name):
+    """One timed FP64 oracle solve (face coefficients + rhs + hierarchy + stationary V(2,2) cycles to
+    1e-10) in this process, with the OpenMP threads its environment gives; prints a JSON line."""
+    import oracle as O
+    from paper_1410_2240_gb300 import synth
+    case = {"c1_32": lambda: synth.case_c1(32), "c2_128": lambda: synth.case_c2(128),
+            "c3_256": lambda: synth.case_c3(256)}[name]()
+    t0 = time.perf_counter()
+    beta = O.face_coeffs(case.phi, case.solid, case.lam)
+    rhs = case.rhs if case.rhs is not None else O.divergence(beta, case.u_star, case.h)
+    mg = O.MG(beta, case.h)
+    t1 = time.perf_counter()
+    _, cyc, _ = mg.solve(rhs, tol=TOL, max_cycles=200)
+    t2 = time.perf_counter()
+    print(json.dumps({"setup_s": t1 - t0, "solve_s": t2 - t1, "cycles": abs(cyc)}))
+
+
+def oracle_timing(args):
+    """The CPU oracle timed on this host: each workload's full solve with all cores and with one,
+    each in a child process (the oracle's OpenMP thread count is fixed when it loads)."""
+    cores = os.cpu_count() or 1
+    rows = []
+    for name, what in ORACLE_CASES.items():
+        for threads in (cores, 1):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-solve", name], env=env,
+                                 capture_output=True, text=True, check=True)
+            r = json.loads(out.stdout.strip().splitlines()[-1])
+            total = r["setup_s"] + r["solve_s"]
+            rows.append({"workload": name, "what": what, "threads": threads, "cycles": r["cycles"],
+                         "setup_s": round(r["setup_s"], 3), "solve_s": round(r["solve_s"], 3),
+                         "solves_per_s": 1.0 / total})
+    print(json.dumps({"metric": "CPU oracle solves/s to 1e-10 (FP64, stationary V(2,2))", "unit": "solves/s",
+                      "kind": "oracle", "host_cores": cores, "rows": rows}))
+
+
 def main():
     args = parse_args()
-    if args.pcg_scaling:
+    if args.oracle_solve:
+        oracle_solve(args.oracle_solve)
+    elif args.oracle_timing:
+        oracle_timing(args)
+    elif args.pcg_scaling:
         pcg_scaling(args)
     elif args.rk2:
         rk2_bench(args)
