@@ -747,10 +747,10 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
         CKS(precondition());
         if (mixed) {
             CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, nullptr, c->partials, c->dscal, sc_cur, sc_cur, -1, s));
-            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 1, s, c->split0));
+            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, -1, 1, s, c->split0));
         } else {
             CK(mg::launch_pcg_dots<double>(n, c->kr, z, nullptr, c->partials, c->dscal, -1, -1, s));
-            CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, 1, s));
+            CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, -1, 1, s));
         }
         for (;;) {
             it++;
@@ -764,7 +764,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             {
                 ProfScope ps(c, MG_PROF_RESID64, true);
                 CK(mg::launch_pcg_update(n, c->kd, c->kq, p, c->kr, mixed ? c->L32[0].b : nullptr, c->partials, c->dscal,
-                                         sc_cur, s, c->split0));
+                                         sc_cur, mixed ? sc_old : -1, s, c->split0));
             }
             CKS(read_scalars(c));
             rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
@@ -775,10 +775,10 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
             if (mixed) {
                 CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, e_old, c->partials, c->dscal, sc_cur, sc_cur, sc_old,
                                          s));
-                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, 0, s, c->split0));
+                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, sc_old, 0, s, c->split0));
             } else {
                 CK(mg::launch_pcg_dots<double>(n, c->kr, z, zo, c->partials, c->dscal, -1, -1, s));
-                CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, 0, s));
+                CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, -1, 0, s));
             }
         }
         if (!std::isfinite(rel)) {

@@ -170,14 +170,18 @@ cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const 
                               double *dscal, int sr_slot, int sz_slot, int so_slot, cudaStream_t s);
 // z = scale * dinv * r (the Jacobi preconditioner of the CG)
 cudaError_t launch_jacobi(size_t n, double scale, const double *dinv, const double *r, double *z, cudaStream_t s);
+// d = D, the CG direction divided by the scale of its preconditioned residual (dscal[sz_slot]);
+// so_slot: the scale of the previous D (-1 on the first direction or without scales)
 template <typename Z>
-cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s,
-                           Split sp = {});
+cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int so_slot, int first,
+                           cudaStream_t s, Split sp = {});
 // op: face coefficients and diagonal pre-scaled by h^-2 (op.dinv holds the scaled diagonal)
 cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double *dv, double *q, double *partials,
                              double *dscal, cudaStream_t s);
+// sd_slot: the scale of the direction dv (its k_pcg_dir's sz_slot; -1 without scales)
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
-                              double *partials, double *dscal, int scale_slot, cudaStream_t s, Split sp = {});
+                              double *partials, double *dscal, int scale_slot, int sd_slot, cudaStream_t s,
+                              Split sp = {});
 
 // projection and adjoint
 cudaError_t launch_divergence(Dims d, double scale, const double *bx, const double *by, const double *bz,

@@ -1526,13 +1526,18 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
     }
 }
 
-// d = sz * Z + beta d,  beta = (<r,z> - <r,z_old>) / <r_old, z_old>  (first: beta = 0)
+// The search direction d = sz Z + beta d_old, beta = (<r,z> - <r,z_old>) / <r_old, z_old> (first:
+// beta = 0), with z = sz Z the preconditioned residual, is kept divided by its z's scale: D = d / sz
+// = Z + (beta so / sz) D_old (so: the scale of D_old), one FP64 operation per cell.  The CG
+// update then moves p and r by <r,z> / (sz <D, A D>) times D and A D (k_pcg_update), the same
+// step.  Without scales (sz_slot, so_slot < 0) D = d.
 template <typename Z>
 __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, const double *__restrict__ dscal,
-                          int sz_slot, int first, Split sp)
+                          int sz_slot, int so_slot, int first, Split sp)
 {
-    const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
-    const double beta = first ? 0.0 : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ];
+    const double beta = first ? 0.0
+                              : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ] *
+                                    (so_slot >= 0 ? dscal[so_slot] / dscal[sz_slot] : 1.0);
     const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
     double2 *d2 = reinterpret_cast<double2 *>(d);
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
@@ -1544,12 +1549,12 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
         }
         const double z0 = widen(z[i0]), z1 = widen(z[i1]);
         double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
-        dv.x = fma(beta, dv.x, sz * z0);
-        dv.y = fma(beta, dv.y, sz * z1);
+        dv.x = fma(beta, dv.x, z0);
+        dv.y = fma(beta, dv.y, z1);
         d2[v] = dv;
     }
     for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride)
-        d[idx] = fma(beta, first ? 0.0 : d[idx], sz * widen(z[idx]));
+        d[idx] = fma(beta, first ? 0.0 : d[idx], widen(z[idx]));
 }
 
 __global__ void k_pcg_shift_rz(double *dscal) { dscal[S_RZ] = dscal[S_RZN]; }
@@ -1599,9 +1604,11 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, LevelArrays<double> L, const
 // scale = RMS of the previous residual (written to scale_slot).  Two elements per iteration.
 __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
                              double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
-                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, Split sp)
+                             double *__restrict__ dscal, int scale_slot, int sd_slot, double *__restrict__ partials,
+                             Split sp)
 {
-    const double alpha = dscal[S_RZ] / dscal[S_SIGMA];
+    // d holds D = (direction) / sd (k_pcg_dir): alpha = <r,z> / <d, A d> times sd
+    const double alpha = dscal[S_RZ] / (dscal[S_SIGMA] * (sd_slot >= 0 ? dscal[sd_slot] : 1.0));
     double inv_scale = 1.0;
     if (r32) {
         const double rms = sqrt(dscal[S_RR] / dscal[S_NLIVE]);
@@ -2079,18 +2086,21 @@ template cudaError_t launch_pcg_dots<float>(size_t, const double *, const float 
                                             int, int, cudaStream_t);
 
 template <typename Z>
-cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int first, cudaStream_t s,
-                           Split sp)
+cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int so_slot, int first,
+                           cudaStream_t s, Split sp)
 {
     if (sp.half && sizeof(Z) != 4) return cudaErrorInvalidValue;  // FP64 fields are never split
+    if (so_slot >= 0 && sz_slot < 0) return cudaErrorInvalidValue;
     note_launch();
-    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, first, sp);
+    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, so_slot, first, sp);
     note_launch();
     k_pcg_shift_rz<<<1, 1, 0, s>>>(dscal);
     return cudaGetLastError();
 }
-template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, cudaStream_t, Split);
-template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, cudaStream_t, Split);
+template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, int, cudaStream_t,
+                                            Split);
+template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, int, cudaStream_t,
+                                           Split);
 
 cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double *dv, double *q, double *partials,
                              double *dscal, cudaStream_t s)
@@ -2104,11 +2114,12 @@ cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double
 }
 
 cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, double *p, double *r, float *r32,
-                              double *partials, double *dscal, int scale_slot, cudaStream_t s, Split sp)
+                              double *partials, double *dscal, int scale_slot, int sd_slot, cudaStream_t s, Split sp)
 {
     const unsigned g = red_grid(n);
+    if (sd_slot >= 0 && sd_slot == scale_slot) return cudaErrorInvalidValue;  // read and written by the kernel
     note_launch();
-    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, partials, sp);
+    k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, sd_slot, partials, sp);
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, -1);
     return cudaGetLastError();
