@@ -68,3 +68,23 @@ def test_reference_arm_prints_contract_line_small_grid():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_timing_child_times_a_full_solve():
+    """The child of --oracle-timing: one oracle solve of the 32^3 workload on one thread, its
+    setup and solve seconds and its V-cycle count as JSON (the cycle count is the oracle's own)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-solve", "c1_32"], env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["setup_s"] > 0 and line["solve_s"] > 0
+    assert 5 <= line["cycles"] <= 40
+
+
+def test_iteration_bytes_count_every_v_cycle():
+    sys.path.insert(0, ROOT)
+    import bench
+    # two FP32 V-cycles and the CG vectors per iteration; one cycle and the refinement step otherwise
+    assert bench.iteration_bytes(2, bench.B_VCYCLE32, 1, bench.B_REFINE) == 2 * bench.B_VCYCLE32 + bench.B_CG_ITER
+    assert bench.iteration_bytes(1, bench.B_VCYCLE64, 0, bench.B_RESID64) == bench.B_VCYCLE64 + bench.B_RESID64
