@@ -4,6 +4,7 @@ The mistake is planted in a temporary copy of oracle/mg_oracle.c compiled on the
 the pins of test_oracle_operator / test_oracle_solver then run against that copy and
 at least one of them must fail.  The real oracle is restored afterwards.
 """
+import inspect
 import os
 import subprocess
 import tempfile
@@ -112,3 +113,37 @@ def test_planted_mistake_is_caught(name, orig, mut, pins, tmp_path):
         assert any(caught), f"no pin caught the mutant '{name}'"
     finally:
         O.use_library(None)
+
+
+# Mistakes planted in the oracle's Python steps (the time step of the Numerical Time Integration
+# section): (name, function, original text, mutated text, pins that must catch it)
+PY_MUTANTS = [
+    ("body force points up", "body_force", "np.where(beta[2] > 0, -g, 0.0)", "np.where(beta[2] > 0, g, 0.0)",
+     [T5.test_rk2_hydrostatic_column_stays_at_rest]),
+    ("second stage drops the 1/2 of Eq. runge2", "rk2_step",
+     "u1 = tuple(0.5 * x for x in correct(beta2, P, ut2, h, dt))", "u1 = tuple(correct(beta2, P, ut2, h, dt))",
+     [T5.test_rk2_keeps_divergence_free_velocity_without_forces]),
+    ("second stage leaves u^k out of Eq. poisson2", "rk2_step",
+     "ut2 = tuple((a + b) + dt * r for a, b, r in zip(us, u, R2))", "ut2 = tuple(a + dt * r for a, r in zip(us, R2))",
+     [T5.test_rk2_keeps_divergence_free_velocity_without_forces]),
+    ("second projection solved with the first stage's density", "rk2_step",
+     "P = solve(beta2, divergence(beta2, ut2, h, dt), h, tol=tol)", "P = solve(beta, divergence(beta, ut2, h, dt), h, tol=tol)",
+     [T5.test_rk2_returns_divergence_free_velocity]),
+]
+
+
+@pytest.mark.parametrize("name,fname,orig,mut,pins", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_planted_python_mistake_is_caught(name, fname, orig, mut, pins, monkeypatch):
+    src = inspect.getsource(getattr(O, fname))
+    assert src.count(orig) == 1, f"mutation anchor not found: {orig}"
+    ns = dict(vars(O))
+    exec(compile(src.replace(orig, mut, 1), f"<mutant {name}>", "exec"), ns)
+    monkeypatch.setattr(O, fname, ns[fname])
+    caught = []
+    for pin in pins:
+        try:
+            pin()
+            caught.append(False)
+        except (AssertionError, RuntimeError, ValueError, ZeroDivisionError, FloatingPointError):
+            caught.append(True)
+    assert any(caught), f"no pin caught the mutant '{name}'"

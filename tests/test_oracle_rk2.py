@@ -65,8 +65,12 @@ def test_rk2_hydrostatic_column_stays_at_rest():
     u1, phi1, P = O.rk2_step(case.phi, None, zero, case.h, dt, g, lam=case.lam, tol=1e-12)
     assert max(np.abs(x).max() for x in u1) <= 1e-9 * dt * g
     assert np.abs(phi1 - case.phi).max() <= 1e-9
-    # the pressure is hydrostatic: dP/dz = -rho g on the z-faces
-    assert np.ptp(P) > 0.1 * g * case.shape[0] * case.h * case.lam
+    # the pressure is hydrostatic: at rest the correction cancels the body force face by face,
+    # so on every interior z-face (P_k - P_{k-1}) / h = -g / beta_z = -g (rho_{k-1} + rho_k) / 2
+    rho = case.lam + (1.0 - case.lam) * case.phi
+    slope = (P[1:] - P[:-1]) / case.h
+    expect = -g * 0.5 * (rho[1:] + rho[:-1])
+    assert np.abs(slope - expect).max() <= 1e-8 * g
 
 
 def test_rk2_keeps_divergence_free_velocity_without_forces():
