@@ -187,8 +187,12 @@ def test_adjoint_with_areas_linearity_and_phi():
     du = tuple(rng.standard_normal(case.shape) for _ in range(3))
     lin = L(tuple(a + b for a, b in zip(case.u_star, du)), case.phi) - L(case.u_star, case.phi)
     assert lin == pytest.approx(sum(float((g * d).sum()) for g, d in zip(gu, du)), rel=1e-9)
-    # phi: a few interface cells
-    idx = np.argwhere((case.phi > 0.05) & (case.phi < 0.95))[:4]
+    # phi: a few interface cells, and a few cells whose low x-face the body cuts (0 < a < 1),
+    # where the area enters the coefficient gradient
+    idx = list(np.argwhere((case.phi > 0.05) & (case.phi < 0.95))[:4])
+    cut = np.argwhere((areas[0] > 0) & (areas[0] < 1))
+    assert len(cut) >= 4
+    idx += list(cut[np.random.default_rng(11).choice(len(cut), size=4, replace=False)])
     for (k, j, i) in idx:
         def Lphi(e):
             ph = case.phi.copy()

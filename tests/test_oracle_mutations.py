@@ -116,7 +116,8 @@ def test_planted_mistake_is_caught(name, orig, mut, pins, tmp_path):
 
 
 # Mistakes planted in the oracle's Python steps (the time step of the Numerical Time Integration
-# section): (name, function, original text, mutated text, pins that must catch it)
+# section, the fractional-area and stretched projections): (name, function, original text, mutated
+# text, pins that must catch it)
 PY_MUTANTS = [
     ("body force points up", "body_force", "np.where(beta[2] > 0, -g, 0.0)", "np.where(beta[2] > 0, g, 0.0)",
      [T5.test_rk2_hydrostatic_column_stays_at_rest]),
@@ -129,6 +130,17 @@ PY_MUTANTS = [
     ("second projection solved with the first stage's density", "rk2_step",
      "P = solve(beta2, divergence(beta2, ut2, h, dt), h, tol=tol)", "P = solve(beta, divergence(beta, ut2, h, dt), h, tol=tol)",
      [T5.test_rk2_returns_divergence_free_velocity]),
+    ("cut-cell operator without the area", "area_coeffs", "np.where(a > 0, a * b, 0.0)", "np.where(a > 0, b, 0.0)",
+     [lambda: T3.test_projection_with_areas_is_divergence_free(False)]),
+    ("cut-cell correction weighted by the area", "open_mask", "np.where(a > 0, b, 0.0)", "np.where(a > 0, a * b, 0.0)",
+     [lambda: T3.test_projection_with_areas_is_divergence_free(False)]),
+    ("adjoint grad_u* without the area", "project_adjoint_area", "np.where(a > 0, x - a * g, x)",
+     "np.where(a > 0, x - g, x)", [T3.test_adjoint_with_areas_linearity_and_phi]),
+    ("adjoint grad_beta without the area", "project_adjoint_area", "dt * gpp * (a * g - x)", "dt * gpp * (g - x)",
+     [T3.test_adjoint_with_areas_linearity_and_phi]),
+    ("stretched correction with the physical spacing", "project_stretched",
+     "u = correct(open_mask(area, bi), p, u_star, 1.0, dt)", "u = correct(open_mask(area, bi), p, u_star, hz[0], dt)",
+     [T4.test_uniform_widths_reproduce_uniform_projection, T4.test_stretched_projection_divergence_free]),
 ]
 
 
