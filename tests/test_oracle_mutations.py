@@ -130,6 +130,14 @@ PY_MUTANTS = [
     ("second projection solved with the first stage's density", "rk2_step",
      "P = solve(beta2, divergence(beta2, ut2, h, dt), h, tol=tol)", "P = solve(beta, divergence(beta, ut2, h, dt), h, tol=tol)",
      [T5.test_rk2_returns_divergence_free_velocity]),
+    ("projection rhs not divided by dt", "project", "rhs = divergence(beta, u_star, h, dt)",
+     "rhs = divergence(beta, u_star, h, 1.0)", [T2.test_projection_is_divergence_free_and_idempotent]),
+    ("adjoint rhs without beta", "project_adjoint", "bw = tuple(b * x for b, x in zip(beta, w))",
+     "bw = tuple(x for b, x in zip(beta, w))", [T2.test_projection_dot_product_test]),
+    ("adjoint grad_u* sign of G q", "project_adjoint", "np.where(b > 0, x - g, x)", "np.where(b > 0, x + g, x)",
+     [T2.test_adjoint_u_gradient_is_exact_for_linear_loss]),
+    ("adjoint grad_beta drops dt", "project_adjoint", "dt * a * (g - x)", "a * (g - x)",
+     [T2.test_adjoint_phi_gradient_central_differences]),
     ("cut-cell operator without the area", "area_coeffs", "np.where(a > 0, a * b, 0.0)", "np.where(a > 0, b, 0.0)",
      [lambda: T3.test_projection_with_areas_is_divergence_free(False)]),
     ("cut-cell correction weighted by the area", "open_mask", "np.where(a > 0, b, 0.0)", "np.where(a > 0, a * b, 0.0)",
