@@ -189,7 +189,9 @@ int mg_face_areas(const mg_grid *g, const double *psi_nodes, double *const area_
  * 1/rho_f; mg_project_adjoint uses the areas in its gradients.  area: device,
  * three low-face arrays in [0, 1] (mg_face_areas), copied; NULL returns to
  * whole faces.  Rebuilds the hierarchy (as mg_update).  Cells are not merged:
- * a cut cell of small open area stays a cell of small coefficients.
+ * a cut cell of small open area stays a cell of small coefficients.  Returns
+ * MG_OK, MG_ERR_ARG (null context, null or unaligned array), MG_ERR_OOM (the
+ * area arrays are allocated on first use) or MG_ERR_CUDA.
  */
 int mg_set_face_areas(mg_ctx *c, const double *const area[3]);
 
@@ -201,6 +203,8 @@ int mg_set_face_areas(mg_ctx *c, const double *const area[3]);
  * through the cell's open face parts (Gauss's theorem), so this adds the body
  * term; in cells the body does not cut, the discrete divergence of a rigid
  * motion is zero.  v: device, three face arrays, copied; NULL: a static body.
+ * Returns MG_OK, MG_ERR_ARG (null context, null or unaligned array),
+ * MG_ERR_OOM (allocated on first use) or MG_ERR_CUDA.
  */
 int mg_set_body_velocity(mg_ctx *c, const double *const v[3]);
 
@@ -220,6 +224,10 @@ int mg_set_body_velocity(mg_ctx *c, const double *const v[3]);
  * (layout as for face coefficients); beta_out, area_out: device, written;
  * wall faces 0.  Errors: MG_ERR_ARG for a bad grid or null/unaligned arrays.
  */
+int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, const double *hz,
+                         const double *const beta[3], const double *const frac[3], double *const beta_out[3],
+                         double *const area_out[3], void *stream);
+
 /*
  * One step of the second-order Runge-Kutta time integration (Numerical Time
  * Integration section) around the projection:
@@ -242,9 +250,6 @@ int mg_set_body_velocity(mg_ctx *c, const double *const v[3]);
 int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water, double g,
                 double dt, double *const u[3], double *phi_out, double *p_out, double tol, mg_stats *stats);
 
-int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, const double *hz,
-                         const double *const beta[3], const double *const frac[3], double *const beta_out[3],
-                         double *const area_out[3], void *stream);
 
 /*
  * Solve A p = b to ||b - A p|| / ||b|| <= tol (multigrid of the Poisson-solver
