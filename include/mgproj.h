@@ -131,6 +131,8 @@ void mg_default_opts(mg_opts *o);
  * phi: device, nx*ny*nz doubles.  solid_mask: device, nx*ny*nz bytes, 1 =
  * solid, or NULL (no body).  beta_out[0..2]: device, nx*ny*nz doubles each
  * (x, y, z low-face layout), written.  Stream-ordered on `stream`.
+ * Returns MG_OK, MG_ERR_ARG (bad grid, null or unaligned array, rho_air or
+ * rho_water not > 0) or MG_ERR_CUDA (the launch failed).
  */
 int mg_face_coeffs(const mg_grid *g, const double *phi, const uint8_t *solid_mask, double rho_air,
                    double rho_water, double *const beta_out[3], void *stream);
@@ -161,6 +163,8 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
  * inverse diagonals, FP32 copies and the coarsest dense inverse.  face_coeffs:
  * device, copied.  Synchronises with the context's stream once (the coarsest
  * operator, at most coarse_max_cells cells, is inverted on the host).
+ * Returns MG_OK, MG_ERR_ARG (null context or array, unaligned array) or
+ * MG_ERR_CUDA.
  */
 int mg_update(mg_ctx *c, const double *const face_coeffs[3]);
 
@@ -269,6 +273,7 @@ int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stat
  * cell-centred full weighting (mean of the 8 children), recursion, exact
  * coarsest solve, trilinear prolongation.  rhs, p: device; rhs is used as
  * given (the caller makes it compatible).
+ * Returns MG_OK, MG_ERR_ARG (null or unaligned array) or MG_ERR_CUDA.
  */
 int mg_vcycle(mg_ctx *c, const double *rhs, double *p);
 
@@ -277,6 +282,8 @@ int mg_vcycle(mg_ctx *c, const double *rhs, double *p);
  *   (D u)_c = h^-1 * sum_axis ( u_high - u_low ) over the OPEN faces of c
  * (closed faces carry the wall/body velocity, zero).  u[0..2]: device face
  * arrays; rhs: device, written.
+ * Returns MG_OK, MG_ERR_ARG (null or unaligned array, dt not > 0) or
+ * MG_ERR_CUDA.
  */
 int mg_divergence(mg_ctx *c, const double *const u[3], double dt, double *rhs);
 
@@ -284,6 +291,7 @@ int mg_divergence(mg_ctx *c, const double *const u[3], double dt, double *rhs);
  * Velocity correction of Eq. runge1: on open faces u_f = u*_f - dt beta_f
  * (p_R - p_L) / h; closed faces copy u*.  u_star, u: device face arrays (u
  * may alias u_star); p: device.
+ * Returns MG_OK, MG_ERR_ARG (null or unaligned array) or MG_ERR_CUDA.
  */
 int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double dt, double *const u[3]);
 
@@ -292,6 +300,9 @@ int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double
  * value is the initial guess), correct (mg_correct).  u_star: device, read;
  * u: device, written (may alias u_star); p: device, in/out.  The divergence
  * of u over the fluid cells is then at the solve's tolerance.
+ * Returns MG_OK, MG_ERR_NOT_CONVERGED (u and p from the last iterate),
+ * MG_ERR_NAN, MG_ERR_ARG (null or unaligned array, dt or tol not > 0) or
+ * MG_ERR_CUDA.
  */
 int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], double *p, double dt, double tol,
                mg_stats *stats);
@@ -307,6 +318,9 @@ int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], dou
  * written; grad_beta: device or NULL; q_out: device scratch of nx*ny*nz
  * doubles that receives q (also the initial guess; pass zeros), may be NULL
  * to use the context's buffer.  stats: host or NULL.
+ * Returns MG_OK, MG_ERR_NOT_CONVERGED (the gradients from the last iterate),
+ * MG_ERR_NAN, MG_ERR_ARG (null, aliased or unaligned array, dt or tol not
+ * > 0) or MG_ERR_CUDA.
  */
 int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, double dt, double tol,
                        double *const grad_u[3], double *const grad_beta[3], double *q_out, mg_stats *stats);
@@ -316,6 +330,8 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
  *   d beta_f / d rho_c = -beta_f^2 / 2,  d rho / d phi = rho_water - rho_air,
  *   grad_phi_c = -(rho_water - rho_air)/2 * sum_{open faces f of c} beta_f^2 grad_beta_f.
  * beta, grad_beta: device face arrays; grad_phi: device, written.
+ * Returns MG_OK, MG_ERR_ARG (bad grid, null or unaligned array) or
+ * MG_ERR_CUDA.
  */
 int mg_phi_grad(const mg_grid *g, const double *const beta[3], const double *const grad_beta[3], double rho_air,
                 double rho_water, double *grad_phi, void *stream);
@@ -323,7 +339,8 @@ int mg_phi_grad(const mg_grid *g, const double *const beta[3], const double *con
 /* Hierarchy introspection (tests): number of levels, dimensions of level l
  * (host int[3] = nx, ny, nz), and a copy of one of its FP64 arrays
  * (which: 0,1,2 = beta x,y,z; 3 = inverse diagonal 1/sum(beta)) into a device
- * buffer of that level's size. */
+ * buffer of that level's size. * Returns the number of levels, 0 for a null context.
+ */
 int mg_num_levels(const mg_ctx *c);
 int mg_level_dims(const mg_ctx *c, int level, int dims[3]);
 int mg_level_array(mg_ctx *c, int level, int which, double *out);
