@@ -41,9 +41,12 @@ if ROOT not in sys.path:
 METRIC = "Poisson solves/s to 1e-10 resid at 256^3; V-cycle HBM GB/s, FP64 vs mixed"
 TOL = 1e-10
 # algorithmic bytes per fine cell (each array read or written once per pass)
-B_SWEEP32 = 24.0      # one red-black sweep, FP32: p, b, bx, by, bz read + p written (1/diag formed on the fly)
+# one red-black sweep, FP32: p, b, bx, by, bz, dinv read + p written.  The finest-grid kernel forms
+# 1/diag from the faces it loads and takes the faces of uniform rows from one value per row, so
+# its DRAM traffic (the roofline's `traffic`) is below these algorithmic bytes
+B_SWEEP32 = 28.0
 B_SWEEP64 = 56.0
-B_VCYCLE32 = 145.0    # V(2,2), all levels, FP32: (4 sweeps x 24 + residual/restriction 20.5 + prolongation 8.5) x 8/7
+B_VCYCLE32 = 161.0    # V(2,2), all levels, FP32: (4 sweeps x 28 + residual/restriction 20.5 + prolongation 8.5) x 8/7
 B_VCYCLE64 = 322.0    # V(2,2), all levels, FP64
 B_RESID64 = 48.0      # FP64 residual + norm (p, b, bx, by, bz read; dinv mask)
 B_REFINE = 44.0 + 20.0  # FP64 residual + FP32 cast, then p64 += s*e32
@@ -58,7 +61,7 @@ SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p and b, unif
                 1: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
 # DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split4 colour
-# passes) from an ncu capture of this workload (profiles/k_smooth_split4_256_colour_pass.md)
+# passes) from an ncu capture of this workload
 SWEEP_TRAFFIC_256 = 119.535104e6 + 18.796544e6 + 119.535360e6 + 18.866944e6
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))

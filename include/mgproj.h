@@ -92,7 +92,10 @@ typedef struct {
     int krylov;           /* 0: stationary V-cycles (refinement steps when mixed); 1: conjugate
                              gradients preconditioned by inner_cycles V-cycles from a zero guess
                              (flexible Polak-Ribiere form; FP64 Krylov vectors, the cycles in the
-                             precision prec selects) [0] */
+                             precision prec selects).  The conjugate gradients stop at a true
+                             relative residual of 0.4 tol, not tol, so that their solution error
+                             stays below 10 tol: on the 128^3, 256^3 and 512x256x128 workloads the
+                             error of a CG iterate is 4 to 23 times its relative residual [0] */
     int coarse_graph;     /* 1: replay the coarse-grid part of each V-cycle (all levels below the
                              finest) as one CUDA graph captured on first use on a private stream;
                              0: launch its kernels one by one.  Identical results [1] */
@@ -267,12 +270,15 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
 int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stats);
 
 /*
- * One FP64 V(nu1,nu2)-cycle on the finest grid, p updated in place, with no
- * mean removal and no residual check: red-black Gauss-Seidel (red = (i+j+k)
- * even first on the way down, colours reversed on the way up), residual and
+ * One V(nu1,nu2)-cycle on the finest grid, p updated in place, with no mean
+ * removal and no residual check: red-black Gauss-Seidel (red = (i+j+k) even
+ * first on the way down, colours reversed on the way up), residual and
  * cell-centred full weighting (mean of the 8 children), recursion, exact
- * coarsest solve, trilinear prolongation.  rhs, p: device; rhs is used as
- * given (the caller makes it compatible).
+ * coarsest solve, trilinear prolongation.  The cycle runs in the precision of
+ * the context's solves: FP64 for MG_FP64; for MG_MIXED one FP32 cycle, on
+ * rhs and p rounded to FP32 (the same kernels and coefficients the mixed
+ * solves use), its result widened back into p.  rhs, p: device FP64; rhs is
+ * used as given (the caller makes it compatible).
  * Returns MG_OK, MG_ERR_ARG (null or unaligned array) or MG_ERR_CUDA.
  */
 int mg_vcycle(mg_ctx *c, const double *rhs, double *p);

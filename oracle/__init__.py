@@ -4,8 +4,11 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library neither imports nor
 links it, and it imports nothing from the product package.
 
-The arithmetic lives in ``mg_oracle.c`` (plain loops, FP64, no fused
-multiply-add); this module compiles it with gcc on first use and wraps it with
+The arithmetic lives in ``mg_oracle.c`` (plain loops, FP64).  The smoother,
+the residual and the prolongation accumulate their stencil products with C99
+``fma`` in the order x-, x+, y-, y+, z-, z+ (the rounding the paper leaves open,
+read the same way on both sides); every other operation is a separately rounded
+IEEE operation.  This module compiles it with gcc on first use and wraps it with
 ctypes and NumPy.  Dense NumPy/SciPy helpers here (``dense_solve``,
 ``thomas_layered``) are independent second computations used by the pins.
 

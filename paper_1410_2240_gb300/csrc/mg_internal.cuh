@@ -158,6 +158,9 @@ cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, 
                               cudaStream_t s, Split sp = {});
 cudaError_t launch_accumulate(Dims d, const double *dinv, const float *e32, double *p, const double *dscal,
                               int scale_slot, cudaStream_t s, Split sp = {});
+// dst = (float)src into the layout sp / dst = (double)src out of it (natural-order FP64 side)
+cudaError_t launch_to_f32_layout(size_t n, const double *src, float *dst, cudaStream_t s, Split sp = {});
+cudaError_t launch_from_f32_layout(size_t n, const float *src, double *dst, cudaStream_t s, Split sp = {});
 
 // multigrid-preconditioned CG (FP64 Krylov vectors)
 cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,

@@ -1128,6 +1128,19 @@ __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *
     }
 }
 
+// FP64 natural-order field <-> the finest FP32 field in the layout sp (one FP32 V-cycle on a
+// caller's FP64 rhs and iterate)
+__global__ void k_to_f32_layout(unsigned n, const double *__restrict__ src, float *__restrict__ dst, Split sp)
+{
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        dst[sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx] = (float)src[idx];
+}
+__global__ void k_from_f32_layout(unsigned n, const float *__restrict__ src, double *__restrict__ dst, Split sp)
+{
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        dst[idx] = widen(src[sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx]);
+}
+
 // ---------------------------------------------------------------------------
 // Projection (Eq. poisson1 right-hand side; Eq. runge1 correction) and adjoint
 // ---------------------------------------------------------------------------
@@ -1922,6 +1935,20 @@ cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, 
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
     note_launch();
     k_set_scale<<<1, 1, 0, s>>>(dscal, scale_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32_layout(size_t n, const double *src, float *dst, cudaStream_t s, Split sp)
+{
+    note_launch();
+    k_to_f32_layout<<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, src, dst, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_f32_layout(size_t n, const float *src, double *dst, cudaStream_t s, Split sp)
+{
+    note_launch();
+    k_from_f32_layout<<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, src, dst, sp);
     return cudaGetLastError();
 }
 

@@ -221,7 +221,8 @@ def test_fused_sweep_bit_identical_to_colour_passes(mgp, name):
 @pytest.mark.parametrize("vcycles", [1, 2])
 def test_pcg_solve_matches_oracle(mgp, name, prec, vcycles):
     """Multigrid-preconditioned CG on the GPU: residual 1e-10 by the oracle's operator, the oracle's
-    solution to 1e-9, and (FP64) the oracle's PCG iteration count within one."""
+    solution to 1e-9, and the oracle's PCG iteration count (FP64 cycles) within one at the library's
+    CG target of 0.4 tol (mixed: FP32 cycles that preconditioned worse would need more iterations)."""
     case = SMALL[name]
     beta_g, ctx = _ctx(mgp, case, prec=prec, krylov=1, inner_cycles=vcycles)
     beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
@@ -234,9 +235,9 @@ def test_pcg_solve_matches_oracle(mgp, name, prec, vcycles):
     b = O.remove_mean(rhs, lab, nc)
     assert np.linalg.norm(O.residual(beta_o, b, pg, case.h)) / np.linalg.norm(b) <= 1.0001e-10
     assert rel(pg, p_o) <= 1e-9
-    if prec == "fp64":
-        _, it_o, _ = mg.pcg(rhs, tol=1e-10, vcycles=vcycles)
-        assert abs(st.cycles - it_o) <= 1, (st.cycles, it_o)
+    assert st.rel_resid <= 0.4e-10
+    _, it_o, _ = mg.pcg(rhs, tol=0.4e-10, vcycles=vcycles)
+    assert abs(st.cycles - it_o) <= 1, (st.cycles, it_o)
 
 
 def test_pcg_projection_and_adjoint(mgp):
@@ -306,12 +307,13 @@ def test_coarse_graph_identical_to_launches(mgp, prec):
 @pytest.mark.parametrize("name", ["c1", "c2_64"])
 def test_jacobi_pcg_matches_oracle(mgp, name):
     """Diagonally preconditioned CG (the comparison solver of the Poisson-solver section): the
-    oracle's iteration count within 3 at the same tolerance, and its solution to 1e-9."""
+    oracle's iteration count within 3 at the same target (the library's CG stops at 0.4 tol), and
+    its solution to 1e-9."""
     case = SMALL[name]
     beta_g, ctx = _ctx(mgp, case, krylov=1, precond=1, max_cycles=100000)
     beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
     rhs = case_rhs(case, beta_o)
-    p_o, it_o = O.cg_solve(beta_o, rhs, case.h, tol=1e-10, max_it=100000)
+    p_o, it_o = O.cg_solve(beta_o, rhs, case.h, tol=0.4e-10, max_it=100000)
     p_ref, _, _ = O.MG(beta_o, case.h, max_coarse=4096).solve(rhs, tol=1e-12, max_cycles=300)
     p_g, st = ctx.solve(dev(rhs), tol=1e-10)
     assert it_o > 0 and abs(st.cycles - it_o) <= 3, (st.cycles, it_o)
