@@ -54,6 +54,11 @@ typedef enum {
     MG_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     MG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; p and stats hold the last iterate */
     MG_ERR_NAN = 4,            /* a residual norm was not finite */
+    MG_ERR_INCOMPATIBLE = 5,   /* the solve converged, but its rhs was incompatible with the Neumann
+                                  problem: on some connected fluid region |mean of the rhs| exceeded
+                                  1e-8 x the RMS of the rhs over all fluid cells (both before the
+                                  means were removed); each region's mean was removed and p, u and
+                                  stats are those of that compatible rhs */
     MG_ERR_OOM = 6             /* device allocation failed */
 } mg_status;
 
@@ -114,7 +119,8 @@ typedef struct {
     int cycles;              /* V-cycles (FP64), refinement steps (mixed) or CG iterations (krylov) */
     double rel_resid;        /* final ||b - A p||_2 / ||b||_2 over fluid cells, FP64 */
     double rhs_norm;         /* ||b||_2 after compatibility projection */
-    double rhs_mean_removed; /* mean of the rhs over fluid cells that was subtracted */
+    double rhs_mean_removed; /* mean of the rhs over all fluid cells (with one connected fluid region,
+                                the value subtracted; with several, each region's own mean is) */
     double resid_hist[256];  /* relative residual after each checked cycle */
     float ms_setup;          /* mg_setup wall time of this context (ms, host clock) */
     float ms_solve;          /* last solve's time (ms, CUDA events on the stream) */
@@ -154,8 +160,14 @@ int mg_face_coeffs(const mg_grid *g, const double *phi, const uint8_t *solid_mas
  * opt: host or NULL (defaults).  stream: cudaStream_t or NULL.  The context
  * owns all its device memory (about 5.3 x the fine face arrays in FP64 plus,
  * when mixed, 2.4 x in FP32) until mg_destroy.  The fluid cells with at least
- * one open face must form one connected component (isolated cells, e.g. solid
- * ones, are allowed and hold p = 0).
+ * one open face may form several connected regions (e.g. sealed pockets): each
+ * hierarchy build labels them on the GPU (union-find over runs of x-joined
+ * cells), and every solve removes the rhs mean and pins p to zero mean on each
+ * region separately, the minimum-norm solution of the singular Neumann
+ * problem; at most 65536 regions (MG_ERR_ARG beyond).  Cells with no open face
+ * hold p = 0.  Every reduction is summed in a fixed order (bitwise
+ * reproducible) for up to 64 regions; beyond that the per-region sums use
+ * atomics and may round differently from run to run.
  */
 int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3], const mg_bc *bc,
              const uint8_t *solid_mask, const mg_opts *opt, void *stream);
@@ -260,12 +272,13 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
 
 /*
  * Solve A p = b to ||b - A p|| / ||b|| <= tol (multigrid of the Poisson-solver
- * section).  rhs: device, read only; its mean over the fluid cells is removed
- * first (compatibility of the Neumann problem) and isolated cells are ignored.
- * p: device, in = initial guess, out = solution with zero mean over the fluid
- * cells (isolated cells 0).  stats: host or NULL.  Returns MG_OK,
- * MG_ERR_NOT_CONVERGED (p holds the last iterate), MG_ERR_NAN, or an error.
- * rhs and p must not alias.
+ * section).  rhs: device, read only; its mean over each connected fluid region
+ * is removed first (compatibility of the Neumann problem, Eq. neumann) and
+ * isolated cells are ignored.  p: device, in = initial guess, out = solution
+ * with zero mean over each fluid region (isolated cells 0).  stats: host or
+ * NULL.  Returns MG_OK, MG_ERR_INCOMPATIBLE (converged; a region's rhs mean was
+ * above the threshold given at mg_status), MG_ERR_NOT_CONVERGED (p holds the
+ * last iterate), MG_ERR_NAN, or an error.  rhs and p must not alias.
  */
 int mg_solve(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *stats);
 
@@ -306,9 +319,10 @@ int mg_correct(mg_ctx *c, const double *const u_star[3], const double *p, double
  * value is the initial guess), correct (mg_correct).  u_star: device, read;
  * u: device, written (may alias u_star); p: device, in/out.  The divergence
  * of u over the fluid cells is then at the solve's tolerance.
- * Returns MG_OK, MG_ERR_NOT_CONVERGED (u and p from the last iterate),
- * MG_ERR_NAN, MG_ERR_ARG (null or unaligned array, dt or tol not > 0) or
- * MG_ERR_CUDA.
+ * Returns MG_OK, MG_ERR_INCOMPATIBLE (as for mg_solve: a nonzero body-velocity
+ * divergence, for instance), MG_ERR_NOT_CONVERGED (u and p from the last
+ * iterate), MG_ERR_NAN, MG_ERR_ARG (null or unaligned array, dt or tol not > 0)
+ * or MG_ERR_CUDA.
  */
 int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], double *p, double dt, double tol,
                mg_stats *stats);
@@ -324,9 +338,9 @@ int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], dou
  * written; grad_beta: device or NULL; q_out: device scratch of nx*ny*nz
  * doubles that receives q (also the initial guess; pass zeros), may be NULL
  * to use the context's buffer.  stats: host or NULL.
- * Returns MG_OK, MG_ERR_NOT_CONVERGED (the gradients from the last iterate),
- * MG_ERR_NAN, MG_ERR_ARG (null, aliased or unaligned array, dt or tol not
- * > 0) or MG_ERR_CUDA.
+ * Returns MG_OK, MG_ERR_INCOMPATIBLE (as for mg_solve), MG_ERR_NOT_CONVERGED
+ * (the gradients from the last iterate), MG_ERR_NAN, MG_ERR_ARG (null, aliased
+ * or unaligned array, dt or tol not > 0) or MG_ERR_CUDA.
  */
 int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, double dt, double tol,
                        double *const grad_u[3], double *const grad_beta[3], double *q_out, mg_stats *stats);
@@ -383,15 +397,21 @@ void mg_profile_reset(mg_ctx *c);
  * out[2] = the mean of b over the live cells, out[3] = the number of live
  * cells, where b0 = b - mean on live cells (cells with an open face) and 0
  * elsewhere -- the same quantities mg_solve reports in mg_stats (rel_resid,
- * rhs_norm, rhs_mean_removed) for its initial iterate.  beta, rhs, p: device,
- * read only; out: device, 4 doubles, written.  Stream-ordered on `stream`.
+ * rhs_norm, rhs_mean_removed) for its initial iterate when the fluid forms one
+ * connected region (this check removes one mean over all live cells).  beta:
+ * the operator's face coefficients (with fractional face areas, area x 1/rho,
+ * the product mg_set_face_areas forms; on a stretched grid, area x beta / d).
+ * beta, rhs, p: device, read only; out: device, 4 doubles, written.
+ * Stream-ordered on `stream`.
  *
  * Its only scratch memory is a static __device__ array of the library
  * (4 * MG_NOALLOC_MAX_PLANES + 2 doubles, 128 KB on every GPU that loads the
  * library, held until the process exits); grids with nz > MG_NOALLOC_MAX_PLANES
  * are rejected with MG_ERR_ARG.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  All calls share the array:
+ * make that first call before any stream capture.  The address is cached per
+ * device for the life of the process: after cudaDeviceReset on a device, do not
+ * call this function on that device again.  All calls share the array:
  * calls that overlap on the GPU (e.g. on two streams) race and must be
  * serialised by the caller.  Nothing is allocated or freed.
  */

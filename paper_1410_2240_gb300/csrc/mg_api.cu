@@ -93,6 +93,16 @@ struct mg_ctx {
     float4 *arow0 = nullptr;
     unsigned *rowcnt = nullptr;
     bool banded = false;
+    // connected regions of the live fine cells: their number; for more than one, each live cell's
+    // region number (cc_label, the union-find labels otherwise), the cells per region (device
+    // cc_cnt, host hcnt) and the per-region sums of the current solve (cc_sum, host hsum)
+    int ncomp = 1;
+    int *cc_label = nullptr, *cc_roots = nullptr;
+    unsigned *cc_ctr = nullptr;
+    double *cc_sum = nullptr, *cc_cnt = nullptr, *cc_part = nullptr;
+    std::vector<double> hcnt, hsum;
+    bool incompat = false;      // the current solve's rhs failed the compatibility test
+    double incompat_mean = 0.0, incompat_rms = 0.0;
     double *b0 = nullptr;       // compatible fine rhs of the current solve
     double *rhs_tmp = nullptr;  // projection / adjoint right-hand side
     double *qbuf = nullptr;     // adjoint solution when the caller passes none
@@ -151,6 +161,9 @@ bool aligned16(std::initializer_list<const void *> ptrs)
         if (reinterpret_cast<uintptr_t>(q) % 16 != 0) return false;
     return true;
 }
+
+// most disconnected fluid regions a context handles (per-region sums and counts: 1 MB)
+constexpr int kMaxRegions = 1 << 16;
 
 bool grid_ok(const mg_grid *g)
 {
@@ -532,6 +545,76 @@ void stats_begin(mg_stats *st)
     for (double &v : st->resid_hist) v = 0.0;
 }
 
+// The compatible right-hand side b0 of a solve (Eq. neumann with Eq. pois: one constant per
+// connected fluid region spans A's null space, so b is solvable only with zero sum on each): the
+// rhs minus its mean on each region, 0 on dead cells; dscal gets S_SUM_B (the sum over the live
+// cells) and S_NB2 (||b0||^2).  The region sums go to the host with the next read_scalars.
+int prepare_rhs(mg_ctx *c, const double *rhs)
+{
+    const Dims d = c->dims[0];
+    if (c->ncomp > 1) {
+        CK(mg::launch_comp_center(d.n(), rhs, c->cc_label, c->ncomp, c->cc_sum, c->cc_cnt, c->b0, c->partials,
+                                  c->dscal, mg::S_NB2, mg::S_SUM_B, c->s, c->cc_part));
+        c->hsum.resize(c->ncomp);
+        CK(cudaMemcpyAsync(c->hsum.data(), c->cc_sum, c->ncomp * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    } else {
+        CK(mg::launch_rhs_prepare(d, rhs, c->L64[0].dinv, c->b0, c->partials, c->dscal, c->s));
+    }
+    return MG_OK;
+}
+
+// After the first read_scalars of a solve: the rhs is incompatible when the mean it had on some
+// region exceeds kIncompatible times its RMS over the live cells (both before the removal):
+// sum b^2 = ||b0||^2 + sum over regions of (cells x mean^2).
+constexpr double kIncompatible = 1e-8;
+void check_compatible(mg_ctx *c)
+{
+    c->incompat = false;
+    const double n = c->nlive, nb2 = c->hscal[mg::S_NB2];
+    if (!(n > 0.0) || !std::isfinite(nb2)) return;
+    double worst = 0.0, sq = nb2;
+    if (c->ncomp > 1) {
+        for (int m = 0; m < c->ncomp; m++) {
+            const double mean = c->hsum[m] / c->hcnt[m];
+            sq += c->hcnt[m] * mean * mean;
+            worst = std::max(worst, std::fabs(mean));
+        }
+    } else {
+        const double mean = c->hscal[mg::S_SUM_B] / n;
+        sq += n * mean * mean;
+        worst = std::fabs(mean);
+    }
+    const double rms = std::sqrt(sq / n);
+    c->incompat = worst > kIncompatible * rms;
+    c->incompat_mean = worst;
+    c->incompat_rms = rms;
+}
+
+// a solve that converged on an incompatible rhs reports it (p is the solution for the rhs with
+// its region means removed)
+int final_status(mg_ctx *c, int status)
+{
+    if (status == MG_OK && c->incompat)
+        return fail(MG_ERR_INCOMPATIBLE,
+                    "right-hand side incompatible with the Neumann problem: mean %.3e on a fluid region against an "
+                    "RMS of %.3e; the mean of each region was removed and the solve converged",
+                    c->incompat_mean, c->incompat_rms);
+    return status;
+}
+
+// p -= its mean over each fluid region (live cells), dead cells 0; with one region the mean is
+// dscal[S_SUM_P] / nlive from the last residual pass
+int remove_p_mean(mg_ctx *c, double *p)
+{
+    const Dims d = c->dims[0];
+    if (c->ncomp > 1)
+        CK(mg::launch_comp_center(d.n(), p, c->cc_label, c->ncomp, c->cc_sum, c->cc_cnt, p, c->partials, c->dscal,
+                                  -1, -1, c->s, c->cc_part));
+    else
+        CK(mg::launch_sub_mean_p(d, c->L64[0].dinv, p, c->dscal, c->s));
+    return MG_OK;
+}
+
 int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st)
 {
     cudaStream_t s = c->s;
@@ -541,7 +624,7 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
     stats_begin(st);
     if (st) st->ms_setup = c->ms_setup;
     CK(cudaEventRecord(c->ev0, s));
-    CK(mg::launch_rhs_prepare(d, rhs, c->L64[0].dinv, c->b0, c->partials, c->dscal, s));
+    CKS(prepare_rhs(c, rhs));
     int scale_slot = mg::S_SCALE0, next_slot = mg::S_SCALE1;
     if (mixed) {
         ProfScope ps(c, MG_PROF_RESID64, true);
@@ -552,6 +635,7 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
         CK(mg::launch_resid_norm(d, ih2, c->L64[0], c->b0, p, c->partials, c->dscal, s));
     }
     CKS(read_scalars(c));
+    check_compatible(c);
     const double nb2 = c->hscal[mg::S_NB2];
     if (st) {
         st->rhs_norm = std::sqrt(nb2);
@@ -563,7 +647,7 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
         CK(cudaEventRecord(c->ev1, s));
         CK(cudaEventSynchronize(c->ev1));
         if (st) cudaEventElapsedTime(&st->ms_solve, c->ev0, c->ev1);
-        return MG_OK;
+        return final_status(c, MG_OK);
     }
     double rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
     int cyc = 0, status = MG_OK;
@@ -597,8 +681,9 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
         rel = std::sqrt(c->hscal[mg::S_RR] / nb2);
         if (st && nhist < 256) st->resid_hist[nhist++] = rel;
     }
-    // zero mean over live cells (the cycle commutes with constant shifts, so once suffices)
-    CK(mg::launch_sub_mean_p(d, c->L64[0].dinv, p, c->dscal, s));
+    // zero mean over each region's live cells (the cycle commutes with constant shifts, so once
+    // suffices)
+    CKS(remove_p_mean(c, p));
     CK(cudaEventRecord(c->ev1, s));
     CK(cudaEventSynchronize(c->ev1));
     if (st) {
@@ -606,7 +691,7 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
         st->rel_resid = rel;
         cudaEventElapsedTime(&st->ms_solve, c->ev0, c->ev1);
     }
-    return status;
+    return final_status(c, status);
 }
 
 int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
@@ -636,6 +721,11 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
                                        op ? &c->kop : nullptr, 1.0 / (c->hs[0] * c->hs[0])));
     }
     CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
+    // connected regions of the live fine cells
+    CK(mg::launch_components(c->dims[0], c->L64[0].dinv, c->L64[0].bx, c->L64[0].by, c->L64[0].bz, c->cc_label,
+                             c->cc_ctr, s));
+    unsigned cc[2] = {0, 0};
+    CK(cudaMemcpyAsync(cc, c->cc_ctr, sizeof cc, cudaMemcpyDeviceToHost, s));
     // coarsest operator to the host
     const int nc = c->ncoarse;
     std::vector<double> cb[3];
@@ -646,6 +736,23 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
     }
     CKS(read_scalars(c));
     c->nlive = c->hscal[mg::S_NLIVE];
+    if (cc[1]) return fail(MG_ERR_CUDA, "fluid-region labelling: a bounded union-find loop gave up");
+    if (cc[0] > (unsigned)kMaxRegions)
+        return fail(MG_ERR_ARG, "the fluid forms %u disconnected regions (at most %d supported)", cc[0], kMaxRegions);
+    c->ncomp = (int)std::max(cc[0], 1u);
+    std::vector<int> roots;
+    if (cc[0] > 1) {  // number the regions by their smallest cell index; cells per region
+        CK(mg::launch_component_roots(n0, c->cc_label, c->cc_roots, c->cc_ctr, (unsigned)kMaxRegions, s));
+        roots.resize(cc[0]);
+        CK(cudaMemcpyAsync(roots.data(), c->cc_roots, cc[0] * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::sort(roots.begin(), roots.end());
+        CK(cudaMemcpyAsync(c->cc_roots, roots.data(), cc[0] * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(mg::launch_component_compact(n0, c->cc_label, c->cc_roots, c->ncomp, c->cc_cnt, c->cc_part, s));
+        c->hcnt.resize(c->ncomp);
+        CK(cudaMemcpyAsync(c->hcnt.data(), c->cc_cnt, c->ncomp * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
     std::vector<double> M;
     CKS(coarse_inverse(dc.nx, dc.ny, dc.nz, c->hs.back(), cb[0], cb[1], cb[2], M));
     CK(cudaMemcpyAsync(c->M, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -698,7 +805,8 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
     stats_begin(st);
     if (st) st->ms_setup = c->ms_setup;
     CK(cudaEventRecord(c->ev0, s));
-    CK(mg::launch_rhs_prepare(d, rhs, c->L64[0].dinv, c->b0, c->partials, c->dscal, s));
+    CKS(prepare_rhs(c, rhs));
+    bool first_check = true;
     float *e_cur = mixed ? c->L32[0].p : nullptr, *e_old = mixed ? c->ke_alt : nullptr;
     int sc_cur = mg::S_SCALE0, sc_old = mg::S_SCALE1;
     double *z = c->kz, *zo = c->kzo;
@@ -727,6 +835,8 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
                                     c->dscal, sc_cur, s, c->split0));
         }
         CKS(read_scalars(c));
+        if (first_check) check_compatible(c);
+        first_check = false;
         nb2 = c->hscal[mg::S_NB2];
         if (st) {
             st->rhs_norm = std::sqrt(nb2);
@@ -795,8 +905,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
         // the loop top re-checks with the true residual (and restarts if needed)
     }
     (void)done;
-    if (!zeroed && (status == MG_OK || status == MG_ERR_NOT_CONVERGED))
-        CK(mg::launch_sub_mean_p(d, c->L64[0].dinv, p, c->dscal, s));
+    if (!zeroed && (status == MG_OK || status == MG_ERR_NOT_CONVERGED)) CKS(remove_p_mean(c, p));
     CK(cudaEventRecord(c->ev1, s));
     CK(cudaEventSynchronize(c->ev1));
     if (st) {
@@ -804,7 +913,7 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
         st->rel_resid = rel;
         cudaEventElapsedTime(&st->ms_solve, c->ev0, c->ev1);
     }
-    return status;
+    return final_status(c, status);
 }
 
 int ensure(mg_ctx *c, double **p, size_t n)
@@ -915,6 +1024,12 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (st == MG_OK) st = c->alloc(&c->partials, 2 * mg::kRedBlocks);
     if (st == MG_OK) st = c->alloc(&c->dscal, mg::S_COUNT);
     if (st == MG_OK) st = c->alloc(&c->M, (size_t)c->ncoarse * c->ncoarse);
+    if (st == MG_OK) st = c->alloc(&c->cc_label, c->dims[0].n());
+    if (st == MG_OK) st = c->alloc(&c->cc_ctr, 4);
+    if (st == MG_OK) st = c->alloc(&c->cc_roots, kMaxRegions);
+    if (st == MG_OK) st = c->alloc(&c->cc_sum, kMaxRegions);
+    if (st == MG_OK) st = c->alloc(&c->cc_cnt, kMaxRegions);
+    if (st == MG_OK) st = c->alloc(&c->cc_part, 8 * mg::kRedBlocks);
     if (st != MG_OK) return bail(st);
     if (cudaMallocHost(&c->hscal, mg::S_COUNT * sizeof(double)) != cudaSuccess ||
         cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
@@ -1118,6 +1233,7 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
     uk.bz = u[2];
     const LevelArrays<double> none{};
     const double drho = rho_water - rho_air, s_dt_h = dt / c->g.h;
+    std::string incompat;  // message of a projection that reported an incompatible rhs
     auto faces = [](const LevelArrays<double> &L) {
         return std::array<double *, 3>{L.bx, L.by, L.bz};
     };
@@ -1134,7 +1250,8 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
         const double *ut[3] = {c->rk_ut.bx, c->rk_ut.by, c->rk_ut.bz};
         double *us[3] = {c->rk_us.bx, c->rk_us.by, c->rk_us.bz};
         const int st = mg_project(c, ut, us, p_out, dt, tol, stats);
-        if (st != MG_OK) return st;
+        if (st == MG_ERR_INCOMPATIBLE) incompat = g_err;
+        else if (st != MG_OK) return st;
     }
     // phi* = phi^k - VOF(u^k, phi^k, dt)
     CK(mg::launch_vof_upwind(d, s_dt_h, c->rk_b1, uk, phi, c->rk_phis, s));
@@ -1154,9 +1271,11 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
     {
         const double *ut[3] = {c->rk_ut.bx, c->rk_ut.by, c->rk_ut.bz};
         const int st = mg_project(c, ut, u, p_out, dt, tol, stats);
-        if (st != MG_OK) return st;
+        if (st == MG_ERR_INCOMPATIBLE) incompat = g_err;
+        else if (st != MG_OK) return st;
     }
     CK(mg::launch_half(n, uk, none, uk, s));
+    if (!incompat.empty()) return fail(MG_ERR_INCOMPATIBLE, "%s", incompat.c_str());
     return MG_OK;
 }
 
@@ -1232,7 +1351,7 @@ int mg_project(mg_ctx *c, const double *const u_star[3], double *const u[3], dou
     CKS(ensure(c, &c->rhs_tmp, c->dims[0].n()));
     CKS(mg_divergence(c, u_star, dt, c->rhs_tmp));
     const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, p, tol, stats) : solve_impl(c, c->rhs_tmp, p, tol, stats);
-    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED && st != MG_ERR_INCOMPATIBLE) return st;
     const std::string keep = g_err;
     CKS(mg_correct(c, u_star, p, dt, u));
     g_err = keep;
@@ -1269,7 +1388,7 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
     CK(mg::launch_divergence(c->dims[0], 1.0 / c->g.h, L.bx, L.by, L.bz, grad_u[0], grad_u[1], grad_u[2], c->rhs_tmp,
                              c->s));
     const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, q, tol, stats) : solve_impl(c, c->rhs_tmp, q, tol, stats);
-    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED && st != MG_ERR_INCOMPATIBLE) return st;
     const std::string keep = g_err;
     double *gb[3] = {nullptr, nullptr, nullptr};
     if (grad_beta)

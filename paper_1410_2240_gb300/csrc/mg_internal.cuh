@@ -145,6 +145,31 @@ cudaError_t launch_tail_down(const TailArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tail_up(const TailArgs<T> &a, cudaStream_t s);
 
+// connected components of the live cells (joined by open faces): label[c] = the smallest cell
+// index of c's component (-1 on dead cells); ctr[0] = number of components, ctr[1] != 0 if a
+// bounded loop gave up (both reset here)
+cudaError_t launch_components(Dims d, const double *dinv, const double *bx, const double *by, const double *bz,
+                              int *label, unsigned *ctr, cudaStream_t s);
+// the component roots (label[c] == c) into roots[0..cap) in any order; *slot = their number
+cudaError_t launch_component_roots(size_t n, const int *label, int *roots, unsigned *slot, unsigned cap,
+                                   cudaStream_t s);
+// Up to kCompOrdered components are summed in a fixed order (bitwise reproducible, one pass per
+// eight components, per-block sums in part[8 * kRedBlocks]); more are summed with atomics (not
+// reproducible bit for bit from run to run).
+constexpr int kCompOrdered = 64;
+// sums[m] = sum of v (v null: 1) over the live cells of component m (comp[c] = m)
+cudaError_t launch_comp_sums(size_t n, const double *v, const int *comp, int ncomp, double *sums, double *part,
+                             cudaStream_t s);
+// label: root -> rank among sorted_roots (the component number); cnt[m] = cells of component m
+cudaError_t launch_component_compact(size_t n, int *label, const int *sorted_roots, int ncomp, double *cnt,
+                                     double *part, cudaStream_t s);
+// out = v - the mean of v over its component on live cells (comp >= 0), 0 elsewhere; sums[m] =
+// the component sums of v; dscal[slot_sq] = ||out||^2, dscal[slot_sum] = sum of v (slots < 0:
+// not written)
+cudaError_t launch_comp_center(size_t n, const double *v, const int *comp, int ncomp, double *sums,
+                               const double *cnt, double *out, double *partials, double *dscal, int slot_sq,
+                               int slot_sum, cudaStream_t s, double *part);
+
 // reductions and fine-level helpers (FP64)
 cudaError_t launch_count_live(Dims d, const double *dinv, double *partials, double *dscal, cudaStream_t s);
 cudaError_t launch_rhs_prepare(Dims d, const double *rhs, const double *dinv, double *b0, double *partials,

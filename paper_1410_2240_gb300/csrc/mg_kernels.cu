@@ -1673,6 +1673,230 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Connected components of the live cells (cells joined by open faces) and the mean removal of
+// the Neumann problem per component (Eq. neumann with Eq. pois: A is singular with one constant
+// per component in its null space, so the rhs is projected to zero mean on each component and p
+// is pinned to zero mean on each).  Union-find over x-runs:
+//   1. each live cell points to the first cell of its run of cells joined by open x-faces;
+//   2. each open y- or z-face joins the roots of its two cells (the larger root is hooked under
+//      the smaller with atomicMin; a hook that finds the root hooked meanwhile continues with the
+//      new parent), except where the face to the left already joined the same two runs;
+//   3. every cell takes its root; a root is the smallest cell index of its component.
+// Every parent has a smaller index than its child, so the pointers form no cycle and every loop
+// below ends; each is still bounded by kCcBudget steps and reports exceeding it in *err.
+// ---------------------------------------------------------------------------
+constexpr unsigned kCcBudget = 1u << 26;
+
+__device__ __forceinline__ int cc_load(const int *label, int x) { return *(const volatile int *)(label + x); }
+
+__device__ __forceinline__ int cc_find(const int *label, int x, unsigned &budget)
+{
+    int y = cc_load(label, x);
+    while (y != x && budget) {
+        budget--;
+        x = y;
+        y = cc_load(label, x);
+    }
+    return x;
+}
+
+__device__ void cc_union(int *label, int a, int b, unsigned *err)
+{
+    unsigned budget = kCcBudget;
+    a = cc_find(label, a, budget);
+    b = cc_find(label, b, budget);
+    while (a != b && budget) {
+        budget--;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(label + b, a);
+        if (old == b) return;  // b was a root: now under a
+        // b had been hooked under old meanwhile (and is now under min(old, a)): join old and a
+        b = cc_find(label, old, budget);
+        a = cc_find(label, a, budget);
+    }
+    if (a != b) atomicOr(err, 1u);
+}
+
+// step 1: one warp per x-row; label = first cell of the run (-1 on dead cells)
+__global__ void k_cc_rows(int nx, int ny, int nz, const double *__restrict__ dinv, const double *__restrict__ bx,
+                          int *__restrict__ label)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const size_t row = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= (size_t)ny * nz) return;  // uniform across the warp
+    const size_t base = row * (size_t)nx;
+    int carry = -1;
+    for (int i0 = 0; i0 < nx; i0 += 32) {
+        const int i = i0 + (int)lane;
+        const bool in = i < nx;
+        const size_t c = base + (size_t)i;
+        const bool live = in && pos_bits(dinv[c]);
+        const bool join = live && i > 0 && pos_bits(bx[c]);
+        const unsigned starts = __ballot_sync(0xffffffffu, live && !join);
+        const unsigned m = starts & (0xffffffffu >> (31u - lane));
+        const int start = m ? (int)(base + (size_t)i0 + (31 - __clz((int)m))) : carry;
+        if (in) label[c] = live ? start : -1;
+        carry = __shfl_sync(0xffffffffu, start, 31);
+    }
+}
+
+// step 2: join the runs across open y- and z-faces
+__global__ void k_cc_merge(int nx, int ny, int nz, const double *__restrict__ bx, const double *__restrict__ by,
+                           const double *__restrict__ bz, int *label, unsigned *err)
+{
+    const unsigned n = (unsigned)nx * ny * nz;
+    const unsigned sxy = (unsigned)nx * ny;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_of(idx, nx, ny, i, j, k);
+        // the run continues from the left (its own low x-face open)
+        const bool left = i > 0 && pos_bits(bx[idx]);
+        if (j > 0 && pos_bits(by[idx])) {
+            // implied when the cell to the left is in this run, its y-face is open and its
+            // neighbour is in the neighbour's run
+            const bool implied = left && pos_bits(by[idx - 1]) && pos_bits(bx[idx - nx]);
+            if (!implied) cc_union(label, (int)idx, (int)(idx - nx), err);
+        }
+        if (k > 0 && pos_bits(bz[idx])) {
+            const bool implied = left && pos_bits(bz[idx - 1]) && pos_bits(bx[idx - sxy]);
+            if (!implied) cc_union(label, (int)idx, (int)(idx - sxy), err);
+        }
+    }
+}
+
+// step 3: every live cell takes its root; count[0] += number of roots
+__global__ void k_cc_flatten(unsigned n, int *label, unsigned *count, unsigned *err)
+{
+    unsigned roots = 0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int l = label[idx];
+        if (l < 0) continue;
+        unsigned budget = kCcBudget;
+        const int r = cc_find(label, l, budget);
+        if (!budget) atomicOr(err, 1u);
+        label[idx] = r;
+        roots += (r == (int)idx);
+    }
+    roots = __reduce_add_sync(0xffffffffu, roots);
+    if ((threadIdx.x & 31u) == 0 && roots) atomicAdd(count, roots);
+}
+
+// the roots (one per component) in any order
+__global__ void k_cc_roots(unsigned n, const int *__restrict__ label, int *__restrict__ roots, unsigned *slot,
+                           unsigned cap)
+{
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        if (label[idx] == (int)idx) {
+            const unsigned q = atomicAdd(slot, 1u);
+            if (q < cap) roots[q] = (int)idx;
+        }
+}
+
+// root -> component number (its rank among the sorted roots)
+__global__ void k_cc_compact(unsigned n, int *__restrict__ label, const int *__restrict__ roots, int ncomp)
+{
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int r = label[idx];
+        if (r < 0) continue;
+        int lo = 0, hi = ncomp - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (roots[mid] < r) lo = mid + 1;
+            else hi = mid;
+        }
+        label[idx] = lo;
+    }
+}
+
+// per-component sums of v (v null: of 1, the cell counts) over the live cells: each thread sums
+// kCcChunk consecutive cells and adds to the component total once per change of component (a
+// domain's cells mostly share one)
+constexpr unsigned kCcChunk = 64;
+__global__ void k_comp_sums(unsigned n, const double *__restrict__ v, const int *__restrict__ comp,
+                            double *__restrict__ sums)
+{
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned c0 = t * kCcChunk; c0 < n; c0 += stride * kCcChunk) {
+        int cur = -1;
+        double acc = 0.0;
+        const unsigned c1 = min(n, c0 + kCcChunk);
+        for (unsigned c = c0; c < c1; c++) {
+            const int id = comp[c];
+            if (id < 0) continue;
+            if (id != cur) {
+                if (cur >= 0) atomicAdd(sums + cur, acc);
+                cur = id;
+                acc = 0.0;
+            }
+            acc += v ? v[c] : 1.0;
+        }
+        if (cur >= 0) atomicAdd(sums + cur, acc);
+    }
+}
+
+// The same sums in a fixed order (bitwise reproducible), eight components per pass: per-block
+// sums of the components g0 .. g0+7 into part[q * gridDim.x + block], then summed over the blocks
+__global__ void k_comp_sums8(unsigned n, const double *__restrict__ v, const int *__restrict__ comp, int g0,
+                             double *__restrict__ part)
+{
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int q = comp[idx] - g0;
+        if ((unsigned)q < 8u) {
+            const double x = v ? v[idx] : 1.0;
+#pragma unroll
+            for (int r = 0; r < 8; r++)
+                if (q == r) acc[r] += x;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const double t = block_sum<kRedThreads>(acc[r]);
+        if (threadIdx.x == 0) part[r * gridDim.x + blockIdx.x] = t;
+    }
+}
+__global__ void k_comp_finish8(const double *__restrict__ part, int nblocks, int g0, int ncomp,
+                               double *__restrict__ sums)
+{
+    for (int r = 0; r < 8; r++) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) a += part[r * nblocks + i];
+        a = block_sum<kRedThreads>(a);
+        if (threadIdx.x == 0 && g0 + r < ncomp) sums[g0 + r] = a;
+    }
+}
+
+// out = v - its component's mean on live cells, 0 elsewhere; partial sums of out^2 and of v
+__global__ void k_comp_center(unsigned n, const double *__restrict__ v, const int *__restrict__ comp,
+                              const double *__restrict__ sums, const double *__restrict__ cnt,
+                              double *__restrict__ out, double *__restrict__ partials)
+{
+    double a = 0.0, b = 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int id = comp[idx];
+        double o = 0.0;
+        if (id >= 0) {
+            o = v[idx] - sums[id] / cnt[id];
+            b += v[idx];
+        }
+        out[idx] = o;
+        a += o * o;
+    }
+    a = block_sum<kRedThreads>(a);
+    b = block_sum<kRedThreads>(b);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
 inline dim3 row_grid(int threads_x, int ny, int nz)
 {
     return dim3((unsigned)((threads_x + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)nz);
@@ -1875,6 +2099,77 @@ template cudaError_t launch_tail_up<float>(const TailArgs<float> &, cudaStream_t
 
 template cudaError_t launch_coarse_solve<double>(int, const double *, const double *, double *, cudaStream_t);
 template cudaError_t launch_coarse_solve<float>(int, const double *, const float *, float *, cudaStream_t);
+
+cudaError_t launch_components(Dims d, const double *dinv, const double *bx, const double *by, const double *bz,
+                              int *label, unsigned *ctr, cudaStream_t s)
+{
+    const unsigned n = (unsigned)d.n();
+    cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const size_t rows = (size_t)d.ny * d.nz;
+    note_launch();
+    k_cc_rows<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(d.nx, d.ny, d.nz, dinv, bx, label);
+    note_launch();
+    k_cc_merge<<<red_grid(n), kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, label, ctr + 1);
+    note_launch();
+    k_cc_flatten<<<red_grid(n), kRedThreads, 0, s>>>(n, label, ctr, ctr + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_component_roots(size_t n, const int *label, int *roots, unsigned *slot, unsigned cap,
+                                   cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(slot, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_cc_roots<<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, label, roots, slot, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_component_compact(size_t n, int *label, const int *sorted_roots, int ncomp, double *cnt,
+                                     double *part, cudaStream_t s)
+{
+    note_launch();
+    k_cc_compact<<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, label, sorted_roots, ncomp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_comp_sums(n, nullptr, label, ncomp, cnt, part, s);
+}
+
+cudaError_t launch_comp_sums(size_t n, const double *v, const int *comp, int ncomp, double *sums, double *part,
+                             cudaStream_t s)
+{
+    if (ncomp <= kCompOrdered) {  // fixed order, eight components per pass
+        const unsigned g = red_grid(n);
+        for (int g0 = 0; g0 < ncomp; g0 += 8) {
+            note_launch();
+            k_comp_sums8<<<g, kRedThreads, 0, s>>>((unsigned)n, v, comp, g0, part);
+            note_launch();
+            k_comp_finish8<<<1, kRedThreads, 0, s>>>(part, (int)g, g0, ncomp, sums);
+        }
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(sums, 0, (size_t)ncomp * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const unsigned threads = (unsigned)((n + kCcChunk - 1) / kCcChunk);
+    note_launch();
+    k_comp_sums<<<red_grid(threads), kRedThreads, 0, s>>>((unsigned)n, v, comp, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_comp_center(size_t n, const double *v, const int *comp, int ncomp, double *sums,
+                               const double *cnt, double *out, double *partials, double *dscal, int slot_sq,
+                               int slot_sum, cudaStream_t s, double *part)
+{
+    cudaError_t e = launch_comp_sums(n, v, comp, ncomp, sums, part, s);
+    if (e != cudaSuccess) return e;
+    const unsigned g = red_grid(n);
+    note_launch();
+    k_comp_center<<<g, kRedThreads, 0, s>>>((unsigned)n, v, comp, sums, cnt, out, partials);
+    note_launch();
+    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, slot_sq, slot_sum);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_count_live(Dims d, const double *dinv, double *partials, double *dscal, cudaStream_t s)
 {

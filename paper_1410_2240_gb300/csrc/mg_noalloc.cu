@@ -28,7 +28,10 @@ constexpr int kSlots = 4 * MG_NOALLOC_MAX_PLANES + 2;
 static __device__ __align__(256) double g_noalloc_scratch[kSlots];
 
 // Host-side cache of the array's device address, one per device (the symbol's
-// name is only a host stand-in; kernels must be given the real address).
+// name is only a host stand-in; kernels must be given the real address).  The
+// address belongs to the device's context: after cudaDeviceReset on a device the
+// cached entry is stale, and the library must not be called again on that device
+// in this process.
 double *g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
@@ -88,7 +91,8 @@ __global__ void k_plane_pass1(int nx, int ny, int nz, const double *__restrict__
     }
 }
 
-// one block: plane partials of pass 1 summed in plane order -> (mean of rhs, live count)
+// one block: plane partials of pass 1 summed by a strided loop and a block reduction (a fixed
+// order, so the result is deterministic) -> (mean of rhs, live count)
 __global__ void k_plane_totals(int nz, const double *scratch_in, double *totals)
 {
     double a = 0.0, b = 0.0;

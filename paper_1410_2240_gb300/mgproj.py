@@ -11,13 +11,14 @@ from __future__ import annotations
 
 import ctypes
 import os
+import warnings
 from typing import Optional, Sequence
 
 import torch
 
 from .build import LIB
 
-MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, MG_ERR_NAN, MG_ERR_OOM = 0, 1, 2, 3, 4, 6
+MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, MG_ERR_NAN, MG_ERR_INCOMPATIBLE, MG_ERR_OOM = 0, 1, 2, 3, 4, 5, 6
 MG_FP64, MG_MIXED = 0, 1
 
 if not os.path.exists(LIB):
@@ -112,10 +113,18 @@ class NotConverged(MGError):
     pass
 
 
+class IncompatibleRhsWarning(UserWarning):
+    """MG_ERR_INCOMPATIBLE: the solve converged after removing a rhs mean above the library's
+    threshold on some fluid region; the results are those of the compatible rhs."""
+
+
 def _check(code, allow_not_converged=False):
     if code == MG_OK:
         return code
     msg = _lib.mg_last_error().decode(errors="replace")
+    if code == MG_ERR_INCOMPATIBLE:
+        warnings.warn(f"[mgproj status {code}] {msg}", IncompatibleRhsWarning, stacklevel=3)
+        return code
     if code == MG_ERR_NOT_CONVERGED:
         if allow_not_converged:
             return code

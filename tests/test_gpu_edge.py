@@ -1,6 +1,7 @@
 """Edge cases and failure reporting of the C ABI on the GPU (no fault is provoked:
 every bad input here is rejected on the host or handled by the kernels' guards)."""
 import math
+import warnings
 
 import numpy as np
 import pytest
@@ -135,22 +136,80 @@ def test_non_default_stream(mgp):
     assert rel(host(p), po) <= 1e-9
 
 
-def test_two_chambers_velocity_matches_and_pressure_differs_by_constants(mgp):
-    """A solid wall splits the fluid.  The velocity is unique and matches the oracle; the
-    library's p is mean-zero over all fluid cells, the oracle's per chamber, so they differ by
-    one constant per chamber (a documented convention, not an error)."""
-    case = synth.small_case(16, solid="wall", seed=9)
-    ctx = mgp.Context(_beta(mgp, case), case.h)
-    u, p, st = ctx.project(faces_dev(case.u_star), tol=1e-10)
-    uo, po, beta_o, _ = O.project(case.phi, case.solid, case.u_star, case.h, lam=case.lam, tol=1e-12)
+def _pockets_case(n=32, seed=21):
+    """A box split by a solid wall into two chambers, with two sealed pockets (hollow solid cubes
+    whose inside is fluid) in one of them: four connected fluid regions."""
+    case = synth.small_case(n, solid="wall", seed=seed)
+    solid = case.solid.copy()
+    for lo, hi in ((3, 9), (20, 27)):
+        solid[lo:hi, lo:hi, lo // 2 + 1:lo // 2 + 1 + (hi - lo)] = 1
+        solid[lo + 1:hi - 1, lo + 1:hi - 1, lo // 2 + 2:lo // 2 + (hi - lo)] = 0
+    case.solid = solid
+    return case
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(krylov=1), dict(prec="mixed", krylov=1, inner_cycles=2),
+                                dict(prec="mixed")])
+def test_fluid_regions_match_oracle(mgp, kw):
+    """Several connected fluid regions (a wall and two sealed pockets): the library labels them and
+    pins p to zero mean on each, as the oracle does (the minimum-norm solution of Eq. neumann with
+    Eq. pois), so p and u match the oracle's; a velocity field gives a compatible rhs (no warning)."""
+    case = _pockets_case()
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    lab, nc = O.components(beta_o)
+    live = O.diag_inv(beta_o) > 0
+    assert len(np.unique(lab[live])) == 4
+    ctx = mgp.Context(_beta(mgp, case), case.h, coarse_max_cells=2048, **kw)
+    with warnings.catch_warnings():
+        warnings.simplefilter("error", mgp.IncompatibleRhsWarning)
+        u, p, st = ctx.project(faces_dev(case.u_star), tol=1e-10)
+    uo, po, _, _ = O.project(case.phi, case.solid, case.u_star, case.h, lam=case.lam, tol=1e-12)
+    assert rel(host(p), po) <= 1e-9
     scale = max(np.abs(x).max() for x in uo)
     for a, b in zip(faces_host(u), uo):
         assert np.abs(a - b).max() <= 1e-8 * scale
-    lab, nc = O.components(beta_o)
-    d = host(p) - po
-    for m in range(nc):
-        sel = lab == m
-        assert np.ptp(d[sel]) <= 1e-8 * np.abs(po).max()
+    pg = host(p)
+    for m in np.unique(lab[live]):
+        assert abs(pg[lab == m].mean()) <= 1e-12 * np.abs(pg).max()
+
+
+def test_incompatible_rhs_on_regions_is_solved_and_reported(mgp):
+    """A raw random rhs has a different mean on each region: each is removed, the solve converges
+    to the oracle's solution, and the status MG_ERR_INCOMPATIBLE is reported (a warning in Python)."""
+    case = _pockets_case(seed=22)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    p_o, cyc, _ = O.MG(beta_o, case.h, max_coarse=4096).solve(case.rhs, tol=1e-12, max_cycles=300)
+    assert cyc > 0
+    ctx = mgp.Context(_beta(mgp, case), case.h, coarse_max_cells=2048)
+    with pytest.warns(mgp.IncompatibleRhsWarning, match="incompatible"):
+        p, st = ctx.solve(dev(case.rhs), tol=1e-10)
+    assert st.rel_resid <= 1e-10
+    assert rel(host(p), p_o) <= 1e-9
+    assert st.rhs_mean_removed == pytest.approx(case.rhs[O.diag_inv(beta_o) > 0].mean(), rel=1e-12)
+
+
+def test_incompatible_rhs_connected_domain(mgp):
+    """One region: a rhs with a mean above 1e-8 of its RMS is reported; its solution is that of the
+    mean-free rhs, which alone passes without a warning."""
+    case = synth.case_c2(32)
+    beta = _beta(mgp, case)
+    ctx = mgp.Context(beta, case.h)
+    rhs = ctx.divergence(faces_dev(case.u_star))
+    rms = float(torch.sqrt((rhs * rhs).mean()))
+    with warnings.catch_warnings():
+        warnings.simplefilter("error", mgp.IncompatibleRhsWarning)
+        p0, st0 = ctx.solve(rhs, tol=1e-11)
+        # a shift of 1e-9 x RMS stays below the threshold
+        ctx.solve(rhs + 1e-9 * rms, tol=1e-11)
+    with pytest.warns(mgp.IncompatibleRhsWarning):
+        p1, st1 = ctx.solve(rhs + 1e-6 * rms, tol=1e-11)
+    assert st1.rhs_mean_removed == pytest.approx(st0.rhs_mean_removed + 1e-6 * rms, rel=1e-6)
+    assert rel(host(p1), host(p0)) <= 1e-10
+    # the raw C status
+    st = mgp.Stats()
+    code = mgp._lib.mg_solve(ctx._c, mgp._vp((rhs + 1e-6 * rms).data_ptr()), mgp._vp(torch.zeros_like(rhs).data_ptr()),
+                             1e-10, mgp.ctypes.byref(st))
+    assert code == mgp.MG_ERR_INCOMPATIBLE
 
 
 def test_launch_counter_advances(mgp):

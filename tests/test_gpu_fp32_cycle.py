@@ -7,15 +7,16 @@ oracle's cycle is the same map in FP64 (the multigrid of the Poisson-solver sect
 readings of the design notes: red-black Gauss-Seidel, face-coefficient restriction, 8-child mean,
 trilinear prolongation, exact coarsest solve).  The two differ by FP32 rounding alone.
 
-Bound: with the FP32 unit roundoff u = 2^-24, each smoothing update rounds ~7 times (six fused
-products and the scaling) and the cycle runs 8 sweeps per level, so the smoothed values carry ~60 u
-relative to the local magnitudes; the residual that feeds the coarse-grid correction loses up to
-another factor ~10 to cancellation on a start that is already smooth.  The tests bound
-max|p_gpu - p_oracle| by 1e-5 max|p_oracle| (~170 u) on the first cycle from p = 0 and on the
-second from the oracle's first iterate.  A smoother or transfer with one wrong coefficient, sign
-or neighbour misses this by orders of magnitude; the cycles the solver runs are the kernels tested
-here (k_smooth_split4 with uniform rows at 256^3, with banded-row records on a z-stretched grid,
-k_smooth_split where nx % 8 != 0).
+Bound: with the FP32 unit roundoff u = 2^-24 = 6.0e-8, each smoothing update rounds ~7 times
+(six fused products and the scaling) and a level runs 8 sweeps, but Gauss-Seidel damps the
+rounding it has already made, so the smoothed values carry a few u relative to the local
+magnitudes; the residual that feeds the coarse-grid correction loses a further factor to
+cancellation once the iterate is smooth.  Measured on GB300: 1.9e-7 to 6.1e-7 (3 to 10 u) over
+the cases below.  The tests bound max|p_gpu - p_oracle| by 3e-6 max|p_oracle| (50 u) on the first
+cycle from p = 0 and on the second from the oracle's first iterate.  A smoother or transfer with
+one wrong coefficient, sign or neighbour misses this by orders of magnitude; the cycles the solver
+runs are the kernels tested here (k_smooth_split4 with uniform rows at 256^3, with banded-row
+records on a z-stretched grid, k_smooth_split where nx % 8 != 0).
 """
 import numpy as np
 import pytest
@@ -28,7 +29,7 @@ from _gpu_util import case_rhs, dev, faces_dev, faces_host, host
 
 pytestmark = pytest.mark.gpu
 
-BOUND = 1e-5
+BOUND = 3e-6
 
 
 @pytest.fixture(scope="module")
