@@ -59,6 +59,7 @@ def iteration_bytes(inner, vcycle_bytes, krylov, resid_bytes):
     return inner * vcycle_bytes + (B_CG_ITER if krylov else resid_bytes)
 SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
                 1: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
+                4: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
 # DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split4 colour
 # passes) from an ncu capture of this workload
@@ -99,9 +100,12 @@ def parse_args():
     ap.add_argument("--inner", type=int, default=2,
                     help="V-cycles per preconditioner application (krylov 1) or per refinement step (krylov 0)")
     ap.add_argument("--inner64", type=int, default=1, help="the same for the plain FP64 comparison solve")
-    ap.add_argument("--smoother", type=int, default=0, help="0 auto, 1 per colour, 2 fused, 3 fused + TMA")
+    ap.add_argument("--smoother", type=int, default=0,
+                    help="0 auto, 1 per colour, 2 fused, 3 fused + TMA, 4 per colour on the finest, fused below")
     ap.add_argument("--coarse-tail", type=int, default=1,
                     help="smallest levels: 0 a launch per pass, 1 one CTA (coarse_tail option)")
+    ap.add_argument("--pass-order", type=int, default=1,
+                    help="finest colour passes: 1 alternate descending/ascending plane order (L2 reuse), 0 ascending")
     ap.add_argument("--krylov", type=int, default=1,
                     help="1: conjugate gradients preconditioned by the V-cycle (default); 0: stationary V-cycles")
     return ap.parse_args()
@@ -478,7 +482,7 @@ def run_ours(args):
 
     # ---- mixed (headline) ----
     opts = {"inner_cycles": args.inner, "smoother": args.smoother, "krylov": args.krylov,
-            "coarse_tail": args.coarse_tail}
+            "coarse_tail": args.coarse_tail, "pass_order": args.pass_order}
     step = Step(case, "mixed", profile=0, **opts)
     dev_uuid = None
     try:
@@ -526,7 +530,7 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64:
         s64 = Step(case, "fp64", profile=1, smoother=args.smoother, krylov=args.krylov, inner_cycles=args.inner64,
-                   coarse_tail=args.coarse_tail)
+                   coarse_tail=args.coarse_tail, pass_order=args.pass_order)
         K64 = max(2, K // 2)
         ms64, _ = time_steps(s64, K64, 3, world)
         sps64, ms64 = replica_throughput(ms64, 2 * K64, world)
@@ -557,7 +561,7 @@ def run_ours(args):
         "cycles_fwd_bwd": list(cyc_mixed),
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-                     "traffic": (SWEEP_TRAFFIC_256 if (args.workload == "c3" and args.n == 256 and args.smoother in (0, 1))
+                     "traffic": (SWEEP_TRAFFIC_256 if (args.workload == "c3" and args.n == 256 and args.smoother in (0, 1, 4))
                                  else None),
                      "traffic_unit": "bytes per sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum)", "kernel": SWEEP_KERNEL[args.smoother] + " (finest grid, FP32, one red-black sweep)",
                      "algorithmic_bytes_per_sweep": B_SWEEP32 * n, "sweep_ms": sweep_ms,

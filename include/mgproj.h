@@ -93,7 +93,9 @@ typedef struct {
                              colour; 2 one fused pass per sweep with register-staged planes on
                              levels of >= 32 x 8 x 8 cells (both precisions); 3 one fused pass per
                              sweep with TMA-staged planes on FP32 levels of >= 32 x 8 x 8 cells
-                             with nx % 4 == 0, one pass per colour elsewhere [0] */
+                             with nx % 4 == 0, one pass per colour elsewhere; 4 (mixed) one pass
+                             per colour on the finest level, register-staged fused sweeps on the
+                             coarser FP32 levels of >= 32 x 8 x 8 cells [0] */
     int krylov;           /* 0: stationary V-cycles (refinement steps when mixed); 1: conjugate
                              gradients preconditioned by inner_cycles V-cycles from a zero guess
                              (flexible Polak-Ribiere form; FP64 Krylov vectors, the cycles in the
@@ -112,6 +114,12 @@ typedef struct {
                              multigrid V-cycles; 1 Jacobi (the inverse diagonal, z = D^-1 r; MG_FP64
                              only), the diagonally preconditioned CG the Poisson-solver section
                              compares multigrid with [0] */
+    int pass_order;       /* plane order of the finest level's FP32 colour passes (colour-split
+                             layout): 1 alternate descending and ascending passes, so that each
+                             starts on the planes the previous kernel touched last, still in L2,
+                             and run the restriction after them descending; 0 every pass
+                             ascending.  Each colour pass updates cells that do not depend on one
+                             another, so the results are identical [1] */
 } mg_opts;
 
 /* Solve statistics (host struct, filled when non-NULL). */

@@ -96,8 +96,9 @@ struct mg_ctx {
     // connected regions of the live fine cells: their number; for more than one, each live cell's
     // region number (cc_label, the union-find labels otherwise), the cells per region (device
     // cc_cnt, host hcnt) and the per-region sums of the current solve (cc_sum, host hsum)
-    int ncomp = 1;
+    int ncomp = 1, ncomp_raw = 0;
     int *cc_label = nullptr, *cc_roots = nullptr;
+    uint8_t *open_bits = nullptr;  // open low faces of each fine cell at the last labelling
     unsigned *cc_ctr = nullptr;
     double *cc_sum = nullptr, *cc_cnt = nullptr, *cc_part = nullptr;
     std::vector<double> hcnt, hsum;
@@ -360,6 +361,7 @@ bool use_fused(const mg_ctx *c, int l)
     if (!fused_level(c->dims[l]) || l == c->nlev - 1) return false;
     if (c->o.smoother == 2) return true;
     if (c->o.smoother == 3) return sizeof(T) == 4;
+    if (c->o.smoother == 4) return sizeof(T) == 4 && l > 0;
     return false;  // auto and 1: one pass per colour (the measured fastest on GB300)
 }
 
@@ -434,6 +436,12 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const float *urow = (sizeof(T) == 4 && l == 0) ? c->urow0 : nullptr;
     const float4 *arow = (sizeof(T) == 4 && l == 0 && c->banded) ? c->arow0 : nullptr;
     T *cur = p, *alt = palt_of<T>(c, l);
+    // plane order of the finest colour passes (pass_order = 1): each group of passes alternates
+    // descending, ascending, ... so that every pass starts on the planes its predecessor (or the
+    // prolongation, ascending) touched last, which are still in L2; the restriction that follows
+    // the last (ascending) pre-smoothing pass runs descending
+    const bool alternate = c->o.pass_order == 1 && sp.half;
+    int npass = 0;
     // one red-black sweep, `first` colour first
     auto sweep = [&](int first) -> int {
         ProfScope ps(c, MG_PROF_SMOOTH, fine);
@@ -445,8 +453,10 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
             std::swap(cur, alt);
         } else if (sp.half) {
             if constexpr (std::is_same<T, float>::value) {
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow));
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow, arow));
+                const int r0 = alternate ? (npass + 1) & 1 : 0;
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow, r0));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow, arow, r0 ^ (alternate ? 1 : 0)));
+                npass += 2;
             }
         } else {
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
@@ -458,8 +468,11 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     const LevelArrays<T> &C = L[l + 1];
     {
         ProfScope ps(c, MG_PROF_RESTRICT, fine);
-        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s, sp, urow));
+        // descending after an ascending last pass (an even number of passes, the last ascending)
+        const int rrev = alternate && npass > 0 && (npass & 1) == 0 ? 1 : 0;
+        CK(mg::launch_resid_restrict<T>(d, ih2, L[l], b, cur, C.b, s, sp, urow, rrev));
     }
+    npass = 0;
     {
         ProfScope ps(c, MG_PROF_COARSE, fine);
         if (fine && c->o.coarse_graph && !c->capturing)
@@ -718,14 +731,10 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
         // the finest level's CG operator (scaled coefficients and diagonal) comes out of the same pass
         const bool op = l == 0 && c->kop.dinv;
         CK(mg::launch_diag_inv<double>(c->dims[l], c->L64[l].bx, c->L64[l].by, c->L64[l].bz, c->L64[l].dinv, s,
-                                       op ? &c->kop : nullptr, 1.0 / (c->hs[0] * c->hs[0])));
+                                       op ? &c->kop : nullptr, 1.0 / (c->hs[0] * c->hs[0]),
+                                       l == 0 ? c->open_bits : nullptr, c->dscal + mg::S_TOPO));
     }
     CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
-    // connected regions of the live fine cells
-    CK(mg::launch_components(c->dims[0], c->L64[0].dinv, c->L64[0].bx, c->L64[0].by, c->L64[0].bz, c->cc_label,
-                             c->cc_ctr, s));
-    unsigned cc[2] = {0, 0};
-    CK(cudaMemcpyAsync(cc, c->cc_ctr, sizeof cc, cudaMemcpyDeviceToHost, s));
     // coarsest operator to the host
     const int nc = c->ncoarse;
     std::vector<double> cb[3];
@@ -736,12 +745,25 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
     }
     CKS(read_scalars(c));
     c->nlive = c->hscal[mg::S_NLIVE];
+    // connected regions of the live fine cells, labelled again where the open faces changed
+    // (first build included: the stored bits start as 0xff)
+    unsigned cc[2] = {(unsigned)c->ncomp, 0};
+    if (c->hscal[mg::S_TOPO] != 0.0) {
+        CK(mg::launch_components(c->dims[0], c->L64[0].dinv, c->L64[0].bx, c->L64[0].by, c->L64[0].bz, c->cc_label,
+                                 c->cc_ctr, s));
+        CK(cudaMemcpyAsync(cc, c->cc_ctr, sizeof cc, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        cc[0] = (unsigned)(c->ncomp_raw);
+    }
     if (cc[1]) return fail(MG_ERR_CUDA, "fluid-region labelling: a bounded union-find loop gave up");
     if (cc[0] > (unsigned)kMaxRegions)
         return fail(MG_ERR_ARG, "the fluid forms %u disconnected regions (at most %d supported)", cc[0], kMaxRegions);
     c->ncomp = (int)std::max(cc[0], 1u);
+    const bool relabel = c->hscal[mg::S_TOPO] != 0.0;
+    c->ncomp_raw = (int)cc[0];
     std::vector<int> roots;
-    if (cc[0] > 1) {  // number the regions by their smallest cell index; cells per region
+    if (cc[0] > 1 && relabel) {  // number the regions by their smallest cell index; cells per region
         CK(mg::launch_component_roots(n0, c->cc_label, c->cc_roots, c->cc_ctr, (unsigned)kMaxRegions, s));
         roots.resize(cc[0]);
         CK(cudaMemcpyAsync(roots.data(), c->cc_roots, cc[0] * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -942,6 +964,7 @@ void mg_default_opts(mg_opts *o)
     o->coarse_graph = 1;
     o->coarse_tail = 1;
     o->precond = 0;
+    o->pass_order = 1;
 }
 
 const char *mg_last_error(void) { return g_err.c_str(); }
@@ -983,8 +1006,9 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
-        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1 ||
-        o.coarse_tail < 0 || o.coarse_tail > 1 || o.precond < 0 || o.precond > 1 ||
+        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 4 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1 ||
+        o.coarse_tail < 0 || o.coarse_tail > 1 || o.precond < 0 || o.precond > 1 || o.pass_order < 0 ||
+        o.pass_order > 1 ||
         (o.precond == 1 && (o.krylov != 1 || o.prec != MG_FP64)))
         return fail(MG_ERR_ARG, "mg_setup: invalid options");
 
@@ -1009,7 +1033,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     c->nlev = (int)c->dims.size();
     // the finest FP32 fields are colour-split when its sweeps are colour passes; a hierarchy of
     // two or more levels has even dims on the finest
-    if (c->o.prec == MG_MIXED && c->o.smoother <= 1 && c->nlev >= 2)
+    if (c->o.prec == MG_MIXED && (c->o.smoother <= 1 || c->o.smoother == 4) && c->nlev >= 2)
         c->split0 = mg::Split{c->dims[0].n() / 2, c->dims[0].nx, c->dims[0].ny, mg::make_fastdiv(c->dims[0].nx),
                               mg::make_fastdiv(c->dims[0].ny)};
     const Dims dc = c->dims.back();
@@ -1025,6 +1049,9 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (st == MG_OK) st = c->alloc(&c->dscal, mg::S_COUNT);
     if (st == MG_OK) st = c->alloc(&c->M, (size_t)c->ncoarse * c->ncoarse);
     if (st == MG_OK) st = c->alloc(&c->cc_label, c->dims[0].n());
+    if (st == MG_OK) st = c->alloc(&c->open_bits, c->dims[0].n());
+    if (st == MG_OK && cudaMemsetAsync(c->open_bits, 0xff, c->dims[0].n(), c->s) != cudaSuccess)
+        st = fail(MG_ERR_CUDA, "mg_setup: memset failed");
     if (st == MG_OK) st = c->alloc(&c->cc_ctr, 4);
     if (st == MG_OK) st = c->alloc(&c->cc_roots, kMaxRegions);
     if (st == MG_OK) st = c->alloc(&c->cc_sum, kMaxRegions);
@@ -1060,7 +1087,8 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     // second iterate buffers for the fused sweeps
     for (int l = 0; l + 1 < c->nlev && st == MG_OK; l++) {
         const bool f64 = c->o.smoother == 2 && fused_level(c->dims[l]);
-        const bool f32 = c->o.prec == MG_MIXED && c->o.smoother >= 2 && fused_level(c->dims[l]);
+        const bool f32 = c->o.prec == MG_MIXED && fused_level(c->dims[l]) &&
+                         ((c->o.smoother >= 2 && c->o.smoother <= 3) || (c->o.smoother == 4 && l > 0));
         if (f64) {
             c->palt64.resize(c->nlev, nullptr);
             st = c->alloc(&c->palt64[l], c->dims[l].n());

@@ -45,6 +45,7 @@ enum Scal {
     S_RZO = 9,     // PCG: <r_new, z_old> (flexible beta)
     S_SIGMA = 10,  // PCG: <d, A d>
     S_ERR = 11,    // set to nonzero by a kernel whose bounded wait expired
+    S_TOPO = 12,   // set to 1 by a hierarchy build whose open faces differ from the last build's
     S_COUNT = 16
 };
 
@@ -99,10 +100,12 @@ struct TailArgs {
 // ---- kernel launchers (mg_kernels.cu); all stream-ordered, return cudaError_t of the launch ----
 cudaError_t launch_face_coeffs(Dims d, const double *phi, const uint8_t *solid, double rho_a, double drho,
                                double *bx, double *by, double *bz, cudaStream_t s);
-// op (optional): also write the CG operator's arrays scaled by `scale` (op->dinv = the scaled sum)
+// op (optional): also write the CG operator's arrays scaled by `scale` (op->dinv = the scaled sum);
+// open (optional): per-cell open bits of the three low faces, updated, *changed = 1 where any changed
 template <typename T>
 cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s,
-                            const LevelArrays<T> *op = nullptr, T scale = T(1));
+                            const LevelArrays<T> *op = nullptr, T scale = T(1), uint8_t *open = nullptr,
+                            double *changed = nullptr);
 cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s);
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
@@ -112,9 +115,10 @@ cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *
                           int z0 = 0, int z1 = -1);
 // one colour of a red-black sweep on the colour-split layout (FP32, all dims even); urow (optional):
 // the level's uniform-row values, arow (optional, nx % 8 == 0, replaces urow in the sweep): its
-// banded-row records (launch_uniform_rows)
+// banded-row records (launch_uniform_rows); rev: blocks take the planes in descending order
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s, const float *urow = nullptr, const float4 *arow = nullptr);
+                                cudaStream_t s, const float *urow = nullptr, const float4 *arow = nullptr,
+                                int rev = 0);
 // urow[k*ny + j] = v if every face around row (j,k) but its two x-walls equals v, else 0; arow
 // (optional) = {vx, vy, vzl, vzh} if the row's x-, y-, low z- and high z-faces hold one value
 // each, else zeros; count (optional, two counters, incremented): uniform rows, banded rows that
@@ -130,10 +134,11 @@ cudaError_t launch_rb_sweep_tma(Dims d, float h2, const LevelArrays<float> &L, c
 template <typename T>
 cudaError_t launch_rb_sweep(Dims d, T h2, const LevelArrays<T> &L, const T *b, const T *p_old, T *p_new, int first,
                             cudaStream_t s);
-// b and p of the fine level in the layout sp (FP32 only may be split); bc natural
+// b and p of the fine level in the layout sp (FP32 only may be split); bc natural; rev (FP32): blocks
+// take the coarse planes in descending order
 template <typename T>
 cudaError_t launch_resid_restrict(Dims fine, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
-                                  cudaStream_t s, Split sp = {}, const float *urow = nullptr);
+                                  cudaStream_t s, Split sp = {}, const float *urow = nullptr, int rev = 0);
 template <typename T>
 cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp = {});
 template <typename T>

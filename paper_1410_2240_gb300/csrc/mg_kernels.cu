@@ -125,6 +125,7 @@ __device__ __forceinline__ double widen(double x) { return x; }
 // clear sign bit; the coefficients, inverse diagonals and live masks it is applied to are never
 // NaN for finite input.  zero_bits(x) equals x == 0 for every x.
 __device__ __forceinline__ bool pos_bits(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool pos_bits(float x) { return __float_as_int(x) > 0; }
 __device__ __forceinline__ bool zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool zero_bits(float x) { return (__float_as_int(x) << 1) == 0; }
 
@@ -190,8 +191,11 @@ __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__
 // open.  Optionally (op != null) the CG operator's arrays scaled by `scale` = h^-2: op->dinv =
 // scale * sum, op->bx/by/bz = scale * the faces.  kRun cells per thread with the divisor memo above.
 template <typename T>
+// open (optional): per cell the open bits of its three low faces (x 1, y 2, z 4), kept from the
+// last call; where they change, *changed = 1 (the fluid regions must be labelled again)
 __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, const T *__restrict__ by,
-                           const T *__restrict__ bz, T *__restrict__ dinv, LevelArrays<T> op, T scale)
+                           const T *__restrict__ bz, T *__restrict__ dinv, LevelArrays<T> op, T scale,
+                           uint8_t *__restrict__ open, double *__restrict__ changed)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
@@ -213,6 +217,13 @@ __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, con
             op.bx[c] = bx[c] * scale;
             op.by[c] = by[c] * scale;
             op.bz[c] = bz_lo * scale;
+        }
+        if (open) {
+            const uint8_t bits = (uint8_t)((pos_bits(bx[c]) ? 1 : 0) | (pos_bits(by[c]) ? 2 : 0) | (pos_bits(bz_lo) ? 4 : 0));
+            if (open[c] != bits) {
+                open[c] = bits;
+                *changed = 1.0;
+            }
         }
         bz_lo = bz_hi;
         T q = T(0);
@@ -364,9 +375,9 @@ __global__ void k_uniform_rows(int nx, int ny, int nz, const float *__restrict__
 // b.  Same arithmetic, in the same order, as k_smooth<float>.  Used where nx % 8 != 0
 // (k_smooth_split4 otherwise).
 __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
-                               float *__restrict__ p, int colour, const float *__restrict__ urow)
+                               float *__restrict__ p, int colour, const float *__restrict__ urow, int rev)
 {
-    const int j = blockIdx.y, k = blockIdx.z;
+    const int j = rev ? ny - 1 - (int)blockIdx.y : (int)blockIdx.y, k = rev ? nz - 1 - (int)blockIdx.z : (int)blockIdx.z;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny, half = sxy * nz / 2;
@@ -493,10 +504,13 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
 template <bool BAND>
 __global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
                                 float *__restrict__ p, int colour, const float *__restrict__ urow,
-                                const float4 *__restrict__ arow)
+                                const float4 *__restrict__ arow, int rev)
 {
+    // rev: the blocks take the planes (and rows) in descending order, so that a pass that follows
+    // an ascending one starts on the data that pass touched last (still in L2)
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    const int by = rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    const int j = by * blockDim.y + threadIdx.y, k = rev ? nz - 1 - (int)blockIdx.z : (int)blockIdx.z;
     if (g >= nx / 8 || j >= ny) return;
     float4 rv;
     if (BAND) {
@@ -587,10 +601,13 @@ template <> struct Pair<double> { using type = double2; };
 template <bool SPLIT>
 __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelArrays<float> L,
                                        const float *__restrict__ b, const float *__restrict__ p,
-                                       float *__restrict__ bc, size_t half, const float *__restrict__ urow)
+                                       float *__restrict__ bc, size_t half, const float *__restrict__ urow,
+                                       int rev)
 {
     const int NX = nx / 2, NY = ny / 2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = rev ? NY - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    const int K = rev ? nz / 2 - 1 - (int)blockIdx.z : (int)blockIdx.z;
     if (I >= NX) return;
     const size_t sxy = (size_t)nx * ny;
     const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
@@ -1931,17 +1948,18 @@ cudaError_t launch_jacobi(size_t n, double scale, const double *dinv, const doub
 
 template <typename T>
 cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *dinv, cudaStream_t s,
-                            const LevelArrays<T> *op, T scale)
+                            const LevelArrays<T> *op, T scale, uint8_t *open, double *changed)
 {
     note_launch();
     k_diag_inv<T><<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv,
-                                                                      op ? *op : LevelArrays<T>{}, scale);
+                                                                      op ? *op : LevelArrays<T>{}, scale, open,
+                                                                      changed);
     return cudaGetLastError();
 }
 template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *,
-                                             cudaStream_t, const LevelArrays<double> *, double);
+                                             cudaStream_t, const LevelArrays<double> *, double, uint8_t *, double *);
 template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, cudaStream_t,
-                                            const LevelArrays<float> *, float);
+                                            const LevelArrays<float> *, float, uint8_t *, double *);
 
 cudaError_t launch_restrict_coeffs(Dims f, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s)
@@ -1976,19 +1994,19 @@ template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> 
                                           cudaStream_t, int, int);
 
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s, const float *urow, const float4 *arow)
+                                cudaStream_t s, const float *urow, const float4 *arow, int rev)
 {
     note_launch();
     if (d.nx % 8 == 0) {  // four cells per thread, blocks of 32 threads x 4 rows
         const int G = d.nx / 8;
         const dim3 grid((G + 31) / 32, (d.ny + 3) / 4, d.nz), block(32, 4);
         if (arow)
-            k_smooth_split4<true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow);
+            k_smooth_split4<true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow, rev);
         else
-            k_smooth_split4<false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, nullptr);
+            k_smooth_split4<false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, nullptr, rev);
     } else {
         k_smooth_split<<<row_grid(d.nx / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour,
-                                                                              urow);
+                                                                              urow, rev);
     }
     return cudaGetLastError();
 }
@@ -2005,15 +2023,16 @@ cudaError_t launch_uniform_rows(Dims d, const float *bx, const float *by, const 
 
 template <typename T>
 cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
-                                  cudaStream_t s, Split sp, const float *urow)
+                                  cudaStream_t s, Split sp, const float *urow, int rev)
 {
     note_launch();
     const dim3 g = row_grid(f.nx / 2, f.ny / 2, f.nz / 2);
     if constexpr (std::is_same<T, float>::value) {
         if (sp.half)
-            k_resid_restrict_pairs<true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half, urow);
+            k_resid_restrict_pairs<true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half, urow,
+                                                                    rev);
         else
-            k_resid_restrict_pairs<false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0, urow);
+            k_resid_restrict_pairs<false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0, urow, rev);
     } else {
         if (urow) return cudaErrorInvalidValue;  // uniform rows describe FP32 coefficients
         if (sp.half) return cudaErrorInvalidValue;  // FP64 fields are never split
@@ -2022,9 +2041,9 @@ cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const 
     return cudaGetLastError();
 }
 template cudaError_t launch_resid_restrict<double>(Dims, double, const LevelArrays<double> &, const double *,
-                                                   const double *, double *, cudaStream_t, Split, const float *);
+                                                   const double *, double *, cudaStream_t, Split, const float *, int);
 template cudaError_t launch_resid_restrict<float>(Dims, float, const LevelArrays<float> &, const float *,
-                                                  const float *, float *, cudaStream_t, Split, const float *);
+                                                  const float *, float *, cudaStream_t, Split, const float *, int);
 
 template <typename T>
 cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp)

@@ -44,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("coarse_max_cells", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("profile", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("krylov", ctypes.c_int), ("coarse_graph", ctypes.c_int), ("coarse_tail", ctypes.c_int),
-                ("precond", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("pass_order", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -207,9 +207,12 @@ def test_incompatible_rhs_connected_domain(mgp):
     assert rel(host(p1), host(p0)) <= 1e-10
     # the raw C status
     st = mgp.Stats()
-    code = mgp._lib.mg_solve(ctx._c, mgp._vp((rhs + 1e-6 * rms).data_ptr()), mgp._vp(torch.zeros_like(rhs).data_ptr()),
-                             1e-10, mgp.ctypes.byref(st))
+    shifted = rhs + 1e-6 * rms
+    p2 = torch.zeros_like(rhs)
+    code = mgp._lib.mg_solve(ctx._c, mgp._vp(shifted.data_ptr()), mgp._vp(p2.data_ptr()), 1e-10, mgp.ctypes.byref(st))
+    torch.cuda.synchronize()
     assert code == mgp.MG_ERR_INCOMPATIBLE
+    assert "incompatible" in mgp._lib.mg_last_error().decode()
 
 
 def test_launch_counter_advances(mgp):

@@ -216,6 +216,24 @@ def test_fused_sweep_bit_identical_to_colour_passes(mgp, name):
         assert st.cycles == s1.cycles and torch.equal(q, q1), sm
 
 
+@pytest.mark.parametrize("name", ["c2_64", "ragged_160x32x32", "ragged_48x24x40", "c3_256"])
+def test_pass_order_identical(mgp, name):
+    """The finest colour passes in alternating plane order (descending, ascending, ...) and the
+    restriction descending give bit-identical mixed solves (stationary and CG) to ascending order:
+    the cells a colour pass updates do not depend on one another."""
+    case = FUSED_CASES[name]()
+    beta = mgp.face_coeffs(dev(case.phi), case.h, None if case.solid is None else dev(case.solid, dtype=torch.uint8),
+                           rho_air=case.lam)
+    rhs = mgp.Context(beta, case.h).divergence(faces_dev(case.u_star))
+    for kw in ({"krylov": 0}, {"krylov": 1, "inner_cycles": 2}):
+        res = []
+        for order in (0, 1):
+            ctx = mgp.Context(beta, case.h, prec="mixed", pass_order=order, coarse_max_cells=2048, **kw)
+            q, st = ctx.solve(rhs, tol=1e-10)
+            res.append((q, st.cycles))
+        assert res[0][1] == res[1][1] and torch.equal(res[0][0], res[1][0]), kw
+
+
 @pytest.mark.parametrize("name", ["c1", "c2_64", "ell16", "odd_coarse_24", "aniso_64x32x16"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("vcycles", [1, 2])
