@@ -93,9 +93,7 @@ typedef struct {
                              colour; 2 one fused pass per sweep with register-staged planes on
                              levels of >= 32 x 8 x 8 cells (both precisions); 3 one fused pass per
                              sweep with TMA-staged planes on FP32 levels of >= 32 x 8 x 8 cells
-                             with nx % 4 == 0, one pass per colour elsewhere; 4 (mixed) one pass
-                             per colour on the finest level, register-staged fused sweeps on the
-                             coarser FP32 levels of >= 32 x 8 x 8 cells [0] */
+                             with nx % 4 == 0, one pass per colour elsewhere [0] */
     int krylov;           /* 0: stationary V-cycles (refinement steps when mixed); 1: conjugate
                              gradients preconditioned by inner_cycles V-cycles from a zero guess
                              (flexible Polak-Ribiere form; FP64 Krylov vectors, the cycles in the
@@ -256,26 +254,68 @@ int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, c
                          double *const area_out[3], void *stream);
 
 /*
+ * Terms of the momentum equations (Eq. navi) other than the pressure gradient:
+ * the body force -g on the z-faces (g = 1/Fr^2); the viscous term
+ * inv_re (1/rho_f) d/dx_j (2 mu S_ij), S_ij = (du_i/dx_j + du_j/dx_i)/2, with
+ * mu = mu_air + (mu_water - mu_air) phi (Eq. density, H(phi) = phi; the
+ * dimensionless viscosities, water 1, air the ratio eta) when inv_re = 1/Re
+ * > 0; the convective term -d/dx_j (u_j u_i) when convection != 0.  The
+ * sub-grid stress is not modelled.
+ */
+typedef struct {
+    double g;          /* 1/Fr^2 */
+    double inv_re;     /* 1/Re (0: no viscous term) */
+    double mu_air;     /* dimensionless viscosity of air (eta = mu_g/mu_l), >= 0 */
+    double mu_water;   /* dimensionless viscosity of water (1), >= 0 */
+    int convection;    /* nonzero: include the convective term */
+} mg_forces;
+
+/*
+ * R_i of Eq. navi without the pressure gradient and the sub-grid stress (the
+ * terms the Runge-Kutta stages add as dt R_i), on every face:
+ *   R_i = -d/dx_j (u_j u_i) + inv_re (1/rho_f) d/dx_j (2 mu S_ij) - delta_i3 g.
+ * The paper does not give the discrete operators; these are the second-order
+ * central conservative MAC forms: u_i u_i at cell centres from the mean of the
+ * cell's two i-faces, u_j u_i at cell edges from the means of the two j-faces
+ * and of the two i-faces that meet there; 2 mu S_ii at cell centres (mu of the
+ * cell), 2 mu S_ij at edges (mu the mean of the four cells around the edge);
+ * each divergence the difference of the two values that bracket the face,
+ * over h.  Walls are free-slip: normal velocity 0 (the stored wall face, or
+ * the unstored high wall), the tangential velocity mirrored into the ghost
+ * row, so no momentum flux and no shear cross a wall.  Faces with beta = 0
+ * (walls, faces at a solid) get R = 0 and enter the stencils of their
+ * neighbours with their stored velocity.  phi: device, nx*ny*nz; beta: device
+ * face arrays, 1/rho on open faces and 0 on closed ones (mg_face_coeffs); u:
+ * device face velocities; R: device face arrays, written (must not alias the
+ * inputs); f: host.  Returns MG_OK, MG_ERR_ARG (bad grid, null, aliased or
+ * unaligned array, forces not finite) or MG_ERR_CUDA.
+ */
+int mg_momentum_rhs(const mg_grid *g, const double *phi, const double *const beta[3], const double *const u[3],
+                    const mg_forces *f, double *const R[3], void *stream);
+
+/*
  * One step of the second-order Runge-Kutta time integration (Numerical Time
  * Integration section) around the projection:
- *   stage 1: beta from phi^k (Eq. density); u~ = u^k + dt R; P* from
- *            Eq. poisson1; u* = u~ - dt beta G P* (Eq. runge1);
+ *   stage 1: beta from phi^k (Eq. density); u~ = u^k + dt R(u^k, phi^k);
+ *            P* from Eq. poisson1; u* = u~ - dt beta G P* (Eq. runge1);
  *            phi* = phi^k - VOF(u^k, phi^k, dt)
- *   stage 2: beta from phi*; u~~ = (u* + u^k) + dt R; P from Eq. poisson2;
- *            u^{k+1} = (u~~ - dt beta G P) / 2 (Eq. runge2);
+ *   stage 2: beta from phi*; u~~ = (u* + u^k) + dt R(u*, phi*); P from
+ *            Eq. poisson2; u^{k+1} = (u~~ - dt beta G P) / 2 (Eq. runge2);
  *            phi^{k+1} = phi^k - VOF((u* + u^k)/2, phi^k, dt)
- * R is the body force of the momentum equations, -g (g = 1/Fr^2) on the open
- * z-faces; the convective, viscous and sub-grid terms are not modelled.  VOF
- * is the conservative first-order upwind flux form of Eq. vof (Q = 0)
- * through the open faces.  The two projections use the context's solver
- * options (and its face areas and body velocity, if set).  phi, solid_mask:
- * as for mg_face_coeffs; u: device face arrays, u^k on entry, u^{k+1} on
- * return; phi_out: device, phi^{k+1} (must not alias phi); p_out: device, P
- * of the second stage.  stats: of the second projection.  Errors: as for
- * mg_project.
+ * R is mg_momentum_rhs with the forces f (each stage's R from that stage's
+ * velocity, volume fraction and 1/rho: Heun's method on the projected
+ * equations, second order in time).  VOF is the conservative first-order
+ * upwind flux form of Eq. vof (Q = 0) through the open faces.  The two
+ * projections use the context's solver options (and its face areas and body
+ * velocity, if set).  phi, solid_mask: as for mg_face_coeffs; f: host; u:
+ * device face arrays, u^k on entry, u^{k+1} on return; phi_out: device,
+ * phi^{k+1} (must not alias phi); p_out: device, P of the second stage.
+ * stats: of the second projection.  Errors: as for mg_project, and MG_ERR_ARG
+ * for null or non-finite forces.
  */
-int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water, double g,
-                double dt, double *const u[3], double *phi_out, double *p_out, double tol, mg_stats *stats);
+int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water,
+                const mg_forces *f, double dt, double *const u[3], double *phi_out, double *p_out, double tol,
+                mg_stats *stats);
 
 
 /*

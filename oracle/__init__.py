@@ -122,6 +122,7 @@ def _load(path: Optional[str] = None):
             lib.orc_divergence_area.argtypes = [i, i, i, d, d] + [_D] * 10
             lib.orc_stretched_metrics.argtypes = [i, i, i] + [_D] * 15
             lib.orc_vof_upwind.argtypes = [i, i, i, d, d] + [_D] * 8
+            lib.orc_momentum_rhs.argtypes = [i, i, i, d, _D, d, d, d, d, i] + [_D] * 9
             _lib = lib
     return _lib
 
@@ -517,27 +518,37 @@ def vof_upwind(beta, u, phi, h, dt):
     return out
 
 
-def body_force(beta, g):
-    """R of the momentum equations kept here: the hydrostatic term -g (g = 1/Fr^2) on the open
-    z-faces, 0 on every other face."""
-    return (np.zeros_like(beta[0]), np.zeros_like(beta[1]), np.where(beta[2] > 0, -g, 0.0))
+def momentum_rhs(phi, beta, u, h, g=0.0, inv_re=0.0, mu_air=1.8e-2, mu_water=1.0, convect=True):
+    """R_i of Eq. navi without the pressure and sub-grid terms (orc_momentum_rhs): the convective
+    term -d/dx_j (u_j u_i) (if convect), the viscous term inv_re * beta * d/dx_j (2 mu S_ij) with
+    mu = mu_air + (mu_water - mu_air) phi (Eq. density) and beta = 1/rho on the face, and -g on the
+    z-faces; open faces only (beta > 0), free-slip walls."""
+    lib = _load()
+    nx, ny, nz = _dims(beta[0])
+    out = [np.empty((nz, ny, nx)) for _ in range(3)]
+    lib.orc_momentum_rhs(nx, ny, nz, h, _p(_f64(phi)), mu_air, mu_water, inv_re, g, 1 if convect else 0,
+                         *[_p(_f64(b)) for b in beta], *[_p(_f64(x)) for x in u], *[_p(o) for o in out])
+    return tuple(out)
 
 
-def rk2_step(phi, solid, u, h, dt, g, lam=1e-3, tol=1e-12):
+def rk2_step(phi, solid, u, h, dt, g, lam=1e-3, tol=1e-12, inv_re=0.0, mu_air=1.8e-2, convect=False):
     """One step of the second-order Runge-Kutta scheme:
-        u~  = u^k + dt R;  P* from Eq. poisson1 with rho(phi^k);  u* = u~ - dt B G P*   (Eq. runge1)
+        u~  = u^k + dt R(u^k, phi^k);  P* from Eq. poisson1 with rho(phi^k);
+        u*  = u~ - dt B G P*                                                             (Eq. runge1)
         phi* = phi^k - VOF(u^k, phi^k, dt)
-        u~~ = u* + u^k + dt R;  P from Eq. poisson2 with rho(phi*);
+        u~~ = u* + u^k + dt R(u*, phi*);  P from Eq. poisson2 with rho(phi*);
         u^{k+1} = (u~~ - dt B* G P) / 2                                                  (Eq. runge2)
         phi^{k+1} = phi^k - VOF((u* + u^k)/2, phi^k, dt)
-    R = the body force.  Returns (u^{k+1}, phi^{k+1}, P)."""
+    R = momentum_rhs: the body force, and with inv_re > 0 the viscous term (mu_water = 1), with
+    convect the convective term, each stage's R from that stage's velocity and volume fraction.
+    Returns (u^{k+1}, phi^{k+1}, P)."""
     beta = face_coeffs(phi, solid, lam)
-    R = body_force(beta, g)
+    R = momentum_rhs(phi, beta, u, h, g, inv_re, mu_air, 1.0, convect)
     ut = tuple(a + dt * r for a, r in zip(u, R))
     us = correct(beta, solve(beta, divergence(beta, ut, h, dt), h, tol=tol), ut, h, dt)
     phis = phi - vof_upwind(beta, u, phi, h, dt)
     beta2 = face_coeffs(phis, solid, lam)
-    R2 = body_force(beta2, g)
+    R2 = momentum_rhs(phis, beta2, us, h, g, inv_re, mu_air, 1.0, convect)
     ut2 = tuple((a + b) + dt * r for a, b, r in zip(us, u, R2))
     P = solve(beta2, divergence(beta2, ut2, h, dt), h, tol=tol)
     u1 = tuple(0.5 * x for x in correct(beta2, P, ut2, h, dt))

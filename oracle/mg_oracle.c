@@ -919,3 +919,119 @@ void orc_phi_grad(int nx, int ny, int nz, double lam, const double *bx, const do
                 gphi[c] = -0.5 * (1.0 - lam) * s;
             }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Momentum right-hand side R_i of Eq. navi without the pressure gradient and */
+/* the sub-grid stress (Numerical Time Integration section: R_i holds the     */
+/* convective, viscous and body-force terms):                                  */
+/*   R_i = -d/dx_j (u_j u_i) + 1/(rho Re) d/dx_j (2 mu S_ij) - delta_i3 g      */
+/* with S_ij = (du_i/dx_j + du_j/dx_i)/2, mu = mu_air + (mu_water - mu_air)   */
+/* phi (Eq. density, H(phi) = phi) and 1/rho on a face = beta_f (the face     */
+/* coefficient 2/(rho_L + rho_R)).  The paper does not give the discrete      */
+/* operators; this is the second-order central, conservative MAC form:        */
+/*   - u_i u_i at cell centres from the mean of the cell's two i-faces;       */
+/*     u_j u_i (j != i) at the cell edges from the mean of the two j-faces    */
+/*     and the mean of the two i-faces that meet there;                       */
+/*   - 2 mu S_ii at cell centres (mu of the cell), 2 mu S_ij at the edges     */
+/*     (mu = mean of the four cells around the edge);                          */
+/*   - each divergence the difference of the two values that bracket the     */
+/*     face, over h.                                                          */
+/* Walls are free-slip: normal velocity 0 (the stored wall face, or the high  */
+/* wall, 0), tangential velocity mirrored into the ghost row, so no momentum  */
+/* flux and no shear cross a wall.  Closed faces (walls, faces at a solid)    */
+/* enter the stencils with their stored velocity and get R = 0.               */
+/* Sums in the order written, separately rounded.                             */
+/* ------------------------------------------------------------------------- */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* face velocity of axis a at face index (i,j,k) along its own axis in [0, n_a]
+   (n_a: the high wall, 0); the other two indices mirrored into the domain */
+static double fvel(const double *u, int a, int i, int j, int k, int nx, int ny, int nz)
+{
+    if ((a == 0 && i >= nx) || (a == 1 && j >= ny) || (a == 2 && k >= nz)) return 0.0;
+    i = clampi(i, 0, nx - 1);
+    j = clampi(j, 0, ny - 1);
+    k = clampi(k, 0, nz - 1);
+    return u[IX(i, j, k)];
+}
+
+static double cmu(const double *phi, double mua, double dmu, int i, int j, int k, int nx, int ny, int nz)
+{
+    i = clampi(i, 0, nx - 1);
+    j = clampi(j, 0, ny - 1);
+    k = clampi(k, 0, nz - 1);
+    return mua + dmu * phi[IX(i, j, k)];
+}
+
+void orc_momentum_rhs(int nx, int ny, int nz, double h, const double *phi, double mu_air, double mu_water,
+                      double inv_re, double g, int convect, const double *bx, const double *by, const double *bz,
+                      const double *ux, const double *uy, const double *uz, double *rx, double *ry, double *rz)
+{
+    const double ih = 1.0 / h, dmu = mu_water - mu_air;
+    const double *U[3] = {ux, uy, uz};
+    const double *B[3] = {bx, by, bz};
+    double *R[3] = {rx, ry, rz};
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                const size_t c = IX(i, j, k);
+                for (int a = 0; a < 3; a++) {
+                    if (!(B[a][c] > 0.0)) {
+                        R[a][c] = 0.0;
+                        continue;
+                    }
+                    /* unit offsets of the face's own axis a and of the two others b, d */
+                    int o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+                    const int *ea = o[a];
+                    double conv = 0.0, visc = 0.0;
+                    /* normal part: cells (face - 1) and (face) along a */
+                    {
+                        const double um = fvel(U[a], a, i - ea[0], j - ea[1], k - ea[2], nx, ny, nz);
+                        const double u0 = fvel(U[a], a, i, j, k, nx, ny, nz);
+                        const double up = fvel(U[a], a, i + ea[0], j + ea[1], k + ea[2], nx, ny, nz);
+                        const double cm = 0.5 * (um + u0), cp = 0.5 * (u0 + up);
+                        conv = (cp * cp - cm * cm) * ih;
+                        const double mum = cmu(phi, mu_air, dmu, i - ea[0], j - ea[1], k - ea[2], nx, ny, nz);
+                        const double mup = cmu(phi, mu_air, dmu, i, j, k, nx, ny, nz);
+                        const double tp = 2.0 * mup * ((up - u0) * ih);
+                        const double tm = 2.0 * mum * ((u0 - um) * ih);
+                        visc = tp - tm;
+                    }
+                    /* the two tangential directions b in the order x, y, z (skipping a) */
+                    for (int b = 0; b < 3; b++) {
+                        if (b == a) continue;
+                        const int *eb = o[b];
+                        /* edges at the low (index of the face) and high (+1 along b) side */
+                        double fl[2], tl[2];
+                        for (int side = 0; side < 2; side++) {
+                            /* edge between faces of axis a at b-index (n-1, n), n = face's b-index + side */
+                            const int si = i + side * eb[0], sj = j + side * eb[1], sk = k + side * eb[2];
+                            /* u_a on the two a-faces meeting at the edge: b-index n-1 and n */
+                            const double ua0 = fvel(U[a], a, si - eb[0], sj - eb[1], sk - eb[2], nx, ny, nz);
+                            const double ua1 = fvel(U[a], a, si, sj, sk, nx, ny, nz);
+                            /* u_b on the two b-faces meeting at the edge: a-index (face - 1) and face */
+                            const double ub0 = fvel(U[b], b, si - ea[0], sj - ea[1], sk - ea[2], nx, ny, nz);
+                            const double ub1 = fvel(U[b], b, si, sj, sk, nx, ny, nz);
+                            const double vb = 0.5 * (ub0 + ub1), va = 0.5 * (ua0 + ua1);
+                            fl[side] = vb * va;
+                            /* mu at the edge: mean of the four cells (a-index face-1, face) x (b-index n-1, n) */
+                            const double m00 = cmu(phi, mu_air, dmu, si - ea[0] - eb[0], sj - ea[1] - eb[1],
+                                                   sk - ea[2] - eb[2], nx, ny, nz);
+                            const double m10 = cmu(phi, mu_air, dmu, si - eb[0], sj - eb[1], sk - eb[2], nx, ny, nz);
+                            const double m01 = cmu(phi, mu_air, dmu, si - ea[0], sj - ea[1], sk - ea[2], nx, ny, nz);
+                            const double m11 = cmu(phi, mu_air, dmu, si, sj, sk, nx, ny, nz);
+                            const double me = 0.25 * (((m00 + m10) + m01) + m11);
+                            tl[side] = me * ((ua1 - ua0) * ih + (ub1 - ub0) * ih);
+                        }
+                        conv = conv + (fl[1] - fl[0]) * ih;
+                        visc = visc + (tl[1] - tl[0]);
+                    }
+                    double r = 0.0;
+                    if (convect) r = -conv;
+                    r = r + (inv_re * B[a][c]) * (visc * ih);
+                    if (a == 2) r = r - g;
+                    R[a][c] = r;
+                }
+            }
+}

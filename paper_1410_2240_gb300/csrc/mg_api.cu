@@ -84,7 +84,7 @@ struct mg_ctx {
     bool has_area = false, has_vb = false;
     LevelArrays<double> karea, kbeta, kvb;
     // the time step's scratch (mg_rk2_step): face coefficients of the two stages, u~, u*, phi*
-    LevelArrays<double> rk_b1, rk_b2, rk_ut, rk_us;
+    LevelArrays<double> rk_b1, rk_b2, rk_ut, rk_us, rk_r;
     double *rk_phis = nullptr;
     float *urow0 = nullptr;  // uniform-row values of the finest FP32 level (with split0)
     // banded-row records of the finest FP32 level (with split0 and nx % 8 == 0), the two row
@@ -165,6 +165,12 @@ bool aligned16(std::initializer_list<const void *> ptrs)
 
 // most disconnected fluid regions a context handles (per-region sums and counts: 1 MB)
 constexpr int kMaxRegions = 1 << 16;
+
+bool forces_ok(const mg_forces *f)
+{
+    return f && std::isfinite(f->g) && std::isfinite(f->inv_re) && f->inv_re >= 0.0 && std::isfinite(f->mu_air) &&
+           f->mu_air >= 0.0 && std::isfinite(f->mu_water) && f->mu_water >= 0.0;
+}
 
 bool grid_ok(const mg_grid *g)
 {
@@ -361,7 +367,6 @@ bool use_fused(const mg_ctx *c, int l)
     if (!fused_level(c->dims[l]) || l == c->nlev - 1) return false;
     if (c->o.smoother == 2) return true;
     if (c->o.smoother == 3) return sizeof(T) == 4;
-    if (c->o.smoother == 4) return sizeof(T) == 4 && l > 0;
     return false;  // auto and 1: one pass per colour (the measured fastest on GB300)
 }
 
@@ -1006,7 +1011,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 || o.check_every < 1 ||
         o.coarse_max_cells < 1 || o.coarse_max_cells > 2048 || (o.prec != MG_FP64 && o.prec != MG_MIXED) ||
-        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 4 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1 ||
+        o.inner_cycles < 1 || o.profile < 0 || o.smoother < 0 || o.smoother > 3 || o.krylov < 0 || o.krylov > 1 || o.coarse_graph < 0 || o.coarse_graph > 1 ||
         o.coarse_tail < 0 || o.coarse_tail > 1 || o.precond < 0 || o.precond > 1 || o.pass_order < 0 ||
         o.pass_order > 1 ||
         (o.precond == 1 && (o.krylov != 1 || o.prec != MG_FP64)))
@@ -1033,7 +1038,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     c->nlev = (int)c->dims.size();
     // the finest FP32 fields are colour-split when its sweeps are colour passes; a hierarchy of
     // two or more levels has even dims on the finest
-    if (c->o.prec == MG_MIXED && (c->o.smoother <= 1 || c->o.smoother == 4) && c->nlev >= 2)
+    if (c->o.prec == MG_MIXED && c->o.smoother <= 1 && c->nlev >= 2)
         c->split0 = mg::Split{c->dims[0].n() / 2, c->dims[0].nx, c->dims[0].ny, mg::make_fastdiv(c->dims[0].nx),
                               mg::make_fastdiv(c->dims[0].ny)};
     const Dims dc = c->dims.back();
@@ -1087,8 +1092,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     // second iterate buffers for the fused sweeps
     for (int l = 0; l + 1 < c->nlev && st == MG_OK; l++) {
         const bool f64 = c->o.smoother == 2 && fused_level(c->dims[l]);
-        const bool f32 = c->o.prec == MG_MIXED && fused_level(c->dims[l]) &&
-                         ((c->o.smoother >= 2 && c->o.smoother <= 3) || (c->o.smoother == 4 && l > 0));
+        const bool f32 = c->o.prec == MG_MIXED && c->o.smoother >= 2 && fused_level(c->dims[l]);
         if (f64) {
             c->palt64.resize(c->nlev, nullptr);
             st = c->alloc(&c->palt64[l], c->dims[l].n());
@@ -1233,14 +1237,45 @@ int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, c
     return MG_OK;
 }
 
-int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water, double g,
-                double dt, double *const u[3], double *phi_out, double *p_out, double tol, mg_stats *stats)
+int mg_momentum_rhs(const mg_grid *g, const double *phi, const double *const beta[3], const double *const u[3],
+                    const mg_forces *f, double *const R[3], void *stream)
 {
     g_err.clear();
-    if (!c || !phi || !u || !u[0] || !u[1] || !u[2] || !phi_out || !p_out)
+    if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_momentum_rhs: bad grid");
+    if (!phi || !beta || !u || !f || !R) return fail(MG_ERR_ARG, "mg_momentum_rhs: null argument");
+    for (int a = 0; a < 3; a++)
+        if (!beta[a] || !u[a] || !R[a]) return fail(MG_ERR_ARG, "mg_momentum_rhs: null face array");
+    if (!forces_ok(f)) return fail(MG_ERR_ARG, "mg_momentum_rhs: forces not finite or viscosities not >= 0");
+    if (!aligned16({phi, beta[0], beta[1], beta[2], u[0], u[1], u[2], R[0], R[1], R[2]}))
+        return fail(MG_ERR_ARG, "mg_momentum_rhs: arrays must be 16-byte aligned");
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            if ((const double *)R[a] == u[b] || (const double *)R[a] == beta[b] || (const double *)R[a] == phi)
+                return fail(MG_ERR_ARG, "mg_momentum_rhs: R must not alias its inputs");
+    LevelArrays<double> B, U, RR;
+    B.bx = const_cast<double *>(beta[0]);
+    B.by = const_cast<double *>(beta[1]);
+    B.bz = const_cast<double *>(beta[2]);
+    U.bx = const_cast<double *>(u[0]);
+    U.by = const_cast<double *>(u[1]);
+    U.bz = const_cast<double *>(u[2]);
+    RR.bx = R[0];
+    RR.by = R[1];
+    RR.bz = R[2];
+    CK(mg::launch_momentum_rhs(Dims{g->nx, g->ny, g->nz}, g->h, phi, f->mu_air, f->mu_water, f->inv_re, f->g,
+                               f->convection, B, U, RR, (cudaStream_t)stream));
+    return MG_OK;
+}
+
+int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double rho_air, double rho_water,
+                const mg_forces *forces, double dt, double *const u[3], double *phi_out, double *p_out, double tol,
+                mg_stats *stats)
+{
+    g_err.clear();
+    if (!c || !phi || !u || !u[0] || !u[1] || !u[2] || !phi_out || !p_out || !forces)
         return fail(MG_ERR_ARG, "mg_rk2_step: null argument");
-    if (!(dt > 0.0) || !(tol > 0.0) || !(rho_air > 0.0) || !(rho_water > 0.0) || !std::isfinite(g))
-        return fail(MG_ERR_ARG, "mg_rk2_step: dt, tol and the densities must be > 0, g finite");
+    if (!(dt > 0.0) || !(tol > 0.0) || !(rho_air > 0.0) || !(rho_water > 0.0) || !forces_ok(forces))
+        return fail(MG_ERR_ARG, "mg_rk2_step: dt, tol and the densities must be > 0, the forces finite");
     if (!aligned16({phi, solid_mask, u[0], u[1], u[2], phi_out, p_out}))
         return fail(MG_ERR_ARG, "mg_rk2_step: arrays must be 16-byte aligned");
     if (phi_out == phi) return fail(MG_ERR_ARG, "mg_rk2_step: phi_out must not alias phi");
@@ -1248,7 +1283,7 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
     const Dims d = c->dims[0];
     cudaStream_t s = c->s;
     if (!c->rk_phis) {
-        for (LevelArrays<double> *L : {&c->rk_b1, &c->rk_b2, &c->rk_ut, &c->rk_us}) {
+        for (LevelArrays<double> *L : {&c->rk_b1, &c->rk_b2, &c->rk_ut, &c->rk_us, &c->rk_r}) {
             CKS(c->alloc(&L->bx, n));
             CKS(c->alloc(&L->by, n));
             CKS(c->alloc(&L->bz, n));
@@ -1272,7 +1307,10 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
         const double *cb1[3] = {b1[0], b1[1], b1[2]};
         CKS(compute_hierarchy(c, cb1));
     }
-    CK(mg::launch_rk_combine(n, uk, none, c->rk_b1.bz, dt, g, c->rk_ut, s));
+    // R(u^k, phi^k) with the first stage's 1/rho
+    CK(mg::launch_momentum_rhs(d, c->g.h, phi, forces->mu_air, forces->mu_water, forces->inv_re, forces->g,
+                               forces->convection, c->rk_b1, uk, c->rk_r, s));
+    CK(mg::launch_rk_combine(n, uk, none, c->rk_r, dt, c->rk_ut, s));
     CK(cudaMemsetAsync(p_out, 0, n * sizeof(double), s));
     {
         const double *ut[3] = {c->rk_ut.bx, c->rk_ut.by, c->rk_ut.bz};
@@ -1290,7 +1328,10 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
         const double *cb2[3] = {b2[0], b2[1], b2[2]};
         CKS(compute_hierarchy(c, cb2));
     }
-    CK(mg::launch_rk_combine(n, c->rk_us, uk, c->rk_b2.bz, dt, g, c->rk_ut, s));
+    // R(u*, phi*) with the second stage's 1/rho
+    CK(mg::launch_momentum_rhs(d, c->g.h, c->rk_phis, forces->mu_air, forces->mu_water, forces->inv_re, forces->g,
+                               forces->convection, c->rk_b2, c->rk_us, c->rk_r, s));
+    CK(mg::launch_rk_combine(n, c->rk_us, uk, c->rk_r, dt, c->rk_ut, s));
     // (u* + u^k) / 2 for the second VOF, kept in u* (u^k is overwritten below)
     CK(mg::launch_half(n, c->rk_us, uk, c->rk_us, s));
     // phi^{k+1} = phi^k - VOF((u* + u^k)/2, phi^k, dt), with the first stage's face mask

@@ -229,10 +229,16 @@ cudaError_t launch_face_areas(Dims d, const double *psi, double *ax, double *ay,
 cudaError_t launch_stretched_metrics(Dims d, const double *hx, const double *hy, const double *hz,
                                     const LevelArrays<double> &beta, const LevelArrays<double> &frac,
                                     const LevelArrays<double> &bout, const LevelArrays<double> &aout, cudaStream_t s);
-// time step pieces: out = (a + b) + dt R with R = -g on open z-faces (b null: a + dt R);
+// time step pieces: out = (a + b) + dt R, R three face arrays (b null: a + dt R);
 // out = 0.5 (a + b); phi_out = phi - (dt/h) sum +-u phi_upwind over open faces
-cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b, const double *bz,
-                              double dt, double g, const LevelArrays<double> &out, cudaStream_t s);
+cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b,
+                              const LevelArrays<double> &r, double dt, const LevelArrays<double> &out, cudaStream_t s);
+// R = the momentum right-hand side of Eq. navi on the faces (convective if convect, viscous with
+// mu = mu_air + (mu_water - mu_air) phi scaled by inv_re and beta = 1/rho, -g on the z-faces),
+// 0 on closed faces (beta == 0)
+cudaError_t launch_momentum_rhs(Dims d, double h, const double *phi, double mu_air, double mu_water, double inv_re,
+                                double g, int convect, const LevelArrays<double> &beta, const LevelArrays<double> &u,
+                                const LevelArrays<double> &r, cudaStream_t s);
 cudaError_t launch_half(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b,
                         const LevelArrays<double> &out, cudaStream_t s);
 cudaError_t launch_vof_upwind(Dims d, double s_dt_h, const LevelArrays<double> &mask, const LevelArrays<double> &u,

@@ -1270,18 +1270,125 @@ __global__ void k_stretched_metrics(int nx, int ny, int nz, const double *__rest
 // open z-faces (beta_z > 0), 0 elsewhere; each operation rounded separately in the order written.
 // ---------------------------------------------------------------------------
 // out = (a + b) + dt R   (b null: a + dt R)
-__global__ void k_rk_combine(size_t n, LevelArrays<double> a, LevelArrays<double> b, const double *__restrict__ bz,
-                             double dt, double g, LevelArrays<double> out)
+__global__ void k_rk_combine(size_t n, LevelArrays<double> a, LevelArrays<double> b, LevelArrays<double> r, double dt,
+                             LevelArrays<double> out)
 {
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
-        const double rz = pos_bits(bz[c]) ? -g : 0.0;
         const double sx = b.bx ? __dadd_rn(a.bx[c], b.bx[c]) : a.bx[c];
         const double sy = b.by ? __dadd_rn(a.by[c], b.by[c]) : a.by[c];
         const double sz = b.bz ? __dadd_rn(a.bz[c], b.bz[c]) : a.bz[c];
-        out.bx[c] = __dadd_rn(sx, __dmul_rn(dt, 0.0));
-        out.by[c] = __dadd_rn(sy, __dmul_rn(dt, 0.0));
-        out.bz[c] = __dadd_rn(sz, __dmul_rn(dt, rz));
+        out.bx[c] = __dadd_rn(sx, __dmul_rn(dt, r.bx[c]));
+        out.by[c] = __dadd_rn(sy, __dmul_rn(dt, r.by[c]));
+        out.bz[c] = __dadd_rn(sz, __dmul_rn(dt, r.bz[c]));
     }
+}
+
+// ---------------------------------------------------------------------------
+// Momentum right-hand side R_i of Eq. navi without the pressure gradient and the sub-grid
+// stress: R_i = -d/dx_j (u_j u_i) + (1/rho_f)/Re d/dx_j (2 mu S_ij) - delta_i3 g, with mu from
+// Eq. density and 1/rho_f the face coefficient.  Second-order central conservative MAC form:
+// u_i u_i at the cell centres (mean of the cell's two i-faces), u_j u_i at the edges (means of
+// the two j-faces and of the two i-faces meeting there), 2 mu S_ii at the centres, 2 mu S_ij at
+// the edges (mu: mean of the four cells around the edge), each divergence the difference of the
+// two values bracketing the face over h.  Free-slip walls: normal velocity 0 (the stored wall
+// face, or the unstored high wall), tangential velocity mirrored into the ghost row; closed faces
+// get R = 0.  Separately rounded operations in a fixed order (bit-reproducible).
+// ---------------------------------------------------------------------------
+struct MomArgs {
+    int nx, ny, nz, convect;
+    double ih, mu_air, dmu, inv_re, g;
+    const double *phi;
+    LevelArrays<double> beta, u, r;
+};
+
+__device__ __forceinline__ int clamp_idx(int v, int hi) { return v < 0 ? 0 : (v > hi ? hi : v); }
+
+// velocity of axis AX on its face (i, j, k): 0 at the high wall of its own axis, the other two
+// indices mirrored into the domain
+template <int AX>
+__device__ __forceinline__ double mom_vel(const MomArgs &m, int i, int j, int k)
+{
+    if ((AX == 0 && i >= m.nx) || (AX == 1 && j >= m.ny) || (AX == 2 && k >= m.nz)) return 0.0;
+    i = clamp_idx(i, m.nx - 1);
+    j = clamp_idx(j, m.ny - 1);
+    k = clamp_idx(k, m.nz - 1);
+    const double *u = AX == 0 ? m.u.bx : (AX == 1 ? m.u.by : m.u.bz);
+    return u[((size_t)k * m.ny + j) * m.nx + i];
+}
+
+__device__ __forceinline__ double mom_mu(const MomArgs &m, int i, int j, int k)
+{
+    i = clamp_idx(i, m.nx - 1);
+    j = clamp_idx(j, m.ny - 1);
+    k = clamp_idx(k, m.nz - 1);
+    return __dadd_rn(m.mu_air, __dmul_rn(m.dmu, m.phi[((size_t)k * m.ny + j) * m.nx + i]));
+}
+
+template <int A, int B>
+__device__ __forceinline__ void mom_tangential(const MomArgs &m, int i, int j, int k, double &conv, double &visc)
+{
+    constexpr int ai = A == 0, aj = A == 1, ak = A == 2, bi = B == 0, bj = B == 1, bk = B == 2;
+    double fl[2], tl[2];
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        const int si = i + side * bi, sj = j + side * bj, sk = k + side * bk;
+        const double ua0 = mom_vel<A>(m, si - bi, sj - bj, sk - bk);
+        const double ua1 = mom_vel<A>(m, si, sj, sk);
+        const double ub0 = mom_vel<B>(m, si - ai, sj - aj, sk - ak);
+        const double ub1 = mom_vel<B>(m, si, sj, sk);
+        const double vb = __dmul_rn(0.5, __dadd_rn(ub0, ub1)), va = __dmul_rn(0.5, __dadd_rn(ua0, ua1));
+        fl[side] = __dmul_rn(vb, va);
+        const double m00 = mom_mu(m, si - ai - bi, sj - aj - bj, sk - ak - bk);
+        const double m10 = mom_mu(m, si - bi, sj - bj, sk - bk);
+        const double m01 = mom_mu(m, si - ai, sj - aj, sk - ak);
+        const double m11 = mom_mu(m, si, sj, sk);
+        const double me = __dmul_rn(0.25, __dadd_rn(__dadd_rn(__dadd_rn(m00, m10), m01), m11));
+        tl[side] = __dmul_rn(me, __dadd_rn(__dmul_rn(__dsub_rn(ua1, ua0), m.ih), __dmul_rn(__dsub_rn(ub1, ub0), m.ih)));
+    }
+    conv = __dadd_rn(conv, __dmul_rn(__dsub_rn(fl[1], fl[0]), m.ih));
+    visc = __dadd_rn(visc, __dsub_rn(tl[1], tl[0]));
+}
+
+template <int A>
+__device__ __forceinline__ double mom_face(const MomArgs &m, int i, int j, int k, double beta)
+{
+    constexpr int ai = A == 0, aj = A == 1, ak = A == 2;
+    const double um = mom_vel<A>(m, i - ai, j - aj, k - ak);
+    const double u0 = mom_vel<A>(m, i, j, k);
+    const double up = mom_vel<A>(m, i + ai, j + aj, k + ak);
+    const double cm = __dmul_rn(0.5, __dadd_rn(um, u0)), cp = __dmul_rn(0.5, __dadd_rn(u0, up));
+    double conv = __dmul_rn(__dsub_rn(__dmul_rn(cp, cp), __dmul_rn(cm, cm)), m.ih);
+    const double mum = mom_mu(m, i - ai, j - aj, k - ak);
+    const double mup = mom_mu(m, i, j, k);
+    const double tp = __dmul_rn(__dmul_rn(2.0, mup), __dmul_rn(__dsub_rn(up, u0), m.ih));
+    const double tm = __dmul_rn(__dmul_rn(2.0, mum), __dmul_rn(__dsub_rn(u0, um), m.ih));
+    double visc = __dsub_rn(tp, tm);
+    if (A == 0) {
+        mom_tangential<0, 1>(m, i, j, k, conv, visc);
+        mom_tangential<0, 2>(m, i, j, k, conv, visc);
+    } else if (A == 1) {
+        mom_tangential<1, 0>(m, i, j, k, conv, visc);
+        mom_tangential<1, 2>(m, i, j, k, conv, visc);
+    } else {
+        mom_tangential<2, 0>(m, i, j, k, conv, visc);
+        mom_tangential<2, 1>(m, i, j, k, conv, visc);
+    }
+    double r = m.convect ? -conv : 0.0;
+    r = __dadd_rn(r, __dmul_rn(__dmul_rn(m.inv_re, beta), __dmul_rn(visc, m.ih)));
+    if (A == 2) r = __dsub_rn(r, m.g);
+    return r;
+}
+
+// one thread per cell: R on its three low faces
+__global__ void k_momentum_rhs(MomArgs m)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= m.nx) return;
+    const size_t c = ((size_t)k * m.ny + j) * m.nx + i;
+    const double bx = m.beta.bx[c], by = m.beta.by[c], bz = m.beta.bz[c];
+    m.r.bx[c] = pos_bits(bx) ? mom_face<0>(m, i, j, k, bx) : 0.0;
+    m.r.by[c] = pos_bits(by) ? mom_face<1>(m, i, j, k, by) : 0.0;
+    m.r.bz[c] = pos_bits(bz) ? mom_face<2>(m, i, j, k, bz) : 0.0;
 }
 
 // out = 0.5 (a + b)   (b null: 0.5 a)
@@ -2314,11 +2421,34 @@ cudaError_t launch_stretched_metrics(Dims d, const double *hx, const double *hy,
     return cudaGetLastError();
 }
 
-cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b, const double *bz,
-                              double dt, double g, const LevelArrays<double> &out, cudaStream_t s)
+cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b,
+                              const LevelArrays<double> &r, double dt, const LevelArrays<double> &out, cudaStream_t s)
 {
     note_launch();
-    k_rk_combine<<<red_grid(n), kRedThreads, 0, s>>>(n, a, b, bz, dt, g, out);
+    k_rk_combine<<<red_grid(n), kRedThreads, 0, s>>>(n, a, b, r, dt, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_momentum_rhs(Dims d, double h, const double *phi, double mu_air, double mu_water, double inv_re,
+                                double g, int convect, const LevelArrays<double> &beta, const LevelArrays<double> &u,
+                                const LevelArrays<double> &r, cudaStream_t s)
+{
+    MomArgs m;
+    m.nx = d.nx;
+    m.ny = d.ny;
+    m.nz = d.nz;
+    m.convect = convect ? 1 : 0;
+    m.ih = 1.0 / h;
+    m.mu_air = mu_air;
+    m.dmu = mu_water - mu_air;
+    m.inv_re = inv_re;
+    m.g = g;
+    m.phi = phi;
+    m.beta = beta;
+    m.u = u;
+    m.r = r;
+    note_launch();
+    k_momentum_rhs<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(m);
     return cudaGetLastError();
 }
 

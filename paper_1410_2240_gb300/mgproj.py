@@ -47,6 +47,16 @@ class Opts(ctypes.Structure):
                 ("precond", ctypes.c_int), ("pass_order", ctypes.c_int)]
 
 
+class Forces(ctypes.Structure):
+    """mg_forces: the terms of Eq. navi besides the pressure (body force, viscous, convective)."""
+    _fields_ = [("g", ctypes.c_double), ("inv_re", ctypes.c_double), ("mu_air", ctypes.c_double),
+                ("mu_water", ctypes.c_double), ("convection", ctypes.c_int)]
+
+
+def forces(g=0.0, inv_re=0.0, mu_air=1.8e-2, mu_water=1.0, convection=False) -> Forces:
+    return Forces(g, inv_re, mu_air, mu_water, 1 if convection else 0)
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("rel_resid", ctypes.c_double), ("rhs_norm", ctypes.c_double),
                 ("rhs_mean_removed", ctypes.c_double), ("resid_hist", ctypes.c_double * 256),
@@ -79,8 +89,9 @@ _lib.mg_update.argtypes = [_vp, _PP]
 _lib.mg_face_areas.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _vp]
 _lib.mg_set_face_areas.argtypes = [_vp, _PP]
 _lib.mg_set_body_velocity.argtypes = [_vp, _PP]
-_lib.mg_rk2_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _PP,
-                              _vp, _vp, ctypes.c_double, ctypes.POINTER(Stats)]
+_lib.mg_rk2_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Forces),
+                              ctypes.c_double, _PP, _vp, _vp, ctypes.c_double, ctypes.POINTER(Stats)]
+_lib.mg_momentum_rhs.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _PP, ctypes.POINTER(Forces), _PP, _vp]
 _lib.mg_stretched_metrics.argtypes = [ctypes.POINTER(Grid), _vp, _vp, _vp, _PP, _PP, _PP, _PP, _vp]
 _lib.mg_kernel_launches.restype = ctypes.c_uint64
 _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -100,7 +111,7 @@ EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_sol
            "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
            "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset",
            "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error", "mg_face_areas", "mg_set_face_areas",
-           "mg_set_body_velocity", "mg_stretched_metrics", "mg_rk2_step"]
+           "mg_set_body_velocity", "mg_stretched_metrics", "mg_rk2_step", "mg_momentum_rhs"]
 
 
 class MGError(RuntimeError):
@@ -206,6 +217,20 @@ def stretched_metrics(hx: torch.Tensor, hy: torch.Tensor, hz: torch.Tensor, beta
     return bo, ao
 
 
+def momentum_rhs(phi: torch.Tensor, beta: Sequence[torch.Tensor], u: Sequence[torch.Tensor], h: float,
+                 f: Forces, out=None, stream=None):
+    """mg_momentum_rhs: R_i of Eq. navi without the pressure (body force, viscous, convective) on
+    the faces; beta = 1/rho on open faces (face_coeffs), 0 on closed ones."""
+    shape = phi.shape
+    nz, ny, nx = shape
+    g = Grid(nx, ny, nz, h)
+    if out is None:
+        out = tuple(torch.empty_like(phi) for _ in range(3))
+    _check(_lib.mg_momentum_rhs(ctypes.byref(g), _dev(phi, shape, name="phi"), _faces(beta, shape, "beta"),
+                                _faces(u, shape, "u"), ctypes.byref(f), _faces(out, shape, "R"), _stream(stream)))
+    return out
+
+
 def phi_grad(beta: Sequence[torch.Tensor], grad_beta: Sequence[torch.Tensor], h: float, rho_air=1e-3,
              rho_water=1.0, out=None, stream=None):
     """mg_phi_grad: chain rule from face coefficients to phi."""
@@ -256,16 +281,19 @@ class Context:
         coefficients of this context are then 1/rho and the operator uses area * 1/rho."""
         _check(_lib.mg_set_face_areas(self._c, None if areas is None else _faces(areas, self.shape, "area")))
 
-    def rk2_step(self, phi, u, dt, g, solid=None, rho_air=1e-3, rho_water=1.0, tol=1e-10, phi_out=None, p=None):
-        """mg_rk2_step: one Runge-Kutta step (u updated in place); returns (phi_new, p, stats)."""
+    def rk2_step(self, phi, u, dt, g=0.0, solid=None, rho_air=1e-3, rho_water=1.0, tol=1e-10, phi_out=None, p=None,
+                 forces: Optional[Forces] = None):
+        """mg_rk2_step: one Runge-Kutta step (u updated in place); returns (phi_new, p, stats).
+        forces: an mg_forces (viscous and convective terms); None: the body force g alone."""
         if phi_out is None:
             phi_out = torch.empty_like(phi)
         if p is None:
             p = torch.empty_like(phi)
+        f = forces if forces is not None else Forces(g, 0.0, 0.0, 1.0, 0)
         st = Stats()
         sp = _vp(0) if solid is None else _dev(solid, self.shape, torch.uint8, "solid")
-        _check(_lib.mg_rk2_step(self._c, _dev(phi, self.shape, name="phi"), sp, rho_air, rho_water, g, dt,
-                                _faces(u, self.shape, "u"), _dev(phi_out, self.shape, name="phi_out"),
+        _check(_lib.mg_rk2_step(self._c, _dev(phi, self.shape, name="phi"), sp, rho_air, rho_water, ctypes.byref(f),
+                                dt, _faces(u, self.shape, "u"), _dev(phi_out, self.shape, name="phi_out"),
                                 _dev(p, self.shape, name="p"), tol, ctypes.byref(st)))
         return phi_out, p, st
 

@@ -1,6 +1,7 @@
 """The Runge-Kutta time step on the GPU (mg_rk2_step) against the oracle's step: velocity,
-volume fraction and pressure after one step with a body and gravity, FP64 and mixed, and a
-hydrostatic column that stays at rest."""
+volume fraction and pressure after one step with a body, gravity and (optionally) the viscous and
+convective terms, FP64 and mixed; a hydrostatic column that stays at rest; the momentum
+right-hand side (mg_momentum_rhs) bit for bit against the oracle's."""
 import numpy as np
 import pytest
 import torch
@@ -21,18 +22,26 @@ def mgp():
     return mgproj
 
 
+MU_AIR = 1.8e-2
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["ell_32", "ragged_48x32x16"])
-def test_rk2_step_matches_oracle(mgp, prec, name):
+@pytest.mark.parametrize("full", [False, True])
+def test_rk2_step_matches_oracle(mgp, prec, name, full):
+    """One step; full: the viscous (1/Re = 0.01, mu ratio 0.018) and convective terms as well."""
     dims = {"ell_32": (32, 32, 32, 7), "ragged_48x32x16": (48, 32, 16, 8)}[name]
     case = synth.small_case(*dims[:3], seed=dims[3], solid="ellipsoid", interface="wave")
     dt, g = 0.2 * case.h, 1.0
-    u_o, phi_o, P_o = O.rk2_step(case.phi, case.solid, case.u_star, case.h, dt, g, lam=case.lam, tol=1e-12)
+    inv_re = 1e-2 if full else 0.0
+    u_o, phi_o, P_o = O.rk2_step(case.phi, case.solid, case.u_star, case.h, dt, g, lam=case.lam, tol=1e-12,
+                                 inv_re=inv_re, mu_air=MU_AIR, convect=full)
     beta = mgp.face_coeffs(dev(case.phi), case.h, dev(case.solid, torch.uint8), rho_air=case.lam)
     ctx = mgp.Context(beta, case.h, prec=prec, krylov=1, inner_cycles=2, coarse_max_cells=2048)
     u = list(faces_dev(case.u_star))
-    phi1, P, st = ctx.rk2_step(dev(case.phi), u, dt, g, solid=dev(case.solid, torch.uint8), rho_air=case.lam,
-                               tol=1e-11)
+    f = mgp.forces(g=g, inv_re=inv_re, mu_air=MU_AIR, convection=full)
+    phi1, P, st = ctx.rk2_step(dev(case.phi), u, dt, solid=dev(case.solid, torch.uint8), rho_air=case.lam,
+                               tol=1e-11, forces=f)
     scale = max(np.abs(x).max() for x in u_o)
     for a, b in zip(faces_host(u), u_o):
         assert np.abs(a - b).max() <= 1e-7 * scale
@@ -49,3 +58,27 @@ def test_rk2_hydrostatic_column_at_rest(mgp):
     phi1, P, st = ctx.rk2_step(dev(case.phi), u, dt, g, rho_air=case.lam, tol=1e-11)
     assert max(float(x.abs().max()) for x in u) <= 1e-8 * dt * g
     assert float((phi1 - dev(case.phi)).abs().max()) <= 1e-8
+
+
+MOM_CASES = {
+    "ell_32_random_phi": lambda: synth.small_case(32, seed=11, solid="ellipsoid", interface="random"),
+    "ragged_40x24x16_wave": lambda: synth.small_case(40, 24, 16, seed=12, solid="ellipsoid", interface="wave"),
+    "wall_16": lambda: synth.small_case(16, seed=13, solid="wall", interface="wave"),
+    "thin_1x6x5": lambda: synth.small_case(1, 6, 5, seed=14, solid="none", interface="random"),
+}
+
+
+@pytest.mark.parametrize("name", list(MOM_CASES))
+@pytest.mark.parametrize("terms", ["all", "viscous", "convective"])
+def test_momentum_rhs_bit_exact(mgp, name, terms):
+    """R of Eq. navi on the GPU equals the oracle's bit for bit: the same separately rounded
+    operations in the same order (walls, bodies, ragged and one-cell-wide grids)."""
+    case = MOM_CASES[name]()
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    inv_re = 0.0 if terms == "convective" else 0.37
+    conv = terms != "viscous"
+    R_o = O.momentum_rhs(case.phi, beta_o, case.u_star, case.h, g=1.3, inv_re=inv_re, mu_air=MU_AIR, convect=conv)
+    f = mgp.forces(g=1.3, inv_re=inv_re, mu_air=MU_AIR, convection=conv)
+    R_g = mgp.momentum_rhs(dev(case.phi), faces_dev(beta_o), faces_dev(case.u_star), case.h, f)
+    for a, b in zip(faces_host(R_g), R_o):
+        assert np.array_equal(a, b)

@@ -13,6 +13,7 @@ import pytest
 
 import oracle as O
 import test_oracle_areas as T3
+import test_oracle_momentum as T6
 import test_oracle_rk2 as T5
 import test_oracle_stretched as T4
 import test_oracle_operator as T1
@@ -84,6 +85,27 @@ MUTANTS = [
      "az[c] = (hx[i] * hz[k]) * (fz ? fz[c] : 1.0);", [T4.test_linear_pressure_face_gradients_exact]),
     ("VOF takes the downwind cell", "#define UPW(u, lo, hi) ((u) > 0.0 ? (u) * phi[lo] : (u) * phi[hi])",
      "#define UPW(u, lo, hi) ((u) > 0.0 ? (u) * phi[hi] : (u) * phi[lo])", [T5.test_vof_upwind_hand_example]),
+    ("normal viscous stress without its factor 2", "const double tp = 2.0 * mup * ((up - u0) * ih);",
+     "const double tp = mup * ((up - u0) * ih);", [lambda: T6.test_viscous_term_exact_for_quadratic_velocity(False)]),
+    ("edge viscosity from two cells", "const double me = 0.25 * (((m00 + m10) + m01) + m11);",
+     "const double me = 0.5 * (m01 + m11);", [lambda: T6.test_viscous_term_exact_for_quadratic_velocity(True)]),
+    ("normal momentum flux sign", "conv = (cp * cp - cm * cm) * ih;", "conv = (cp * cp + cm * cm) * ih;",
+     [T6.test_convective_term_exact_for_linear_velocity]),
+    ("shear takes the wrong tangential face", "const double ub0 = fvel(U[b], b, si - ea[0], sj - ea[1], sk - ea[2], nx, ny, nz);",
+     "const double ub0 = fvel(U[b], b, si - eb[0], sj - eb[1], sk - eb[2], nx, ny, nz);",
+     [T6.test_convective_term_exact_for_linear_velocity, lambda: T6.test_viscous_term_exact_for_quadratic_velocity(False)]),
+    ("viscous term without 1/rho", "r = r + (inv_re * B[a][c]) * (visc * ih);", "r = r + inv_re * (visc * ih);",
+     [lambda: T6.test_viscous_term_exact_for_quadratic_velocity(False)]),
+    ("walls hold zero ghosts instead of mirrored tangential velocity",
+     "    i = clampi(i, 0, nx - 1);\n    j = clampi(j, 0, ny - 1);\n    k = clampi(k, 0, nz - 1);\n    return u[IX(i, j, k)];",
+     "    if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return 0.0;\n    return u[IX(i, j, k)];",
+     [T6.test_free_slip_walls_shear_closed_form]),
+    ("momentum gravity points up", "if (a == 2) r = r - g;", "if (a == 2) r = r + g;",
+     [T5.test_rk2_hydrostatic_column_stays_at_rest]),
+    ("momentum flux at the high edge from the low rows",
+     "const double ua1 = fvel(U[a], a, si, sj, sk, nx, ny, nz);",
+     "const double ua1 = fvel(U[a], a, si - eb[0], sj - eb[1], sk - eb[2], nx, ny, nz);",
+     [T6.test_free_slip_walls_flux_closed_form, T6.test_convective_term_exact_for_linear_velocity]),
 ]
 
 
@@ -119,14 +141,15 @@ def test_planted_mistake_is_caught(name, orig, mut, pins, tmp_path):
 # section, the fractional-area and stretched projections): (name, function, original text, mutated
 # text, pins that must catch it)
 PY_MUTANTS = [
-    ("body force points up", "body_force", "np.where(beta[2] > 0, -g, 0.0)", "np.where(beta[2] > 0, g, 0.0)",
-     [T5.test_rk2_hydrostatic_column_stays_at_rest]),
     ("second stage drops the 1/2 of Eq. runge2", "rk2_step",
      "u1 = tuple(0.5 * x for x in correct(beta2, P, ut2, h, dt))", "u1 = tuple(correct(beta2, P, ut2, h, dt))",
      [T5.test_rk2_keeps_divergence_free_velocity_without_forces]),
     ("second stage leaves u^k out of Eq. poisson2", "rk2_step",
      "ut2 = tuple((a + b) + dt * r for a, b, r in zip(us, u, R2))", "ut2 = tuple(a + dt * r for a, r in zip(us, R2))",
      [T5.test_rk2_keeps_divergence_free_velocity_without_forces]),
+    ("second stage's R from u^k instead of u*", "rk2_step",
+     "R2 = momentum_rhs(phis, beta2, us, h, g, inv_re, mu_air, 1.0, convect)",
+     "R2 = momentum_rhs(phis, beta2, u, h, g, inv_re, mu_air, 1.0, convect)", [T6.test_rk2_second_order_in_time]),
     ("second projection solved with the first stage's density", "rk2_step",
      "P = solve(beta2, divergence(beta2, ut2, h, dt), h, tol=tol)", "P = solve(beta, divergence(beta, ut2, h, dt), h, tol=tol)",
      [T5.test_rk2_returns_divergence_free_velocity]),
