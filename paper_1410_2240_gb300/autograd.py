@@ -3,9 +3,12 @@
 ``project(u_star, phi)`` returns the divergence-free velocity u = u* - dt beta grad p
 (Eq. runge1) and the pressure p.  Its backward is the adjoint projection of the C ABI
 (mg_project_adjoint: one more solve with the same self-adjoint operator) followed by
-the chain rule to phi (mg_phi_grad).  Saved for backward: the face coefficients and p.
-The multigrid hierarchy lives in a cached context (see ``clear_cache``); backward
-rebuilds it only when another forward has rebuilt that context since this one.
+the chain rule to phi (mg_phi_grad).  Saved for backward: p, the one array the forward
+creates, and references to its inputs phi and the solid mask; the face coefficients are
+formed again from them in backward (mg_face_coeffs) unless the cached context still
+holds this forward's.  The multigrid hierarchy lives in that cached context (see
+``clear_cache``); backward rebuilds it only when another forward has rebuilt the
+context since this one.
 """
 from __future__ import annotations
 
@@ -35,7 +38,17 @@ def _context(beta, h, prec, token):
     elif getattr(mg, "built_for", None) is not token:
         mg.update(beta)
     mg.built_for = token
+    mg.beta = beta  # this forward's face coefficients, for a backward that finds the context unchanged
     return mg
+
+
+def _cached_beta(h, prec, shape, device, token):
+    """The face coefficients of the forward named by token, if its context still holds them."""
+    key = (tuple(shape), float(h), int(prec), device.index, torch.cuda.current_stream().cuda_stream)
+    mg = _CONTEXTS.get(key)
+    if mg is not None and getattr(mg, "built_for", None) is token:
+        return mg.beta
+    return None
 
 
 def clear_cache():
@@ -52,15 +65,18 @@ class _Project(torch.autograd.Function):
         mg = _context(beta, h, prec, ctx.token)
         p = torch.zeros_like(phi)
         u, p, st = mg.project((ux, uy, uz), p=p, dt=dt, tol=tol)
-        ctx.save_for_backward(p, *beta)
+        ctx.save_for_backward(phi, solid, p)
         ctx.cfg = (h, dt, rho_air, rho_water, tol, prec)
         ctx.mark_non_differentiable(p)
         return u[0], u[1], u[2], p
 
     @staticmethod
     def backward(ctx, gux, guy, guz, gp):
-        p, *beta = ctx.saved_tensors
+        phi, solid, p = ctx.saved_tensors
         h, dt, rho_air, rho_water, tol, prec = ctx.cfg
+        beta = _cached_beta(h, prec, p.shape, p.device, ctx.token)
+        if beta is None:
+            beta = mgproj.face_coeffs(phi.detach(), h, solid, rho_air, rho_water)
         w = tuple((g if g is not None else torch.zeros_like(p)).contiguous() for g in (gux, guy, guz))
         mg = _context(beta, h, prec, ctx.token)
         grad_u, grad_beta, _ = mg.project_adjoint(w, p, dt=dt, tol=tol, q=torch.zeros_like(p))

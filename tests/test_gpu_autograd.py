@@ -1,9 +1,11 @@
 """The differentiable projection (autograd.project) against the oracle's forward and adjoint.
 
-The autograd op keeps one multigrid context per grid and saves the face coefficients of
-its forward call; these tests check that a backward uses its own forward's coefficients
-and hierarchy also when other forwards on the same grid ran in between (the pattern of a
-Runge-Kutta step with two projections, or of a batch of projections on one grid).
+The autograd op keeps one multigrid context per grid and saves p with references to its
+inputs phi and the solid mask (the face coefficients are formed again in backward when the
+context no longer holds them); these tests check that a backward uses its own forward's
+coefficients and hierarchy also when other forwards on the same grid ran in between (the
+pattern of a Runge-Kutta step with two projections, or of a batch of projections on one grid),
+and that nothing but p is stored for backward.
 """
 import numpy as np
 import pytest
@@ -75,3 +77,15 @@ def test_repeated_steps_give_identical_gradients(ag):
         grads.append([host(phi.grad)] + [host(x.grad) for x in u])
     for g0, g1 in zip(*grads):
         assert np.array_equal(g0, g1)
+
+
+def test_saves_only_p_beside_its_inputs(ag):
+    """The graph holds phi (the caller's tensor itself), the solid mask and p: one array of the
+    grid's size per projection, not the face coefficients or the hierarchy."""
+    case = synth.small_case(16, seed=4, solid="ellipsoid")
+    phi, u, solid = _leaf(case)
+    (ux, uy, uz), p = ag.project(u, phi, case.h, solid=solid, rho_air=case.lam, tol=TOL, precision="mixed")
+    saved = ux.grad_fn.saved_tensors
+    assert len(saved) == 3
+    assert saved[0].data_ptr() == phi.data_ptr() and saved[1].data_ptr() == solid.data_ptr()
+    assert saved[2].data_ptr() == p.data_ptr()
