@@ -713,10 +713,21 @@ def rk2_bench(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # the momentum right-hand side alone (mg_momentum_rhs on u^k, phi^k): CUDA events over 10 calls
+    R = tuple(torch.empty_like(x) for x in u0)
+    for _ in range(2):
+        mgproj.momentum_rhs(phi, beta, u0, case.h, forces, out=R)
+    e0.record()
+    for _ in range(10):
+        mgproj.momentum_rhs(phi, beta, u0, case.h, forces, out=R)
+    e1.record()
+    torch.cuda.synchronize()
+    mom_ms = e0.elapsed_time(e1) / 10
     print(json.dumps({"metric": "Runge-Kutta time steps per second (2 projections to rel. resid 1e-10, gravity, "
                                 "viscous and convective terms, upwind VOF)", "value": K / (ms / 1e3), "unit": "steps/s",
                       "ms_per_step": ms / K,
                       "solves_per_s": 2 * K / (ms / 1e3), "second_stage_cg_iterations": cycles[-1],
+                      "momentum_rhs_ms": mom_ms,
                       "gpu_launches": int(mgproj.kernel_launches() - launches0), "steps": K, "warmup": W,
                       "config": {"workload": f"{args.n}^3 unit cube, 4-mode free surface (amp 0.08, seed 2) + "
                                              "piercing ellipsoid (0.3,0.06,0.05), rho_air/rho_water 1e-3, u^k ~ "

@@ -139,8 +139,12 @@ __global__ void __launch_bounds__(THREADS) k_rb_sweep_tma(const __grid_constant_
         return tiles + ((size_t)st * NA + a) * TILE;
     };
     auto at = [&](const float *t, int y, int x) -> float { return t[y * BW + x]; };
-    // thread 0: stage plane z (TMA for planes inside the grid, a bare arrive otherwise)
+    // thread 0: stage plane z (TMA for planes inside the grid, a bare arrive otherwise); planes are
+    // issued in order, each at most STAGES ahead of the oldest one not yet waited for, so every
+    // stage has at most one copy outstanding
+    int last_issued = zfirst - 1;
     auto issue = [&](int z) {
+        last_issued = z;
         unsigned long long *bar = &bars[(z - zfirst) % STAGES];
         if (z >= 0 && z < nz && z <= zlast) {
             mbar_expect_tx(bar, stage_bytes);
@@ -149,11 +153,15 @@ __global__ void __launch_bounds__(THREADS) k_rb_sweep_tma(const __grid_constant_
             mbar_arrive(bar);
         }
     };
-    // all threads: wait until plane z is staged; the decision to give up is CTA-uniform
+    // all threads: wait until plane z is staged; the decision to give up is CTA-uniform.
+    // next_wait: the oldest plane whose copy has not been waited for
+    int next_wait = zfirst;
     auto wait_plane = [&](int z) -> bool {
         const unsigned parity = (unsigned)(((z - zfirst) / STAGES) & 1);
         bool ok = mbar_wait(&bars[(z - zfirst) % STAGES], parity);
-        return !__syncthreads_or(!ok);
+        ok = !__syncthreads_or(!ok);
+        if (ok) next_wait = z + 1;
+        return ok;
     };
 
     if (threadIdx.x == 0) {
@@ -228,11 +236,11 @@ __global__ void __launch_bounds__(THREADS) k_rb_sweep_tma(const __grid_constant_
     // so on success no copy is in flight here
     if (!ok && threadIdx.x == 0) {
         dscal[S_ERR] = 1.0;
-        // bounded drain so that no copy is left writing into this CTA's shared memory
-        for (int st = 0; st < STAGES; st++) {
-            mbar_wait(&bars[st], 0);
-            mbar_wait(&bars[st], 1);
-        }
+        // drain: wait once more (bounded) for each plane issued and not yet waited for, on the
+        // phase its copy completes, so that no copy is left writing into this CTA's shared memory
+        // unless it is still not delivered after that second bounded wait
+        for (int z = next_wait; z <= last_issued; z++)
+            mbar_wait(&bars[(z - zfirst) % STAGES], (unsigned)(((z - zfirst) / STAGES) & 1));
     }
 }
 
