@@ -430,6 +430,21 @@ enum {
     MG_PROF_KRYLOV = 5, MG_PROF_COARSE = 6, MG_PROF_UPDATE = 7, MG_PROF_GROUPS = 8
 };
 uint64_t mg_kernel_launches(void);
+
+/*
+ * Bounds-check build.  A library compiled with -DMGP_CHECK (build(check=True):
+ * libmgproj_check.so) checks in its kernels, before the loads and stores, that
+ * every index a thread is about to use -- a cell, its stencil neighbours within
+ * the stencil's guards, a colour-split slot, a coarse cell, a row of the
+ * coarsest inverse -- lies inside the array it indexes; a thread with an index
+ * outside skips its accesses and records it (nothing traps).  mg_check_read
+ * returns the record since the previous read and resets it: *enabled = 1 in a
+ * check build (0 otherwise, with *first = *count = 0), *first = the kernel's
+ * check id << 48 | the index (0: none), *count = the number of skipped
+ * accesses.  Host pointers.  Returns MG_OK, MG_ERR_ARG (null pointer) or
+ * MG_ERR_CUDA.
+ */
+int mg_check_read(int *enabled, uint64_t *first, uint64_t *count);
 int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total);
 void mg_profile_reset(mg_ctx *c);
 

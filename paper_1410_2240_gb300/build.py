@@ -1,8 +1,10 @@
 """Build the CUDA library libmgproj.so in-tree (sm_103a only, nvcc, no cmake).
 
-Run ``python -m paper_1410_2240_gb300.build`` or call ``build()``.  The two
-translation units compile in parallel and are linked into
-``paper_1410_2240_gb300/_build/libmgproj.so`` (git-ignored).
+Run ``python -m paper_1410_2240_gb300.build`` or call ``build()``.  The translation
+units compile in parallel and are linked into ``paper_1410_2240_gb300/_build/libmgproj.so``
+(git-ignored).  ``build(check=True)`` (``--check``) makes the bounds-check variant
+``_build/check/libmgproj_check.so``, compiled with -DMGP_CHECK: its kernels check every index
+before they use it and record instead of accessing out of range (mg_check_read).
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmgproj.so")
+CHECK_DIR = os.path.join(OUT_DIR, "check")
+LIB_CHECK = os.path.join(CHECK_DIR, "libmgproj_check.so")
 SOURCES = ["mg_kernels.cu", "mg_api.cu", "mg_noalloc.cu", "mg_sweep_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,18 +37,21 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    lib, out_dir = (LIB_CHECK, CHECK_DIR) if check else (LIB, OUT_DIR)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps():
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
                     "-I", os.path.join(ROOT, "include")]
+    if check:
+        flags += ["-DMGP_CHECK"]
     if verbose:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -56,15 +63,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for _, err in results:
             sys.stderr.write(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-cudart", "static", "-Xcompiler",
                                                                              "-fopenmp", "-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

@@ -1509,6 +1509,19 @@ int mg_level_array(mg_ctx *c, int level, int which, double *out)
 
 uint64_t mg_kernel_launches(void) { return (uint64_t)mg::launch_count(); }
 
+int mg_check_read(int *enabled, uint64_t *first, uint64_t *count)
+{
+    g_err.clear();
+    if (!enabled || !first || !count) return fail(MG_ERR_ARG, "mg_check_read: null argument");
+    unsigned long long f = 0, n = 0;
+    const int r = mg::check_read(&f, &n);
+    if (r < 0) return fail(MG_ERR_CUDA, "mg_check_read: reading the check record failed");
+    *enabled = r;
+    *first = f;
+    *count = n;
+    return MG_OK;
+}
+
 int mg_profile_read(mg_ctx *c, int group, int *count, double *ms_total)
 {
     g_err.clear();

@@ -49,6 +49,11 @@ enum Scal {
     S_COUNT = 16
 };
 
+// bounds-check build (-DMGP_CHECK): the first recorded out-of-range index (kernel id << 48 |
+// index) and the number of skipped accesses since the last read, then reset; returns 1 in a check
+// build, 0 otherwise (first = count = 0), -1 if the device copy failed
+int check_read(unsigned long long *first, unsigned long long *count);
+
 // total kernels launched by this library in this process
 unsigned long long launch_count();
 void note_kernel_launch();

@@ -129,6 +129,52 @@ __device__ __forceinline__ bool pos_bits(float x) { return __float_as_int(x) > 0
 __device__ __forceinline__ bool zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool zero_bits(float x) { return (__float_as_int(x) << 1) == 0; }
 
+// ---------------------------------------------------------------------------
+// Bounds-check build (-DMGP_CHECK).  Before its loads and stores a kernel checks that every index
+// it is about to use, within the guards of its stencil, lies inside the array it indexes
+// (nx*ny*nz cells, a colour half, a coarse level); a thread with an index outside skips its
+// accesses and records the kernel and the index (the first such record and a count, read by
+// mg_check_read).  Nothing traps.  In the normal build MG_CK is the constant true and every check
+// folds away.
+// ---------------------------------------------------------------------------
+enum CheckKernel : unsigned {
+    CK_SMOOTH = 1, CK_SMOOTH_SPLIT, CK_SMOOTH_SPLIT4, CK_RESTRICT, CK_RESTRICT_PAIRS, CK_PROLONG, CK_COARSE_SOLVE,
+    CK_TAIL, CK_RESID, CK_SPLIT_SLOT, CK_PCG_APPLY, CK_DIVERGENCE, CK_CORRECT, CK_ADJOINT, CK_PHI_GRAD,
+    CK_FACE_COEFFS, CK_DIAG_INV, CK_MOMENTUM, CK_LABEL, CK_VOF
+};
+#ifdef MGP_CHECK
+__device__ unsigned long long g_check_first = 0;  // kernel id << 48 | (index & (2^48 - 1)); 0: none
+__device__ unsigned long long g_check_count = 0;
+__device__ __noinline__ void ck_record(unsigned kid, long long idx)
+{
+    atomicAdd(&g_check_count, 1ull);
+    atomicCAS(&g_check_first, 0ull,
+              ((unsigned long long)kid << 48) | ((unsigned long long)idx & 0xffffffffffffull));
+}
+// [lo, hi] inside [0, n)
+__device__ __forceinline__ bool ck_in(long long lo, long long hi, long long n, unsigned kid)
+{
+    if (lo >= 0 && hi < n) return true;
+    ck_record(kid, lo < 0 ? lo : hi);
+    return false;
+}
+#define MG_CK(lo, hi, n, kid) ck_in((long long)(lo), (long long)(hi), (long long)(n), (unsigned)(kid))
+#else
+#define MG_CK(lo, hi, n, kid) true
+#endif
+// cell c = (i, j, k) and the neighbours its guards admit (i > 0: c - 1, i < nx - 1: c + 1, ...)
+// inside the nx*ny*nz cells
+__device__ __forceinline__ bool ck_cell(long long c, int i, int j, int k, int nx, int ny, int nz, unsigned kid)
+{
+    const long long n = (long long)nx * ny * nz, sxy = (long long)nx * ny;
+    (void)n;
+    (void)sxy;
+    return MG_CK(c, c, n, kid) && (i == 0 || MG_CK(c - 1, c - 1, n, kid)) &&
+           (i >= nx - 1 || MG_CK(c + 1, c + 1, n, kid)) && (j == 0 || MG_CK(c - nx, c - nx, n, kid)) &&
+           (j >= ny - 1 || MG_CK(c + nx, c + nx, n, kid)) && (k == 0 || MG_CK(c - sxy, c - sxy, n, kid)) &&
+           (k >= nz - 1 || MG_CK(c + sxy, c + sxy, n, kid));
+}
+
 inline dim3 run_grid(int nx, int ny, int nz)
 {
     return dim3((unsigned)((nx + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)((nz + kRun - 1) / kRun));
@@ -306,6 +352,7 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
     const int j = blockIdx.y, k = blockIdx.z + z0;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
     if (i >= nx) return;
+    if (!ck_cell(((long long)k * ny + j) * nx + i, i, j, k, nx, ny, nz, CK_SMOOTH)) return;
     smooth_cell<T, true>(i, j, k, nx, ny, nz, h2, L, b, p);
 }
 
@@ -386,6 +433,14 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
     const float *__restrict__ o = p + (colour ? 0 : half);  // the other colour
     const int odd = i & 1;
     const size_t own = (colour ? half : 0) + m;
+    if (!(ck_cell((long long)c, i, j, k, nx, ny, nz, CK_SMOOTH_SPLIT) && MG_CK(m, m, half, CK_SMOOTH_SPLIT) &&
+          (i == 0 || MG_CK(m - 1 + odd, m - 1 + odd, half, CK_SMOOTH_SPLIT)) &&
+          (i >= nx - 1 || MG_CK(m + odd, m + odd, half, CK_SMOOTH_SPLIT)) &&
+          (j == 0 || MG_CK((long long)m - (long long)hx, m, half, CK_SMOOTH_SPLIT)) &&
+          (j >= ny - 1 || MG_CK(m, m + hx, half, CK_SMOOTH_SPLIT)) &&
+          (k == 0 || MG_CK((long long)m - (long long)hxy, m, half, CK_SMOOTH_SPLIT)) &&
+          (k >= nz - 1 || MG_CK(m, m + hxy, half, CK_SMOOTH_SPLIT))))
+        return;
     // the neighbours and b are loaded before the row's uniform value is known, so a uniform row
     // waits for one memory round trip, not two
     const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
@@ -437,6 +492,23 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
     const float *__restrict__ o = p + (colour ? 0 : half);
     float *own = p + (colour ? half : 0);
     const float *bo = b + (colour ? half : 0);
+    {
+        const long long n = (long long)sxy * nz, c0 = 2 * (long long)mb, m = (long long)mb;
+        (void)n;
+        (void)c0;
+        (void)m;
+        if (!(MG_CK(m, m + 3, half, CK_SMOOTH_SPLIT4) &&
+              (OFF ? (g >= G - 1 || MG_CK(m + 4, m + 4, half, CK_SMOOTH_SPLIT4))
+                   : (g == 0 || MG_CK(m - 1, m - 1, half, CK_SMOOTH_SPLIT4))) &&
+              (j == 0 || MG_CK(m - (long long)hx, m - (long long)hx + 3, half, CK_SMOOTH_SPLIT4)) &&
+              (j >= ny - 1 || MG_CK(m + hx, m + hx + 3, half, CK_SMOOTH_SPLIT4)) &&
+              (k == 0 || MG_CK(m - (long long)hxy, m - (long long)hxy + 3, half, CK_SMOOTH_SPLIT4)) &&
+              (k >= nz - 1 || MG_CK(m + hxy, m + hxy + 3, half, CK_SMOOTH_SPLIT4)) &&
+              (v != 0.f || (MG_CK(c0, c0 + 7 + ((OFF && 8 * g + 7 < nx - 1) ? 1 : 0), n, CK_SMOOTH_SPLIT4) &&
+                            (j >= ny - 1 || MG_CK(c0 + nx, c0 + nx + 7, n, CK_SMOOTH_SPLIT4)) &&
+                            (k >= nz - 1 || MG_CK(c0 + sxy, c0 + sxy + 7, n, CK_SMOOTH_SPLIT4))))))
+            return;
+    }
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 ox = *reinterpret_cast<const float4 *>(o + mb);
     const float oxe = OFF ? ((g < G - 1) ? o[mb + 4] : 0.f) : ((g > 0) ? o[mb - 1] : 0.f);
@@ -528,6 +600,7 @@ template <typename T>
 __device__ __forceinline__ T residual_at(int i, int j, int k, size_t c, int nx, int ny, int nz, size_t sxy, T ih2,
                                          const LevelArrays<T> &L, const T *b, const T *p)
 {
+    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_RESID)) return T(0);
     const T pc = p[c];
     T s = T(0);
     if (i > 0) s = fma(L.bx[c], p[c - 1] - pc, s);
@@ -565,6 +638,9 @@ __device__ __forceinline__ void restrict_cell(int I, int J, int K, int nx, int n
 {
     const int NX = nx / 2, NY = ny / 2;
     const size_t sxy = (size_t)nx * ny;
+    if (!MG_CK(((long long)K * NY + J) * NX + I, ((long long)K * NY + J) * NX + I, (long long)NX * NY * (nz / 2),
+               CK_RESTRICT))
+        return;
     T s = T(0);
 #pragma unroll
     for (int dk = 0; dk < 2; dk++)
@@ -612,6 +688,21 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
     const size_t sxy = (size_t)nx * ny;
     const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
     const bool xhi = i0 + 2 < nx, ylo = j0 > 0, yhi = j0 + 2 < ny, zlo = k0 > 0, zhi = k0 + 2 < nz;
+    {
+        // the lowest and highest fine cells any load reaches: (i0 - 1, j0 - 1 | j0, k0 - 1 | k0) ...
+        // (i0 + 2, j0 + 2, k0 + 1) within the guards, and the coarse cell
+        const long long n = (long long)sxy * nz;
+        const long long lo = ((long long)(k0 - (zlo ? 1 : 0)) * ny + j0 - (ylo ? 1 : 0)) * nx + i0 - (i0 > 0 ? 1 : 0);
+        const long long hi = ((long long)(k0 + (zhi ? 2 : 1)) * ny + j0 + (yhi ? 2 : 1)) * nx + i0 + (xhi ? 2 : 1);
+        (void)n;
+        (void)lo;
+        (void)hi;
+        if (!(MG_CK(lo, hi, n, CK_RESTRICT_PAIRS) &&
+              MG_CK(((long long)K * NY + J) * NX + I, ((long long)K * NY + J) * NX + I, (long long)NX * NY * (nz / 2),
+                    CK_RESTRICT_PAIRS) &&
+              (!SPLIT || MG_CK(lo >> 1, hi >> 1, (long long)half, CK_RESTRICT_PAIRS))))
+            return;
+    }
     auto ld2 = [](const float *a, size_t c) { return *reinterpret_cast<const float2 *>(a + c); };
     // p and b pairs: natural, or the two colours' slots c >> 1 (row parity q decides the order)
     auto ldf2 = [&](const float *a, size_t c, int q) {
@@ -717,6 +808,11 @@ __device__ __forceinline__ void prolong_corr(int I, int J, int K, int NX, int NY
     const int Is[3] = {max(I - 1, 0), I, min(I + 1, NX - 1)};
     const int Js[3] = {max(J - 1, 0), J, min(J + 1, NY - 1)};
     const int Ks[3] = {max(K - 1, 0), K, min(K + 1, NZ - 1)};
+    if (!(MG_CK(((long long)Ks[0] * NY + Js[0]) * NX + Is[0], ((long long)Ks[2] * NY + Js[2]) * NX + Is[2],
+                (long long)NX * NY * NZ, CK_PROLONG))) {
+        for (int q = 0; q < 8; q++) (&corr[0][0][0])[q] = T(0);
+        return;
+    }
     T e[3][3][3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -752,6 +848,16 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
     const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
     if (I >= NX) return;
+    {
+        const long long n = (long long)nx * ny * nz;
+        const long long c0 = ((long long)(2 * K) * ny + 2 * J) * nx + 2 * I;
+        const long long c1 = ((long long)(2 * K + 1) * ny + 2 * J + 1) * nx + 2 * I + 1;
+        (void)n;
+        (void)c0;
+        (void)c1;
+        if (!(MG_CK(c0, c1, n, CK_PROLONG) && (!SPLIT || MG_CK(c0 >> 1, c1 >> 1, (long long)half, CK_PROLONG))))
+            return;
+    }
     P2 dv[2][2], pv[2][2];
 #pragma unroll
     for (int dz = 0; dz < 2; dz++)
@@ -914,6 +1020,7 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ M, const T *__r
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     for (int r = blockIdx.x * warps + warp; r < n; r += gridDim.x * warps) {
+        if (!MG_CK((long long)r * n, (long long)r * n + n - 1, (long long)n * n, CK_COARSE_SOLVE)) continue;
         const double *row = M + (size_t)r * n;
         double s = 0.0;
         for (int q = lane; q < n; q += 32) s = fma(row[q], sb[q], s);
@@ -942,7 +1049,8 @@ __device__ void tail_colour(const TailLevel<T> &v, int colour)
         const int jk = (int)fdiv(t, v.fhx), k = (int)fdiv(jk, v.fny);
         const int u = t - jk * hx, j = jk - k * v.ny;
         const int i = 2 * u + ((j + k + colour) & 1);
-        if (i < v.nx) smooth_cell<T, true>(i, j, k, v.nx, v.ny, v.nz, v.h2, v.L, v.L.b, v.L.p);
+        if (i < v.nx && ck_cell(((long long)k * v.ny + j) * v.nx + i, i, j, k, v.nx, v.ny, v.nz, CK_TAIL))
+            smooth_cell<T, true>(i, j, k, v.nx, v.ny, v.nz, v.h2, v.L, v.L.b, v.L.p);
     }
     __syncthreads();
 }
@@ -975,6 +1083,7 @@ __device__ void tail_prolong(const TailLevel<T> &f, const T *ec)
 #pragma unroll
                 for (int dx = 0; dx < 2; dx++) {
                     const size_t c = ((size_t)(2 * K + dz) * f.ny + (2 * J + dy)) * f.nx + 2 * I + dx;
+                    if (!MG_CK(c, c, (long long)f.nx * f.ny * f.nz, CK_TAIL)) continue;
                     if (!zero_bits(f.L.dinv[c])) f.L.p[c] = f.L.p[c] + corr[dz][dy][dx];
                 }
     }
@@ -1110,7 +1219,8 @@ __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<dou
         const double r = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         rr += r * r;
         if (pos_bits(L.dinv[idx])) sp += p[idx];
-        r32[half ? split_slot(idx, (j + k) & 1, half) : idx] = (float)(r * inv_scale);
+        const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
+        if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = (float)(r * inv_scale);
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
@@ -1141,6 +1251,7 @@ __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *
     const double s = dscal[scale_slot];
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const size_t e = sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx;
+        if (!MG_CK(e, e, (long long)n, CK_SPLIT_SLOT)) continue;
         p[idx] = fma(s, widen(e32[e]), p[idx]);
     }
 }
@@ -1150,12 +1261,18 @@ __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *
 __global__ void k_to_f32_layout(unsigned n, const double *__restrict__ src, float *__restrict__ dst, Split sp)
 {
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        dst[sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx] = (float)src[idx];
+    {
+        const size_t e = sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx;
+        if (MG_CK(e, e, (long long)n, CK_SPLIT_SLOT)) dst[e] = (float)src[idx];
+    }
 }
 __global__ void k_from_f32_layout(unsigned n, const float *__restrict__ src, double *__restrict__ dst, Split sp)
 {
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        dst[idx] = widen(src[sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx]);
+    {
+        const size_t e = sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx;
+        if (MG_CK(e, e, (long long)n, CK_SPLIT_SLOT)) dst[idx] = widen(src[e]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1170,6 +1287,7 @@ __global__ void k_divergence(int nx, int ny, int nz, double scale, const double 
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_DIVERGENCE)) return;
     double d = 0.0;
     if (i < nx - 1 && pos_bits(bx[c + 1])) d += ux[c + 1];
     if (pos_bits(bx[c])) d -= ux[c];
@@ -1385,6 +1503,7 @@ __global__ void k_momentum_rhs(MomArgs m)
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= m.nx) return;
     const size_t c = ((size_t)k * m.ny + j) * m.nx + i;
+    if (!MG_CK(c, c, (long long)m.nx * m.ny * m.nz, CK_MOMENTUM)) return;
     const double bx = m.beta.bx[c], by = m.beta.by[c], bz = m.beta.bz[c];
     m.r.bx[c] = pos_bits(bx) ? mom_face<0>(m, i, j, k, bx) : 0.0;
     m.r.by[c] = pos_bits(by) ? mom_face<1>(m, i, j, k, by) : 0.0;
@@ -1410,6 +1529,7 @@ __global__ void k_vof_upwind(int nx, int ny, int nz, double s, LevelArrays<doubl
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_VOF)) return;
     auto upw = [&](double uf, size_t lo, size_t hi) { return __dmul_rn(uf, pos_bits(uf) ? phi[lo] : phi[hi]); };
     double d = 0.0;
     if (i < nx - 1 && pos_bits(mask.bx[c + 1])) d = __dadd_rn(d, upw(u.bx[c + 1], c, c + 1));
@@ -1474,6 +1594,7 @@ __global__ void k_correct(int nx, int ny, int nz, double dt, double h, double in
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_CORRECT)) return;
     const double pc = p[c];
     double b = bx[c], u = ux0[c], bv = val.bx ? val.bx[c] : b;
     if (i > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
@@ -1533,6 +1654,7 @@ __global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double inv_h, 
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_ADJOINT)) return;
     const double pc = p[c], qc = q[c];
     double gu, gb;
     adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, inv_h, pow2, dt, area.bx, c, gu,
@@ -1559,6 +1681,7 @@ __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const d
     if (i >= nx) return;
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
+    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_PHI_GRAD)) return;
     double s = 0.0;
     s = __dadd_rn(s, __dmul_rn(__dmul_rn(bx[c], bx[c]), gbx[c]));
     if (i < nx - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(bx[c + 1], bx[c + 1]), gbx[c + 1]));
@@ -1597,7 +1720,10 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
         cell_of(idx, nx, ny, i, j, k);
         const double v = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         r[idx] = v;
-        if (r32) r32[half ? split_slot(idx, (j + k) & 1, half) : idx] = (float)(v * inv_scale);
+        if (r32) {
+            const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
+            if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = (float)(v * inv_scale);
+        }
         rr += v * v;
         if (pos_bits(L.dinv[idx])) sp += p[idx];
     }
@@ -1683,6 +1809,7 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
             const int q = row_parity(2 * v, sp);
             i0 = (q ? sp.half : 0) + v;
             i1 = (q ? 0 : sp.half) + v;
+            if (!(MG_CK(i0, i0, (long long)n, CK_SPLIT_SLOT) && MG_CK(i1, i1, (long long)n, CK_SPLIT_SLOT))) continue;
         }
         const double z0 = widen(z[i0]), z1 = widen(z[i1]);
         double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
@@ -1718,6 +1845,7 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, LevelArrays<double> L, const
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int i, j, k;
         cell_of(idx, nx, ny, i, j, k);
+        if (!ck_cell(idx, i, j, k, nx, ny, nz, CK_PCG_APPLY)) continue;
         const double dc = d[idx];
         double s = -diag[idx] * dc;
         if (i > 0) s = fma(L.bx[idx], d[idx - 1], s);
@@ -1813,7 +1941,11 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
 // ---------------------------------------------------------------------------
 constexpr unsigned kCcBudget = 1u << 26;
 
-__device__ __forceinline__ int cc_load(const int *label, int x) { return *(const volatile int *)(label + x); }
+__device__ __forceinline__ int cc_load(const int *label, int x)
+{
+    if (!MG_CK(x, x, 0x7fffffffll, CK_LABEL)) return x;
+    return *(const volatile int *)(label + x);
+}
 
 __device__ __forceinline__ int cc_find(const int *label, int x, unsigned &budget)
 {
@@ -2594,6 +2726,22 @@ cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, doubl
     note_launch();
     k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, -1);
     return cudaGetLastError();
+}
+
+int check_read(unsigned long long *first, unsigned long long *count)
+{
+#ifdef MGP_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(first, g_check_first, sizeof *first);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(count, g_check_count, sizeof *count);
+    const unsigned long long zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_first, &zero, sizeof zero);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_count, &zero, sizeof zero);
+    return e == cudaSuccess ? 1 : -1;
+#else
+    *first = 0;
+    *count = 0;
+    return 0;
+#endif
 }
 
 }  // namespace mg

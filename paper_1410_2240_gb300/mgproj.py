@@ -5,7 +5,9 @@ the same name; all arithmetic runs in the library's CUDA kernels.  Tensors are
 torch CUDA tensors (device memory and streams come from PyTorch): float64,
 contiguous, shape (nz, ny, nx); face fields are 3-tuples of such tensors in the
 low-face layout.  Importing this module loads the library and raises if it has
-not been built (there is no fallback).
+not been built (there is no fallback).  The environment variable MGPROJ_LIB names
+another build of the same library to load instead (the bounds-check build,
+build(check=True)).
 """
 from __future__ import annotations
 
@@ -21,10 +23,11 @@ from .build import LIB
 MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, MG_ERR_NAN, MG_ERR_INCOMPATIBLE, MG_ERR_OOM = 0, 1, 2, 3, 4, 5, 6
 MG_FP64, MG_MIXED = 0, 1
 
-if not os.path.exists(LIB):
-    raise ImportError(f"{LIB} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+LIB_PATH = os.environ.get("MGPROJ_LIB", LIB)
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
                       "or `python -m paper_1410_2240_gb300.build`")
-_lib = ctypes.CDLL(LIB)
+_lib = ctypes.CDLL(LIB_PATH)
 
 _vp = ctypes.c_void_p
 _P3 = _vp * 3
@@ -98,8 +101,18 @@ _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)
 _lib.mg_profile_reset.argtypes = [_vp]
 _lib.mg_residual_norm_noalloc.argtypes = [ctypes.POINTER(Grid), _PP, _vp, _vp, _vp, _vp]
 _lib.mg_destroy.argtypes = [_vp]
+_lib.mg_check_read.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_uint64)]
 
 PROF_SMOOTH, PROF_RESTRICT, PROF_PROLONG, PROF_RESID64, PROF_APPLY, PROF_KRYLOV, PROF_COARSE, PROF_UPDATE = range(8)
+
+
+def check_read():
+    """mg_check_read: (enabled, first record, count) of the bounds-check build since the last read;
+    (False, 0, 0) from the normal build."""
+    en, first, count = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.mg_check_read(ctypes.byref(en), ctypes.byref(first), ctypes.byref(count)))
+    return bool(en.value), int(first.value), int(count.value)
 
 
 def kernel_launches() -> int:
@@ -111,7 +124,7 @@ EXPORTS = ["mg_default_opts", "mg_face_coeffs", "mg_setup", "mg_update", "mg_sol
            "mg_correct", "mg_project", "mg_project_adjoint", "mg_phi_grad", "mg_num_levels", "mg_level_dims",
            "mg_level_array", "mg_kernel_launches", "mg_profile_read", "mg_profile_reset",
            "mg_residual_norm_noalloc", "mg_destroy", "mg_last_error", "mg_face_areas", "mg_set_face_areas",
-           "mg_set_body_velocity", "mg_stretched_metrics", "mg_rk2_step", "mg_momentum_rhs"]
+           "mg_set_body_velocity", "mg_stretched_metrics", "mg_rk2_step", "mg_momentum_rhs", "mg_check_read"]
 
 
 class MGError(RuntimeError):

@@ -34,6 +34,15 @@ def test_library_exports_every_declared_symbol():
     assert set(_declared()) <= exported
 
 
+def test_check_build_exports_every_declared_symbol():
+    """The bounds-check variant (-DMGP_CHECK) builds for sm_103a and exports the same boundary."""
+    from paper_1410_2240_gb300.build import build
+    lib_path = build(check=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mg_\w+)", out))
+    assert set(_declared()) <= exported
+
+
 def test_binding_lists_every_declared_symbol():
     src = open(os.path.join(ROOT, "paper_1410_2240_gb300", "mgproj.py")).read()
     m = re.search(r"EXPORTS = \[(.*?)\]", src, re.S)
