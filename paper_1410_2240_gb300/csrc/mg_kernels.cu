@@ -349,9 +349,9 @@ template <typename T>
 __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T *__restrict__ b,
                          T *__restrict__ p, int colour, int z0)
 {
-    const int j = blockIdx.y, k = blockIdx.z + z0;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z + z0;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
-    if (i >= nx) return;
+    if (i >= nx || j >= ny) return;
     if (!ck_cell(((long long)k * ny + j) * nx + i, i, j, k, nx, ny, nz, CK_SMOOTH)) return;
     smooth_cell<T, true>(i, j, k, nx, ny, nz, h2, L, b, p);
 }
@@ -659,8 +659,8 @@ template <typename T>
 __global__ void k_resid_restrict(int nx, int ny, int nz, T ih2, LevelArrays<T> L, const T *__restrict__ b,
                                  const T *__restrict__ p, T *__restrict__ bc)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
-    if (I >= nx / 2) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y, K = blockIdx.z;
+    if (I >= nx / 2 || J >= ny / 2) return;
     restrict_cell<T>(I, J, K, nx, ny, nz, ih2, L, b, p, bc);
 }
 
@@ -682,9 +682,10 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
 {
     const int NX = nx / 2, NY = ny / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = rev ? NY - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    const int Jb = blockIdx.y * blockDim.y + threadIdx.y;
+    const int J = rev ? NY - 1 - Jb : Jb;
     const int K = rev ? nz / 2 - 1 - (int)blockIdx.z : (int)blockIdx.z;
-    if (I >= NX) return;
+    if (I >= NX || Jb >= NY) return;
     const size_t sxy = (size_t)nx * ny;
     const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
     const bool xhi = i0 + 2 < nx, ylo = j0 > 0, yhi = j0 + 2 < ny, zlo = k0 > 0, zhi = k0 + 2 < nz;
@@ -846,8 +847,8 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
 {
     using P2 = typename Pair<T>::type;
     const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
-    if (I >= NX) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y, K = blockIdx.z;
+    if (I >= NX || J >= NY) return;
     {
         const long long n = (long long)nx * ny * nz;
         const long long c0 = ((long long)(2 * K) * ny + 2 * J) * nx + 2 * I;
@@ -2158,6 +2159,22 @@ inline dim3 row_grid(int threads_x, int ny, int nz)
     return dim3((unsigned)((threads_x + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)nz);
 }
 
+// Blocks of kRowThreads threads over rows of threads_x threads each: x the next power of two >=
+// threads_x (at most kRowThreads), the rest of the block over consecutive rows, so that a coarse
+// level's short rows (32 or 64 threads) do not leave most of each block idle.  Kernels launched so
+// take their row from blockIdx.y * blockDim.y + threadIdx.y and skip rows past the last.
+inline dim3 row_block2(int threads_x)
+{
+    int bx = 1;
+    while (bx < threads_x && bx < kRowThreads) bx *= 2;
+    return dim3((unsigned)bx, (unsigned)(kRowThreads / bx));
+}
+inline dim3 row_grid2(int threads_x, int ny, int nz)
+{
+    const dim3 b = row_block2(threads_x);
+    return dim3((unsigned)((threads_x + b.x - 1) / b.x), (unsigned)((ny + b.y - 1) / b.y), (unsigned)nz);
+}
+
 inline unsigned red_grid(size_t n)
 {
     size_t b = (n + kRedThreads - 1) / kRedThreads;
@@ -2223,8 +2240,8 @@ cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *
     if (z1 < 0) z1 = d.nz;
     if (z1 <= z0) return cudaSuccess;
     note_launch();
-    k_smooth<T><<<row_grid((d.nx + 1) / 2, d.ny, z1 - z0), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour,
-                                                                                z0);
+    k_smooth<T><<<row_grid2((d.nx + 1) / 2, d.ny, z1 - z0), row_block2((d.nx + 1) / 2), 0, s>>>(
+        d.nx, d.ny, d.nz, h2, L, b, p, colour, z0);
     return cudaGetLastError();
 }
 template cudaError_t launch_smooth<double>(Dims, double, const LevelArrays<double> &, const double *, double *, int,
@@ -2265,17 +2282,16 @@ cudaError_t launch_resid_restrict(Dims f, T ih2, const LevelArrays<T> &L, const 
                                   cudaStream_t s, Split sp, const float *urow, int rev)
 {
     note_launch();
-    const dim3 g = row_grid(f.nx / 2, f.ny / 2, f.nz / 2);
+    const dim3 g = row_grid2(f.nx / 2, f.ny / 2, f.nz / 2), blk = row_block2(f.nx / 2);
     if constexpr (std::is_same<T, float>::value) {
         if (sp.half)
-            k_resid_restrict_pairs<true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half, urow,
-                                                                    rev);
+            k_resid_restrict_pairs<true><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, sp.half, urow, rev);
         else
-            k_resid_restrict_pairs<false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0, urow, rev);
+            k_resid_restrict_pairs<false><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc, 0, urow, rev);
     } else {
         if (urow) return cudaErrorInvalidValue;  // uniform rows describe FP32 coefficients
         if (sp.half) return cudaErrorInvalidValue;  // FP64 fields are never split
-        k_resid_restrict<T><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc);
+        k_resid_restrict<T><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ih2, L, b, p, bc);
     }
     return cudaGetLastError();
 }
@@ -2288,16 +2304,16 @@ template <typename T>
 cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp)
 {
     note_launch();
-    const dim3 g = row_grid(f.nx / 2, f.ny / 2, f.nz / 2);
+    const dim3 g = row_grid2(f.nx / 2, f.ny / 2, f.nz / 2), blk = row_block2(f.nx / 2);
     if constexpr (std::is_same<T, float>::value) {
         if (sp.half) {
-            k_prolong<T, true><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, sp.half);
+            k_prolong<T, true><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, sp.half);
             return cudaGetLastError();
         }
     } else if (sp.half) {
         return cudaErrorInvalidValue;  // FP64 fields are never split
     }
-    k_prolong<T, false><<<g, kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, 0);
+    k_prolong<T, false><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, 0);
     return cudaGetLastError();
 }
 template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t, Split);
