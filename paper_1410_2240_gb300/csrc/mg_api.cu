@@ -402,8 +402,11 @@ int tail_start(const mg_ctx *c)
     return -1;
 }
 
+// zero: p is taken as zero on entry (a cycle from a zero guess): the coarsest solve overwrites it,
+// the coarse tail zeroes it in its kernel, and the per-colour passes start with a pass that reads
+// no iterate, so no separate clearing pass is needed (the fused sweeps and nu1 = 0 clear it first)
 template <typename T>
-int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T *p)
+int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T *p, bool zero = false)
 {
     cudaStream_t s = c->s;
     const Dims d = c->dims[l];
@@ -416,6 +419,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
         a.nlev = c->nlev - l;
         a.nu1 = c->o.nu1;
         a.nu2 = c->o.nu2;
+        a.zero0 = zero ? 1 : 0;
         for (int q = 0; q < a.nlev; q++) {
             const int lv = l + q;
             const Dims dl = c->dims[lv];
@@ -447,6 +451,9 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     // the last (ascending) pre-smoothing pass runs descending
     const bool alternate = c->o.pass_order == 1 && sp.half;
     int npass = 0;
+    // the first pass reads no iterate when p starts at zero; otherwise clear p first
+    bool zpass = zero && !fused && c->o.nu1 >= 1;
+    if (zero && !zpass) CK(cudaMemsetAsync(p, 0, d.n() * sizeof(T), s));
     // one red-black sweep, `first` colour first
     auto sweep = [&](int first) -> int {
         ProfScope ps(c, MG_PROF_SMOOTH, fine);
@@ -459,14 +466,15 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
         } else if (sp.half) {
             if constexpr (std::is_same<T, float>::value) {
                 const int r0 = alternate ? (npass + 1) & 1 : 0;
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow, r0));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow, r0, zpass));
                 CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow, arow, r0 ^ (alternate ? 1 : 0)));
                 npass += 2;
             }
         } else {
-            CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s));
+            CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first, s, 0, -1, zpass));
             CK(mg::launch_smooth<T>(d, h2, L[l], b, cur, first ^ 1, s));
         }
+        zpass = false;
         return MG_OK;
     };
     for (int it = 0; it < c->o.nu1; it++) CKS(sweep(0));
@@ -482,10 +490,8 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
         ProfScope ps(c, MG_PROF_COARSE, fine);
         if (fine && c->o.coarse_graph && !c->capturing)
             CKS(coarse_correction_graph<T>(c, L));
-        else {
-            CK(cudaMemsetAsync(C.p, 0, c->dims[l + 1].n() * sizeof(T), s));
-            CKS(vcycle<T>(c, L, l + 1, C.b, C.p));
-        }
+        else
+            CKS(vcycle<T>(c, L, l + 1, C.b, C.p, true));
     }
     {
         ProfScope ps(c, MG_PROF_PROLONG, fine);
@@ -514,8 +520,7 @@ int coarse_correction_graph(mg_ctx *c, const std::vector<LevelArrays<T>> &L)
         cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             st = [&]() -> int {
-                CK(cudaMemsetAsync(L[1].p, 0, c->dims[1].n() * sizeof(T), c->s));
-                CKS(vcycle<T>(c, L, 1, L[1].b, L[1].p));
+                CKS(vcycle<T>(c, L, 1, L[1].b, L[1].p, true));
                 return MG_OK;
             }();
             e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -682,8 +687,8 @@ int solve_impl(mg_ctx *c, const double *rhs, double *p, double tol, mg_stats *st
         }
         cyc++;
         if (mixed) {
-            CK(cudaMemsetAsync(c->L32[0].p, 0, d.n() * sizeof(float), s));
-            for (int ic = 0; ic < c->o.inner_cycles; ic++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, c->L32[0].p));
+            for (int ic = 0; ic < c->o.inner_cycles; ic++)
+                CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, c->L32[0].p, ic == 0));
             CK(mg::launch_accumulate(d, c->L64[0].dinv, c->L32[0].p, p, c->dscal, scale_slot, s, c->split0));
             std::swap(scale_slot, next_slot);
             ProfScope ps(c, MG_PROF_RESID64, true);
@@ -846,11 +851,9 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
         if (c->o.precond == 1) {
             CK(mg::launch_jacobi(n, -c->hs[0] * c->hs[0], c->L64[0].dinv, c->kr, z, s));
         } else if (mixed) {
-            CK(cudaMemsetAsync(e_cur, 0, n * sizeof(float), s));
-            for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, e_cur));
+            for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<float>(c, c->L32, 0, c->L32[0].b, e_cur, v == 0));
         } else {
-            CK(cudaMemsetAsync(z, 0, n * sizeof(double), s));
-            for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<double>(c, c->L64, 0, c->kr, z));
+            for (int v = 0; v < c->o.inner_cycles; v++) CKS(vcycle<double>(c, c->L64, 0, c->kr, z, v == 0));
         }
         return MG_OK;
     };

@@ -99,6 +99,7 @@ struct TailLevel {
 template <typename T>
 struct TailArgs {
     int nlev, nu1, nu2;
+    int zero0;  // nonzero: lev[0].p starts at zero (zeroed here, not by the caller)
     TailLevel<T> lev[kTailMaxLevels];
 };
 
@@ -114,16 +115,17 @@ cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *di
 cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s);
 cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
-// one colour of a red-black sweep on planes [z0, z1) (z1 < 0: to the last plane)
+// one colour of a red-black sweep on planes [z0, z1) (z1 < 0: to the last plane); zero: the
+// iterate is zero and is not read (the first pass of a cycle from a zero guess)
 template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
-                          int z0 = 0, int z1 = -1);
+                          int z0 = 0, int z1 = -1, bool zero = false);
 // one colour of a red-black sweep on the colour-split layout (FP32, all dims even); urow (optional):
 // the level's uniform-row values, arow (optional, nx % 8 == 0, replaces urow in the sweep): its
 // banded-row records (launch_uniform_rows); rev: blocks take the planes in descending order
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
                                 cudaStream_t s, const float *urow = nullptr, const float4 *arow = nullptr,
-                                int rev = 0);
+                                int rev = 0, bool zero = false);
 // urow[k*ny + j] = v if every face around row (j,k) but its two x-walls equals v, else 0; arow
 // (optional) = {vx, vy, vzl, vzh} if the row's x-, y-, low z- and high z-faces hold one value
 // each, else zeros; count (optional, two counters, incremented): uniform rows, banded rows that

@@ -324,8 +324,10 @@ __device__ __forceinline__ T inv_diag(T stored, T bxl, T bxh, T byl, T byh, T bz
 // products accumulated with fused multiply-adds in that order.
 // ---------------------------------------------------------------------------
 // one cell's update (shared by k_smooth and the coarse tail, so both round alike).  STORED: take
-// 1/sum from L.dinv also in FP32, where the hierarchy stores exactly inv_diag's value
-template <typename T, bool STORED = false>
+// 1/sum from L.dinv also in FP32, where the hierarchy stores exactly inv_diag's value.  ZERO: the
+// iterate is zero (the first pass of a cycle from a zero guess): the neighbours are not read, the
+// products with +0 give the +0 sum the loads of a zeroed array would
+template <typename T, bool STORED = false, bool ZERO = false>
 __device__ __forceinline__ void smooth_cell(int i, int j, int k, int nx, int ny, int nz, T h2, const LevelArrays<T> &L,
                                             const T *b, T *p)
 {
@@ -335,17 +337,18 @@ __device__ __forceinline__ void smooth_cell(int i, int j, int k, int nx, int ny,
     const T bxl = L.bx[c], bxh = (i < nx - 1) ? L.bx[c + 1] : T(0);
     const T byl = L.by[c], byh = (j < ny - 1) ? L.by[c + nx] : T(0);
     const T bzl = L.bz[c], bzh = (k < nz - 1) ? L.bz[c + sxy] : T(0);
-    if (i > 0) s = fma(bxl, p[c - 1], s);
-    if (i < nx - 1) s = fma(bxh, p[c + 1], s);
-    if (j > 0) s = fma(byl, p[c - nx], s);
-    if (j < ny - 1) s = fma(byh, p[c + nx], s);
-    if (k > 0) s = fma(bzl, p[c - sxy], s);
-    if (k < nz - 1) s = fma(bzh, p[c + sxy], s);
+    auto nb = [&](size_t q) { return ZERO ? T(0) : p[q]; };
+    if (i > 0) s = fma(bxl, nb(c - 1), s);
+    if (i < nx - 1) s = fma(bxh, nb(c + 1), s);
+    if (j > 0) s = fma(byl, nb(c - nx), s);
+    if (j < ny - 1) s = fma(byh, nb(c + nx), s);
+    if (k > 0) s = fma(bzl, nb(c - sxy), s);
+    if (k < nz - 1) s = fma(bzh, nb(c + sxy), s);
     const T d = (STORED || sizeof(T) == 8) ? L.dinv[c] : inv_diag<T>(T(0), bxl, bxh, byl, byh, bzl, bzh);
     p[c] = d * fma(-h2, b[c], s);
 }
 
-template <typename T>
+template <typename T, bool ZERO>
 __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T *__restrict__ b,
                          T *__restrict__ p, int colour, int z0)
 {
@@ -353,7 +356,7 @@ __global__ void k_smooth(int nx, int ny, int nz, T h2, LevelArrays<T> L, const T
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
     if (i >= nx || j >= ny) return;
     if (!ck_cell(((long long)k * ny + j) * nx + i, i, j, k, nx, ny, nz, CK_SMOOTH)) return;
-    smooth_cell<T, true>(i, j, k, nx, ny, nz, h2, L, b, p);
+    smooth_cell<T, true, ZERO>(i, j, k, nx, ny, nz, h2, L, b, p);
 }
 
 // Colour-split layout (Split in mg_internal.cuh): slot of natural cell c in a row of parity
@@ -422,7 +425,7 @@ __global__ void k_uniform_rows(int nx, int ny, int nz, const float *__restrict__
 // b.  Same arithmetic, in the same order, as k_smooth<float>.  Used where nx % 8 != 0
 // (k_smooth_split4 otherwise).
 __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
-                               float *__restrict__ p, int colour, const float *__restrict__ urow, int rev)
+                               float *__restrict__ p, int colour, const float *__restrict__ urow, int rev, int zero)
 {
     const int j = rev ? ny - 1 - (int)blockIdx.y : (int)blockIdx.y, k = rev ? nz - 1 - (int)blockIdx.z : (int)blockIdx.z;
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + colour) & 1);
@@ -444,9 +447,10 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
     // the neighbours and b are loaded before the row's uniform value is known, so a uniform row
     // waits for one memory round trip, not two
     const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
-    const float pxm = i > 0 ? o[m - 1 + odd] : 0.f, pxp = i < nx - 1 ? o[m + odd] : 0.f;
-    const float pym = j > 0 ? o[m - hx] : 0.f, pyp = j < ny - 1 ? o[m + hx] : 0.f;
-    const float pzm = k > 0 ? o[m - hxy] : 0.f, pzp = k < nz - 1 ? o[m + hxy] : 0.f;
+    // zero: the iterate is zero (first pass of a cycle from a zero guess), nothing to read
+    const float pxm = (!zero && i > 0) ? o[m - 1 + odd] : 0.f, pxp = (!zero && i < nx - 1) ? o[m + odd] : 0.f;
+    const float pym = (!zero && j > 0) ? o[m - hx] : 0.f, pyp = (!zero && j < ny - 1) ? o[m + hx] : 0.f;
+    const float pzm = (!zero && k > 0) ? o[m - hxy] : 0.f, pzp = (!zero && k < nz - 1) ? o[m + hxy] : 0.f;
     const float bv = b[own];
     float bxl, bxh, byl, byh, bzl, bzh;
     if (v != 0.f) {  // uniform row: the stored values, x-walls 0
@@ -480,7 +484,7 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
 // OFF = (j + k + colour) & 1, the x offset of the colour in the row (uniform across a warp).
 // BAND: the row's record is {vx, vy, vzl, vzh} of a banded row (all four equal on a uniform row,
 // zeros elsewhere), else {v, v, v, v} from urow.
-template <int OFF, bool BAND>
+template <int OFF, bool BAND, bool ZERO>
 __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, const LevelArrays<float> &L,
                                             const float *__restrict__ b, float *__restrict__ p, int colour, float4 rv,
                                             int g, int j, int k)
@@ -510,12 +514,13 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
             return;
     }
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 ox = *reinterpret_cast<const float4 *>(o + mb);
-    const float oxe = OFF ? ((g < G - 1) ? o[mb + 4] : 0.f) : ((g > 0) ? o[mb - 1] : 0.f);
-    const float4 oym = j > 0 ? *reinterpret_cast<const float4 *>(o + mb - hx) : zero4;
-    const float4 oyp = j < ny - 1 ? *reinterpret_cast<const float4 *>(o + mb + hx) : zero4;
-    const float4 ozm = k > 0 ? *reinterpret_cast<const float4 *>(o + mb - hxy) : zero4;
-    const float4 ozp = k < nz - 1 ? *reinterpret_cast<const float4 *>(o + mb + hxy) : zero4;
+    // ZERO: the other colour is zero (first pass of a cycle from a zero guess), nothing to read
+    const float4 ox = ZERO ? zero4 : *reinterpret_cast<const float4 *>(o + mb);
+    const float oxe = ZERO ? 0.f : (OFF ? ((g < G - 1) ? o[mb + 4] : 0.f) : ((g > 0) ? o[mb - 1] : 0.f));
+    const float4 oym = (!ZERO && j > 0) ? *reinterpret_cast<const float4 *>(o + mb - hx) : zero4;
+    const float4 oyp = (!ZERO && j < ny - 1) ? *reinterpret_cast<const float4 *>(o + mb + hx) : zero4;
+    const float4 ozm = (!ZERO && k > 0) ? *reinterpret_cast<const float4 *>(o + mb - hxy) : zero4;
+    const float4 ozp = (!ZERO && k < nz - 1) ? *reinterpret_cast<const float4 *>(o + mb + hxy) : zero4;
     const float4 bv = *reinterpret_cast<const float4 *>(bo + mb);
     const float xs[6] = {OFF ? 0.f : oxe, ox.x, ox.y, ox.z, ox.w, OFF ? oxe : 0.f};  // slots mb-1 .. mb+4
     const float oy0[4] = {oym.x, oym.y, oym.z, oym.w}, oy1[4] = {oyp.x, oyp.y, oyp.z, oyp.w};
@@ -573,7 +578,7 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
     }
     *reinterpret_cast<float4 *>(own + mb) = make_float4(out[0], out[1], out[2], out[3]);
 }
-template <bool BAND>
+template <bool BAND, bool ZERO>
 __global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
                                 float *__restrict__ p, int colour, const float *__restrict__ urow,
                                 const float4 *__restrict__ arow, int rev)
@@ -591,8 +596,8 @@ __global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<fl
         const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
         rv = make_float4(v, v, v, v);
     }
-    if ((j + k + colour) & 1) split4_body<1, BAND>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
-    else split4_body<0, BAND>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
+    if ((j + k + colour) & 1) split4_body<1, BAND, ZERO>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
+    else split4_body<0, BAND, ZERO>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
 }
 
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
@@ -1098,7 +1103,7 @@ __global__ void __launch_bounds__(kTailDownThreads) k_tail_down(TailArgs<T> a)
 {
     for (int l = 0; l < a.nlev - 1; l++) {
         const TailLevel<T> v = a.lev[l];
-        if (l > 0) {
+        if (l > 0 || a.zero0) {
             const int n = v.nx * v.ny * v.nz;
             for (int t = threadIdx.x; t < n; t += blockDim.x) v.L.p[t] = T(0);
             __syncthreads();
@@ -2235,34 +2240,47 @@ cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_
 
 template <typename T>
 cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *p, int colour, cudaStream_t s,
-                          int z0, int z1)
+                          int z0, int z1, bool zero)
 {
     if (z1 < 0) z1 = d.nz;
     if (z1 <= z0) return cudaSuccess;
     note_launch();
-    k_smooth<T><<<row_grid2((d.nx + 1) / 2, d.ny, z1 - z0), row_block2((d.nx + 1) / 2), 0, s>>>(
-        d.nx, d.ny, d.nz, h2, L, b, p, colour, z0);
+    const dim3 g = row_grid2((d.nx + 1) / 2, d.ny, z1 - z0), blk = row_block2((d.nx + 1) / 2);
+    if (zero)
+        k_smooth<T, true><<<g, blk, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, z0);
+    else
+        k_smooth<T, false><<<g, blk, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, z0);
     return cudaGetLastError();
 }
 template cudaError_t launch_smooth<double>(Dims, double, const LevelArrays<double> &, const double *, double *, int,
-                                           cudaStream_t, int, int);
+                                           cudaStream_t, int, int, bool);
 template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> &, const float *, float *, int,
-                                          cudaStream_t, int, int);
+                                          cudaStream_t, int, int, bool);
 
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s, const float *urow, const float4 *arow, int rev)
+                                cudaStream_t s, const float *urow, const float4 *arow, int rev, bool zero)
 {
     note_launch();
     if (d.nx % 8 == 0) {  // four cells per thread, blocks of 32 threads x 4 rows
         const int G = d.nx / 8;
         const dim3 grid((G + 31) / 32, (d.ny + 3) / 4, d.nz), block(32, 4);
-        if (arow)
-            k_smooth_split4<true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow, rev);
-        else
-            k_smooth_split4<false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, nullptr, rev);
+        if (arow) {
+            if (zero)
+                k_smooth_split4<true, true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow, rev);
+            else
+                k_smooth_split4<true, false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow,
+                                                                    rev);
+        } else {
+            if (zero)
+                k_smooth_split4<false, true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, nullptr,
+                                                                    rev);
+            else
+                k_smooth_split4<false, false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow,
+                                                                     nullptr, rev);
+        }
     } else {
         k_smooth_split<<<row_grid(d.nx / 2, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour,
-                                                                              urow, rev);
+                                                                              urow, rev, zero ? 1 : 0);
     }
     return cudaGetLastError();
 }
