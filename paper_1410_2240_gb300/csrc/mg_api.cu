@@ -495,7 +495,7 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
     }
     {
         ProfScope ps(c, MG_PROF_PROLONG, fine);
-        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, cur, s, sp));
+        CK(mg::launch_prolong<T>(d, C.p, L[l].dinv, cur, s, sp, urow));
     }
     for (int it = 0; it < c->o.nu2; it++) CKS(sweep(1));
     if (cur != p) CK(cudaMemcpyAsync(p, cur, d.n() * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -894,10 +894,10 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
         CKS(precondition());
         if (mixed) {
             CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, nullptr, c->partials, c->dscal, sc_cur, sc_cur, -1, s));
-            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, -1, 1, s, c->split0));
+            CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, -1, 1, s, c->split0, c->partials));
         } else {
             CK(mg::launch_pcg_dots<double>(n, c->kr, z, nullptr, c->partials, c->dscal, -1, -1, s));
-            CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, -1, 1, s));
+            CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, -1, 1, s, {}, c->partials));
         }
         for (;;) {
             it++;
@@ -922,10 +922,10 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
             if (mixed) {
                 CK(mg::launch_pcg_dots32(n, c->L32[0].b, e_cur, e_old, c->partials, c->dscal, sc_cur, sc_cur, sc_old,
                                          s));
-                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, sc_old, 0, s, c->split0));
+                CK(mg::launch_pcg_dir<float>(n, e_cur, c->kd, c->dscal, sc_cur, sc_old, 0, s, c->split0, c->partials));
             } else {
                 CK(mg::launch_pcg_dots<double>(n, c->kr, z, zo, c->partials, c->dscal, -1, -1, s));
-                CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, -1, 0, s));
+                CK(mg::launch_pcg_dir<double>(n, z, c->kd, c->dscal, -1, -1, 0, s, {}, c->partials));
             }
         }
         if (!std::isfinite(rel)) {
@@ -1053,7 +1053,9 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     c->L64.resize(c->nlev);
     for (int l = 0; l < c->nlev && st == MG_OK; l++) st = level_alloc<double>(c, c->L64[l], c->dims[l].n(), l > 0);
     if (st == MG_OK) st = c->alloc(&c->b0, c->dims[0].n());
-    if (st == MG_OK) st = c->alloc(&c->partials, 2 * mg::kRedBlocks);
+    if (st == MG_OK) st = c->alloc(&c->partials, mg::kRedPartials);
+    if (st == MG_OK && cudaMemsetAsync(c->partials, 0, mg::kRedPartials * sizeof(double), c->s) != cudaSuccess)
+        st = fail(MG_ERR_CUDA, "mg_setup: memset failed");
     if (st == MG_OK) st = c->alloc(&c->dscal, mg::S_COUNT);
     if (st == MG_OK) st = c->alloc(&c->M, (size_t)c->ncoarse * c->ncoarse);
     if (st == MG_OK) st = c->alloc(&c->cc_label, c->dims[0].n());

@@ -27,8 +27,11 @@ struct LevelArrays {
 };
 
 // Number of CTAs of the grid-stride vector and reduction kernels (16 per SM on 152 SMs,
-// enough loads in flight to keep HBM busy).
+// enough loads in flight to keep HBM busy).  A reduction's partials buffer holds 2 * kRedBlocks
+// doubles and, after them, the counter of the blocks that have finished (kRedPartials doubles in
+// all, the counter zero between reductions).
 constexpr int kRedBlocks = 2432;
+constexpr int kRedPartials = 2 * kRedBlocks + 2;
 constexpr int kRedThreads = 256;
 
 // Device scalar slots (FP64) in ctx->dscal.
@@ -147,7 +150,9 @@ template <typename T>
 cudaError_t launch_resid_restrict(Dims fine, T ih2, const LevelArrays<T> &L, const T *b, const T *p, T *bc,
                                   cudaStream_t s, Split sp = {}, const float *urow = nullptr, int rev = 0);
 template <typename T>
-cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp = {});
+// urow (optional, FP32): the fine level's uniform-row values (cells of uniform rows are all live)
+cudaError_t launch_prolong(Dims fine, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp = {},
+                           const float *urow = nullptr);
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double *M, const T *b, T *e, cudaStream_t s);
 // the coarse tail's descent (pre-smoothing, restriction down to lev[nlev-1].b) and ascent
@@ -214,7 +219,7 @@ cudaError_t launch_jacobi(size_t n, double scale, const double *dinv, const doub
 // so_slot: the scale of the previous D (-1 on the first direction or without scales)
 template <typename Z>
 cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int so_slot, int first,
-                           cudaStream_t s, Split sp = {});
+                           cudaStream_t s, Split sp, double *partials);
 // op: face coefficients and diagonal pre-scaled by h^-2 (op.dinv holds the scaled diagonal)
 cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double *dv, double *q, double *partials,
                              double *dscal, cudaStream_t s);

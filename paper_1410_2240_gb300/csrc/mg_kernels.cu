@@ -68,6 +68,39 @@ __global__ void k_finish2(const double *__restrict__ partials, int nblocks, doub
     }
 }
 
+// The end of a grid-wide reduction in the reducing kernel itself: every block stores its pair of
+// block sums (valid in thread 0); the last block to finish -- a counter in the word after the
+// 2 * kRedBlocks partials, reset by that block -- sums the pairs in k_finish2's order and writes
+// dscal[slot0], dscal[slot1] (slots < 0: not written).  The same sums as a separate k_finish2
+// launch, one launch fewer.  Returns true in the last block (all its threads).
+__device__ bool reduce_finish(double a, double b, double *partials, double *dscal, int slot0, int slot1)
+{
+    __shared__ bool last;
+    unsigned *ctr = reinterpret_cast<unsigned *>(partials + 2 * kRedBlocks);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double x = 0.0, y = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        x += __ldcg(partials + 2 * i);
+        y += __ldcg(partials + 2 * i + 1);
+    }
+    x = block_sum<kRedThreads>(x);
+    y = block_sum<kRedThreads>(y);
+    if (threadIdx.x == 0) {
+        if (slot0 >= 0) dscal[slot0] = x;
+        if (slot1 >= 0) dscal[slot1] = y;
+        *ctr = 0u;
+    }
+    return true;
+}
+
 __device__ __forceinline__ void cell_of(unsigned idx, int nx, int ny, int &i, int &j, int &k)
 {
     const unsigned t = idx / (unsigned)nx;
@@ -140,7 +173,7 @@ __device__ __forceinline__ bool zero_bits(float x) { return (__float_as_int(x) <
 enum CheckKernel : unsigned {
     CK_SMOOTH = 1, CK_SMOOTH_SPLIT, CK_SMOOTH_SPLIT4, CK_RESTRICT, CK_RESTRICT_PAIRS, CK_PROLONG, CK_COARSE_SOLVE,
     CK_TAIL, CK_RESID, CK_SPLIT_SLOT, CK_PCG_APPLY, CK_DIVERGENCE, CK_CORRECT, CK_ADJOINT, CK_PHI_GRAD,
-    CK_FACE_COEFFS, CK_DIAG_INV, CK_MOMENTUM, CK_LABEL, CK_VOF
+    CK_FACE_COEFFS, CK_DIAG_INV, CK_MOMENTUM, CK_LABEL, CK_VOF, CK_NARROW
 };
 #ifdef MGP_CHECK
 __device__ unsigned long long g_check_first = 0;  // kernel id << 48 | (index & (2^48 - 1)); 0: none
@@ -162,6 +195,38 @@ __device__ __forceinline__ bool ck_in(long long lo, long long hi, long long n, u
 #else
 #define MG_CK(lo, hi, n, kid) true
 #endif
+// double -> float, rounded to nearest (ties to even), on the integer pipe: the hardware conversion
+// issues on the FP64 unit, the limiting resource of the FP64 passes that hand an FP32 copy to the
+// cycles.  From the IEEE 754 layouts: the exponent rebiased (1023 -> 127), the 52-bit fraction cut
+// to its top 23 bits and rounded by the 29 bits cut off (above half, or exactly half with an odd
+// result, adds one unit; a carry into the exponent is the correct rounding, up to infinity).
+// Zeros map exactly; results that would be subnormal, and infinities and NaNs, take the hardware
+// conversion.  The check build compares every result with the hardware conversion.
+__device__ __noinline__ float d2f_slow(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float narrow(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    float f;
+    if (e == 0 && m == 0) {
+        f = __uint_as_float(sgn);
+    } else if (e - 896 <= 0 || e - 896 >= 255) {
+        f = d2f_slow(x);
+    } else {
+        const unsigned mant = (unsigned)(m >> 29), rest = (unsigned)(m & 0x1fffffffull);
+        unsigned u = sgn | ((unsigned)(e - 896) << 23) | mant;
+        if (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) u += 1u;
+        f = __uint_as_float(u);
+    }
+#ifdef MGP_CHECK
+    if (__float_as_uint(f) != __float_as_uint(__double2float_rn(x)) && !(isnan(x) && isnan(f)))
+        ck_record(CK_NARROW, (long long)(b >> 16));
+#endif
+    return f;
+}
+
 // cell c = (i, j, k) and the neighbours its guards admit (i > 0: c - 1, i < nx - 1: c + 1, ...)
 // inside the nx*ny*nz cells
 __device__ __forceinline__ bool ck_cell(long long c, int i, int j, int k, int nx, int ny, int nz, unsigned kid)
@@ -303,7 +368,7 @@ __global__ void k_restrict_coeffs(int nx, int ny, int nz, const double *__restri
 __global__ void k_cast_f32(size_t n, const double *__restrict__ src, float *__restrict__ dst)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+        dst[i] = narrow(src[i]);
 }
 
 // Inverse diagonal of a smoothing update: FP64 levels use the stored 1/sum(beta); FP32 levels
@@ -846,9 +911,11 @@ __device__ __forceinline__ void prolong_corr(int I, int J, int K, int NX, int NY
             }
 }
 
+// urow (optional, the finest FP32 level): a fine row with a uniform value has every cell live, so
+// its inverse diagonals are not read
 template <typename T, bool SPLIT>
 __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, const T *__restrict__ dinv,
-                          T *__restrict__ p, size_t half)
+                          T *__restrict__ p, size_t half, const float *__restrict__ urow)
 {
     using P2 = typename Pair<T>::type;
     const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
@@ -870,7 +937,12 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
 #pragma unroll
         for (int dy = 0; dy < 2; dy++) {
             const size_t c = ((size_t)(2 * K + dz) * ny + (2 * J + dy)) * nx + 2 * I;
-            dv[dz][dy] = *reinterpret_cast<const P2 *>(dinv + c);
+            if (urow && urow[(size_t)(2 * K + dz) * ny + 2 * J + dy] != 0.f) {
+                dv[dz][dy].x = T(1);
+                dv[dz][dy].y = T(1);
+            } else {
+                dv[dz][dy] = *reinterpret_cast<const P2 *>(dinv + c);
+            }
             if (SPLIT) {  // the pair's two colours at slot c >> 1 of each half
                 const size_t m = c >> 1;
                 const bool q = (2 * J + dy + 2 * K + dz) & 1;
@@ -1134,35 +1206,27 @@ __global__ void __launch_bounds__(kTailUpThreads) k_tail_up(TailArgs<T> a)
 // ---------------------------------------------------------------------------
 // Fine-level reductions (FP64, grid-stride, per-block partial pairs)
 // ---------------------------------------------------------------------------
-__global__ void k_count_live(unsigned n, const double *__restrict__ dinv, double *__restrict__ partials)
+__global__ void k_count_live(unsigned n, const double *__restrict__ dinv, double *__restrict__ partials, double *dscal)
 {
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
         a += pos_bits(dinv[idx]) ? 1.0 : 0.0;
-    a = block_sum<kRedThreads>(a);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = 0.0;
-    }
+    reduce_finish(block_sum<kRedThreads>(a), 0.0, partials, dscal, S_NLIVE, -1);
 }
 
 // pass 1 of the rhs preparation: sum of rhs over live cells
 __global__ void k_sum_live(unsigned n, const double *__restrict__ v, const double *__restrict__ dinv,
-                           double *__restrict__ partials)
+                           double *__restrict__ partials, double *dscal)
 {
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
         if (pos_bits(dinv[idx])) a += v[idx];
-    a = block_sum<kRedThreads>(a);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = 0.0;
-    }
+    reduce_finish(block_sum<kRedThreads>(a), 0.0, partials, dscal, S_SUM_B, -1);
 }
 
 // pass 2: b0 = rhs - mean on live cells, 0 elsewhere; partial ||b0||^2
 __global__ void k_rhs_center(unsigned n, const double *__restrict__ rhs, const double *__restrict__ dinv,
-                             double *__restrict__ b0, const double *__restrict__ dscal, double *__restrict__ partials)
+                             double *__restrict__ b0, double *dscal, double *__restrict__ partials)
 {
     const double mean = dscal[S_SUM_B] / dscal[S_NLIVE];
     double a = 0.0;
@@ -1171,16 +1235,13 @@ __global__ void k_rhs_center(unsigned n, const double *__restrict__ rhs, const d
         b0[idx] = v;
         a += v * v;
     }
-    a = block_sum<kRedThreads>(a);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = 0.0;
-    }
+    reduce_finish(block_sum<kRedThreads>(a), 0.0, partials, dscal, S_NB2, -1);
 }
 
 // ||b - A p||^2 and sum of p over live cells
 __global__ void k_resid_norm(int nx, int ny, int nz, double ih2, LevelArrays<double> L,
-                             const double *__restrict__ b, const double *__restrict__ p, double *__restrict__ partials)
+                             const double *__restrict__ b, const double *__restrict__ p, double *__restrict__ partials,
+                             double *dscal)
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
@@ -1194,10 +1255,7 @@ __global__ void k_resid_norm(int nx, int ny, int nz, double ih2, LevelArrays<dou
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = rr;
-        partials[2 * blockIdx.x + 1] = sp;
-    }
+    reduce_finish(rr, sp, partials, dscal, S_RR, S_SUM_P);
 }
 
 // p -= mean of p over live cells (mean = dscal[S_SUM_P] / dscal[S_NLIVE]); dead cells 0
@@ -1212,8 +1270,7 @@ __global__ void k_sub_mean_p(unsigned n, const double *__restrict__ dinv, double
 // Mixed refinement: r = b - A p in FP64, stored as FP32 r / scale_in; partial ||r||^2.
 __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<double> L,
                              const double *__restrict__ b, const double *__restrict__ p, float *__restrict__ r32,
-                             const double *__restrict__ dscal, int scale_in, double *__restrict__ partials,
-                             size_t half)
+                             double *dscal, int scale_in, int scale_out, double *__restrict__ partials, size_t half)
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
@@ -1226,21 +1283,15 @@ __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<dou
         rr += r * r;
         if (pos_bits(L.dinv[idx])) sp += p[idx];
         const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
-        if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = (float)(r * inv_scale);
+        if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = narrow(r * inv_scale);
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = rr;
-        partials[2 * blockIdx.x + 1] = sp;
+    // the last block also sets the next scale: the RMS of this residual over the live cells (1 if 0)
+    if (reduce_finish(rr, sp, partials, dscal, S_RR, S_SUM_P) && threadIdx.x == 0 && scale_out >= 0) {
+        const double rms = sqrt(dscal[S_RR] / dscal[S_NLIVE]);
+        dscal[scale_out] = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
     }
-}
-
-// next scale = RMS of the residual over live cells (1 if zero)
-__global__ void k_set_scale(double *dscal, int slot)
-{
-    const double rms = sqrt(dscal[S_RR] / dscal[S_NLIVE]);
-    dscal[slot] = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
 }
 
 __global__ void k_scale_from_nb2(double *dscal, int slot)
@@ -1269,7 +1320,7 @@ __global__ void k_to_f32_layout(unsigned n, const double *__restrict__ src, floa
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
     {
         const size_t e = sp.half ? split_slot(idx, row_parity(idx, sp), sp.half) : idx;
-        if (MG_CK(e, e, (long long)n, CK_SPLIT_SLOT)) dst[e] = (float)src[idx];
+        if (MG_CK(e, e, (long long)n, CK_SPLIT_SLOT)) dst[e] = narrow(src[idx]);
     }
 }
 __global__ void k_from_f32_layout(unsigned n, const float *__restrict__ src, double *__restrict__ dst, Split sp)
@@ -1728,23 +1779,20 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
         r[idx] = v;
         if (r32) {
             const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
-            if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = (float)(v * inv_scale);
+            if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = narrow(v * inv_scale);
         }
         rr += v * v;
         if (pos_bits(L.dinv[idx])) sp += p[idx];
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = rr;
-        partials[2 * blockIdx.x + 1] = sp;
-    }
+    reduce_finish(rr, sp, partials, dscal, S_RR, S_SUM_P);
 }
 
 // <r, z> and <r, z_old> with z = sz * Z, z_old = so * Zo (Z double: scales 1)
 template <typename Z>
 __global__ void k_pcg_dots(unsigned n, const double *__restrict__ r, const Z *__restrict__ z, const Z *__restrict__ zo,
-                           const double *__restrict__ dscal, int sz_slot, int so_slot, double *__restrict__ partials)
+                           double *dscal, int sz_slot, int so_slot, double *__restrict__ partials)
 {
     const double sz = sz_slot >= 0 ? dscal[sz_slot] : 1.0;
     const double so = so_slot >= 0 ? dscal[so_slot] : 1.0;
@@ -1756,17 +1804,14 @@ __global__ void k_pcg_dots(unsigned n, const double *__restrict__ r, const Z *__
     }
     a = block_sum<kRedThreads>(a) * sz;
     c = block_sum<kRedThreads>(c) * so;
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = c;
-    }
+    reduce_finish(a, c, partials, dscal, S_RZN, S_RZO);
 }
 
 // Mixed-precision variant: <r, z> = sr sz <r32, e32> from the FP32 copy r32 = r / sr that the
 // preconditioner read.  Products and short per-thread sums are FP32, block sums FP64: the CG
 // scalars need only the accuracy of the FP32 preconditioner they weigh.
 __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const float *__restrict__ z,
-                             const float *__restrict__ zo, const double *__restrict__ dscal, int sr_slot, int sz_slot,
+                             const float *__restrict__ zo, double *dscal, int sr_slot, int sz_slot,
                              int so_slot, double *__restrict__ partials)
 {
     const double sr = dscal[sr_slot];
@@ -1789,10 +1834,7 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
     }
     a = block_sum<kRedThreads>(a) * sr * dscal[sz_slot];
     c = block_sum<kRedThreads>(c) * (so_slot >= 0 ? sr * dscal[so_slot] : 0.0);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = c;
-    }
+    reduce_finish(a, c, partials, dscal, S_RZN, S_RZO);
 }
 
 // The search direction d = sz Z + beta d_old, beta = (<r,z> - <r,z_old>) / <r_old, z_old> (first:
@@ -1801,8 +1843,8 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
 // update then moves p and r by <r,z> / (sz <D, A D>) times D and A D (k_pcg_update), the same
 // step.  Without scales (sz_slot, so_slot < 0) D = d.
 template <typename Z>
-__global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, const double *__restrict__ dscal,
-                          int sz_slot, int so_slot, int first, Split sp)
+__global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, double *dscal,
+                          int sz_slot, int so_slot, int first, Split sp, double *__restrict__ partials)
 {
     const double beta = first ? 0.0
                               : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ] *
@@ -1825,9 +1867,9 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
     }
     for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride)
         d[idx] = fma(beta, first ? 0.0 : d[idx], widen(z[idx]));
+    // every block has read <r, z> above: the last one moves the new <r, z> into its place
+    if (reduce_finish(0.0, 0.0, partials, dscal, -1, -1) && threadIdx.x == 0) dscal[S_RZ] = dscal[S_RZN];
 }
-
-__global__ void k_pcg_shift_rz(double *dscal) { dscal[S_RZ] = dscal[S_RZN]; }
 
 // Jacobi preconditioner: z = (scale * dinv) * r, dead cells 0
 __global__ void k_jacobi(unsigned n, double scale, const double *__restrict__ dinv, const double *__restrict__ r,
@@ -1843,7 +1885,8 @@ __global__ void k_jacobi(unsigned n, double scale, const double *__restrict__ di
 // only perturbs the recursive residual; convergence is confirmed on the true residual in
 // difference form.
 __global__ void k_pcg_apply(int nx, int ny, int nz, LevelArrays<double> L, const double *__restrict__ diag,
-                            const double *__restrict__ d, double *__restrict__ q, double *__restrict__ partials)
+                            const double *__restrict__ d, double *__restrict__ q, double *__restrict__ partials,
+                            double *dscal)
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
@@ -1864,18 +1907,14 @@ __global__ void k_pcg_apply(int nx, int ny, int nz, LevelArrays<double> L, const
         q[idx] = qv;
         dq = fma(dc, qv, dq);
     }
-    dq = block_sum<kRedThreads>(dq);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = dq;
-        partials[2 * blockIdx.x + 1] = 0.0;
-    }
+    reduce_finish(block_sum<kRedThreads>(dq), 0.0, partials, dscal, S_SIGMA, -1);
 }
 
 // alpha = <r,z>/<d,Ad>; p += alpha d; r -= alpha q; ||r||^2; optionally r32 = r / scale with
 // scale = RMS of the previous residual (written to scale_slot).  Two elements per iteration.
 __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const double *__restrict__ q,
                              double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
-                             double *__restrict__ dscal, int scale_slot, int sd_slot, double *__restrict__ partials,
+                             double *dscal, int scale_slot, int sd_slot, double *__restrict__ partials,
                              Split sp)
 {
     // d holds D = (direction) / sd (k_pcg_dir): alpha = <r,z> / <d, A d> times sd
@@ -1905,7 +1944,7 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
         p2[v] = pv;
         rv2[v] = rv;
         if (r32) {
-            const float r0 = (float)rv.x * inv_scale32, r1 = (float)rv.y * inv_scale32;
+            const float r0 = narrow(rv.x) * inv_scale32, r1 = narrow(rv.y) * inv_scale32;
             if (sp.half) {  // colour-split r32: the pair's colours at slot v of each half
                 const int qp = row_parity(2 * v, sp);
                 r32[(qp ? sp.half : 0) + v] = r0;
@@ -1921,14 +1960,10 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
         p[idx] = fma(alpha, d[idx], p[idx]);
         const double rv = fma(-alpha, q[idx], r[idx]);
         r[idx] = rv;
-        if (r32) r32[idx] = (float)rv * inv_scale32;
+        if (r32) r32[idx] = narrow(rv) * inv_scale32;
         rr = fma(rv, rv, rr);
     }
-    rr = block_sum<kRedThreads>(rr);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = rr;
-        partials[2 * blockIdx.x + 1] = 0.0;
-    }
+    reduce_finish(block_sum<kRedThreads>(rr), 0.0, partials, dscal, S_RR, -1);
 }
 
 
@@ -2319,23 +2354,25 @@ template cudaError_t launch_resid_restrict<float>(Dims, float, const LevelArrays
                                                   const float *, float *, cudaStream_t, Split, const float *, int);
 
 template <typename T>
-cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp)
+cudaError_t launch_prolong(Dims f, const T *ec, const T *dinv, T *p, cudaStream_t s, Split sp, const float *urow)
 {
     note_launch();
     const dim3 g = row_grid2(f.nx / 2, f.ny / 2, f.nz / 2), blk = row_block2(f.nx / 2);
     if constexpr (std::is_same<T, float>::value) {
         if (sp.half) {
-            k_prolong<T, true><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, sp.half);
+            k_prolong<T, true><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, sp.half, urow);
             return cudaGetLastError();
         }
     } else if (sp.half) {
         return cudaErrorInvalidValue;  // FP64 fields are never split
     }
-    k_prolong<T, false><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, 0);
+    k_prolong<T, false><<<g, blk, 0, s>>>(f.nx, f.ny, f.nz, ec, dinv, p, 0, sizeof(T) == 4 ? urow : nullptr);
     return cudaGetLastError();
 }
-template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t, Split);
-template cudaError_t launch_prolong<float>(Dims, const float *, const float *, float *, cudaStream_t, Split);
+template cudaError_t launch_prolong<double>(Dims, const double *, const double *, double *, cudaStream_t, Split,
+                                            const float *);
+template cudaError_t launch_prolong<float>(Dims, const float *, const float *, float *, cudaStream_t, Split,
+                                           const float *);
 
 // Tiles of 32 x 8 columns; z-chunks sized so that the grid has about 4 CTAs per SM.
 template <typename T>
@@ -2467,9 +2504,7 @@ cudaError_t launch_count_live(Dims d, const double *dinv, double *partials, doub
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_count_live<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), dinv, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_NLIVE, -1);
+    k_count_live<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), dinv, partials, dscal);
     return cudaGetLastError();
 }
 
@@ -2478,13 +2513,9 @@ cudaError_t launch_rhs_prepare(Dims d, const double *rhs, const double *dinv, do
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_sum_live<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), rhs, dinv, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_SUM_B, -1);
+    k_sum_live<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), rhs, dinv, partials, dscal);
     note_launch();
     k_rhs_center<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), rhs, dinv, b0, dscal, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_NB2, -1);
     return cudaGetLastError();
 }
 
@@ -2493,9 +2524,7 @@ cudaError_t launch_resid_norm(Dims d, double ih2, const LevelArrays<double> &L, 
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_resid_norm<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
+    k_resid_norm<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, partials, dscal);
     return cudaGetLastError();
 }
 
@@ -2517,11 +2546,8 @@ cudaError_t launch_resid_cast(Dims d, double ih2, const LevelArrays<double> &L, 
         k_scale_from_nb2<<<1, 1, 0, s>>>(dscal, scale_in);
     }
     note_launch();
-    k_resid_cast<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r32, dscal, scale_in, partials, sp.half);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
-    note_launch();
-    k_set_scale<<<1, 1, 0, s>>>(dscal, scale_out);
+    k_resid_cast<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r32, dscal, scale_in, scale_out, partials,
+                                           sp.half);
     return cudaGetLastError();
 }
 
@@ -2691,8 +2717,6 @@ cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, c
     const unsigned g = red_grid(d.n());
     note_launch();
     k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials, sp.half);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, S_SUM_P);
     return cudaGetLastError();
 }
 
@@ -2703,8 +2727,6 @@ cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, 
     const unsigned g = red_grid(n);
     note_launch();
     k_pcg_dots<Z><<<g, kRedThreads, 0, s>>>((unsigned)n, r, z, zo, dscal, sz_slot, so_slot, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RZN, S_RZO);
     return cudaGetLastError();
 }
 cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const float *zo, double *partials,
@@ -2713,8 +2735,6 @@ cudaError_t launch_pcg_dots32(size_t n, const float *r32, const float *z, const 
     const unsigned g = red_grid(n);
     note_launch();
     k_pcg_dots32<<<g, kRedThreads, 0, s>>>((unsigned)n, r32, z, zo, dscal, sr_slot, sz_slot, so_slot, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RZN, S_RZO);
     return cudaGetLastError();
 }
 template cudaError_t launch_pcg_dots<double>(size_t, const double *, const double *, const double *, double *,
@@ -2724,29 +2744,25 @@ template cudaError_t launch_pcg_dots<float>(size_t, const double *, const float 
 
 template <typename Z>
 cudaError_t launch_pcg_dir(size_t n, const Z *z, double *d, double *dscal, int sz_slot, int so_slot, int first,
-                           cudaStream_t s, Split sp)
+                           cudaStream_t s, Split sp, double *partials)
 {
     if (sp.half && sizeof(Z) != 4) return cudaErrorInvalidValue;  // FP64 fields are never split
     if (so_slot >= 0 && sz_slot < 0) return cudaErrorInvalidValue;
     note_launch();
-    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, so_slot, first, sp);
-    note_launch();
-    k_pcg_shift_rz<<<1, 1, 0, s>>>(dscal);
+    k_pcg_dir<Z><<<red_grid(n), kRedThreads, 0, s>>>((unsigned)n, z, d, dscal, sz_slot, so_slot, first, sp, partials);
     return cudaGetLastError();
 }
 template cudaError_t launch_pcg_dir<double>(size_t, const double *, double *, double *, int, int, int, cudaStream_t,
-                                            Split);
+                                            Split, double *);
 template cudaError_t launch_pcg_dir<float>(size_t, const float *, double *, double *, int, int, int, cudaStream_t,
-                                           Split);
+                                           Split, double *);
 
 cudaError_t launch_pcg_apply(Dims d, const LevelArrays<double> &op, const double *dv, double *q, double *partials,
                              double *dscal, cudaStream_t s)
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_pcg_apply<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, op, op.dinv, dv, q, partials);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_SIGMA, -1);
+    k_pcg_apply<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, op, op.dinv, dv, q, partials, dscal);
     return cudaGetLastError();
 }
 
@@ -2757,8 +2773,6 @@ cudaError_t launch_pcg_update(size_t n, const double *dv, const double *q, doubl
     if (sd_slot >= 0 && sd_slot == scale_slot) return cudaErrorInvalidValue;  // read and written by the kernel
     note_launch();
     k_pcg_update<<<g, kRedThreads, 0, s>>>((unsigned)n, dv, q, p, r, r32, dscal, scale_slot, sd_slot, partials, sp);
-    note_launch();
-    k_finish2<<<1, kRedThreads, 0, s>>>(partials, (int)g, dscal, S_RR, -1);
     return cudaGetLastError();
 }
 
