@@ -715,11 +715,12 @@ def rk2_bench(args):
     ms = e0.elapsed_time(e1)
     # the momentum right-hand side alone (mg_momentum_rhs on u^k, phi^k): CUDA events over 10 calls
     R = tuple(torch.empty_like(x) for x in u0)
+    work = torch.empty(12 * phi.numel(), dtype=torch.float64, device="cuda")
     for _ in range(2):
-        mgproj.momentum_rhs(phi, beta, u0, case.h, forces, out=R)
+        mgproj.momentum_rhs(phi, beta, u0, case.h, forces, out=R, work=work)
     e0.record()
     for _ in range(10):
-        mgproj.momentum_rhs(phi, beta, u0, case.h, forces, out=R)
+        mgproj.momentum_rhs(phi, beta, u0, case.h, forces, out=R, work=work)
     e1.record()
     torch.cuda.synchronize()
     mom_ms = e0.elapsed_time(e1) / 10

@@ -280,18 +280,20 @@ typedef struct {
  * and of the two i-faces that meet there; 2 mu S_ii at cell centres (mu of the
  * cell), 2 mu S_ij at edges (mu the mean of the four cells around the edge);
  * each divergence the difference of the two values that bracket the face,
- * over h.  Walls are free-slip: normal velocity 0 (the stored wall face, or
+ * over h; the edge viscosity sums its four cells in the order of their index.  Walls are free-slip: normal velocity 0 (the stored wall face, or
  * the unstored high wall), the tangential velocity mirrored into the ghost
  * row, so no momentum flux and no shear cross a wall.  Faces with beta = 0
  * (walls, faces at a solid) get R = 0 and enter the stencils of their
  * neighbours with their stored velocity.  phi: device, nx*ny*nz; beta: device
  * face arrays, 1/rho on open faces and 0 on closed ones (mg_face_coeffs); u:
  * device face velocities; R: device face arrays, written (must not alias the
- * inputs); f: host.  Returns MG_OK, MG_ERR_ARG (bad grid, null, aliased or
- * unaligned array, forces not finite) or MG_ERR_CUDA.
+ * inputs); work: device scratch of 12*nx*ny*nz doubles (the fluxes and stresses
+ * each cell shares with its faces, computed once per cell), overwritten; f:
+ * host.  Returns MG_OK, MG_ERR_ARG (bad grid, null, aliased or unaligned array,
+ * forces not finite) or MG_ERR_CUDA.
  */
 int mg_momentum_rhs(const mg_grid *g, const double *phi, const double *const beta[3], const double *const u[3],
-                    const mg_forces *f, double *const R[3], void *stream);
+                    const mg_forces *f, double *const R[3], double *work, void *stream);
 
 /*
  * One step of the second-order Runge-Kutta time integration (Numerical Time

@@ -933,7 +933,8 @@ void orc_phi_grad(int nx, int ny, int nz, double lam, const double *bx, const do
 /*     u_j u_i (j != i) at the cell edges from the mean of the two j-faces    */
 /*     and the mean of the two i-faces that meet there;                       */
 /*   - 2 mu S_ii at cell centres (mu of the cell), 2 mu S_ij at the edges     */
-/*     (mu = mean of the four cells around the edge);                          */
+/*     (mu = mean of the four cells around the edge, summed in cell-index     */
+/*     order);                                                                */
 /*   - each divergence the difference of the two values that bracket the     */
 /*     face, over h.                                                          */
 /* Walls are free-slip: normal velocity 0 (the stored wall face, or the high  */
@@ -1021,7 +1022,11 @@ void orc_momentum_rhs(int nx, int ny, int nz, double h, const double *phi, doubl
                             const double m10 = cmu(phi, mu_air, dmu, si - eb[0], sj - eb[1], sk - eb[2], nx, ny, nz);
                             const double m01 = cmu(phi, mu_air, dmu, si - ea[0], sj - ea[1], sk - ea[2], nx, ny, nz);
                             const double m11 = cmu(phi, mu_air, dmu, si, sj, sk, nx, ny, nz);
-                            const double me = 0.25 * (((m00 + m10) + m01) + m11);
+                            /* the four cells summed in the order of their cell index (the lower
+                               of the two axes varies fastest), the same for all four faces that
+                               share the edge */
+                            const double me = a < b ? 0.25 * (((m00 + m10) + m01) + m11)
+                                                    : 0.25 * (((m00 + m01) + m10) + m11);
                             tl[side] = me * ((ua1 - ua0) * ih + (ub1 - ub0) * ih);
                         }
                         conv = conv + (fl[1] - fl[0]) * ih;

@@ -86,6 +86,7 @@ struct mg_ctx {
     // the time step's scratch (mg_rk2_step): face coefficients of the two stages, u~, u*, phi*
     LevelArrays<double> rk_b1, rk_b2, rk_ut, rk_us, rk_r;
     double *rk_phis = nullptr;
+    double *rk_work = nullptr;  // the momentum terms' per-cell fluxes and stresses
     float *urow0 = nullptr;  // uniform-row values of the finest FP32 level (with split0)
     // banded-row records of the finest FP32 level (with split0 and nx % 8 == 0), the two row
     // counts of the last hierarchy build, and whether its sweeps use the records (more banded
@@ -1243,15 +1244,15 @@ int mg_stretched_metrics(const mg_grid *g, const double *hx, const double *hy, c
 }
 
 int mg_momentum_rhs(const mg_grid *g, const double *phi, const double *const beta[3], const double *const u[3],
-                    const mg_forces *f, double *const R[3], void *stream)
+                    const mg_forces *f, double *const R[3], double *work, void *stream)
 {
     g_err.clear();
     if (!grid_ok(g)) return fail(MG_ERR_ARG, "mg_momentum_rhs: bad grid");
-    if (!phi || !beta || !u || !f || !R) return fail(MG_ERR_ARG, "mg_momentum_rhs: null argument");
+    if (!phi || !beta || !u || !f || !R || !work) return fail(MG_ERR_ARG, "mg_momentum_rhs: null argument");
     for (int a = 0; a < 3; a++)
         if (!beta[a] || !u[a] || !R[a]) return fail(MG_ERR_ARG, "mg_momentum_rhs: null face array");
     if (!forces_ok(f)) return fail(MG_ERR_ARG, "mg_momentum_rhs: forces not finite or viscosities not >= 0");
-    if (!aligned16({phi, beta[0], beta[1], beta[2], u[0], u[1], u[2], R[0], R[1], R[2]}))
+    if (!aligned16({phi, beta[0], beta[1], beta[2], u[0], u[1], u[2], R[0], R[1], R[2], work}))
         return fail(MG_ERR_ARG, "mg_momentum_rhs: arrays must be 16-byte aligned");
     for (int a = 0; a < 3; a++)
         for (int b = 0; b < 3; b++)
@@ -1268,7 +1269,7 @@ int mg_momentum_rhs(const mg_grid *g, const double *phi, const double *const bet
     RR.by = R[1];
     RR.bz = R[2];
     CK(mg::launch_momentum_rhs(Dims{g->nx, g->ny, g->nz}, g->h, phi, f->mu_air, f->mu_water, f->inv_re, f->g,
-                               f->convection, B, U, RR, (cudaStream_t)stream));
+                               f->convection, B, U, RR, work, (cudaStream_t)stream));
     return MG_OK;
 }
 
@@ -1294,6 +1295,7 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
             CKS(c->alloc(&L->bz, n));
         }
         CKS(c->alloc(&c->rk_phis, n));
+        CKS(c->alloc(&c->rk_work, mg::kMomWork * n));
     }
     LevelArrays<double> uk{};
     uk.bx = u[0];
@@ -1314,7 +1316,7 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
     }
     // R(u^k, phi^k) with the first stage's 1/rho
     CK(mg::launch_momentum_rhs(d, c->g.h, phi, forces->mu_air, forces->mu_water, forces->inv_re, forces->g,
-                               forces->convection, c->rk_b1, uk, c->rk_r, s));
+                               forces->convection, c->rk_b1, uk, c->rk_r, c->rk_work, s));
     CK(mg::launch_rk_combine(n, uk, none, c->rk_r, dt, c->rk_ut, s));
     CK(cudaMemsetAsync(p_out, 0, n * sizeof(double), s));
     {
@@ -1335,7 +1337,7 @@ int mg_rk2_step(mg_ctx *c, const double *phi, const uint8_t *solid_mask, double 
     }
     // R(u*, phi*) with the second stage's 1/rho
     CK(mg::launch_momentum_rhs(d, c->g.h, c->rk_phis, forces->mu_air, forces->mu_water, forces->inv_re, forces->g,
-                               forces->convection, c->rk_b2, c->rk_us, c->rk_r, s));
+                               forces->convection, c->rk_b2, c->rk_us, c->rk_r, c->rk_work, s));
     CK(mg::launch_rk_combine(n, c->rk_us, uk, c->rk_r, dt, c->rk_ut, s));
     // (u* + u^k) / 2 for the second VOF, kept in u* (u^k is overwritten below)
     CK(mg::launch_half(n, c->rk_us, uk, c->rk_us, s));

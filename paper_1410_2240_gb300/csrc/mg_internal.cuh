@@ -247,10 +247,11 @@ cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const Leve
                               const LevelArrays<double> &r, double dt, const LevelArrays<double> &out, cudaStream_t s);
 // R = the momentum right-hand side of Eq. navi on the faces (convective if convect, viscous with
 // mu = mu_air + (mu_water - mu_air) phi scaled by inv_re and beta = 1/rho, -g on the z-faces),
-// 0 on closed faces (beta == 0)
+// 0 on closed faces (beta == 0); work: 12 nx*ny*nz doubles (the per-cell fluxes and stresses)
+constexpr int kMomWork = 12;
 cudaError_t launch_momentum_rhs(Dims d, double h, const double *phi, double mu_air, double mu_water, double inv_re,
                                 double g, int convect, const LevelArrays<double> &beta, const LevelArrays<double> &u,
-                                const LevelArrays<double> &r, cudaStream_t s);
+                                const LevelArrays<double> &r, double *work, cudaStream_t s);
 cudaError_t launch_half(size_t n, const LevelArrays<double> &a, const LevelArrays<double> &b,
                         const LevelArrays<double> &out, cudaStream_t s);
 cudaError_t launch_vof_upwind(Dims d, double s_dt_h, const LevelArrays<double> &mask, const LevelArrays<double> &u,

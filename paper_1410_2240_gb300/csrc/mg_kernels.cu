@@ -1464,16 +1464,25 @@ __global__ void k_rk_combine(size_t n, LevelArrays<double> a, LevelArrays<double
 // Eq. density and 1/rho_f the face coefficient.  Second-order central conservative MAC form:
 // u_i u_i at the cell centres (mean of the cell's two i-faces), u_j u_i at the edges (means of
 // the two j-faces and of the two i-faces meeting there), 2 mu S_ii at the centres, 2 mu S_ij at
-// the edges (mu: mean of the four cells around the edge), each divergence the difference of the
-// two values bracketing the face over h.  Free-slip walls: normal velocity 0 (the stored wall
-// face, or the unstored high wall), tangential velocity mirrored into the ghost row; closed faces
-// get R = 0.  Separately rounded operations in a fixed order (bit-reproducible).
+// the edges (mu: mean of the four cells around the edge, in cell-index order), each divergence
+// the difference of the two values bracketing the face over h.  Free-slip walls: normal velocity
+// 0 (the stored wall face, or the unstored high wall), tangential velocity mirrored into the
+// ghost row; closed faces get R = 0.  Separately rounded operations in a fixed order.
+//
+// Two passes.  k_mom_parts computes, once per cell, the quantities every face shares: for each
+// axis a the centre flux C_a = U_a^2 (U_a the cell's mean a-velocity) and stress T_a = 2 mu
+// dU_a/dx_a, and for each plane (a, b), a < b, at the cell's low edge the flux F_ab = (mean u_b)
+// (mean u_a) and the shear S_ab = mu_edge (du_a/dx_b + du_b/dx_a).  k_mom_combine forms each
+// open face's R from the values bracketing it.  A face's F_ab and S_ab are the same numbers
+// whichever of the four faces at the edge uses them (the product and the sum commute exactly), so
+// R is bitwise the per-face evaluation, with a third of its FP64 operations.
 // ---------------------------------------------------------------------------
 struct MomArgs {
     int nx, ny, nz, convect;
     double ih, mu_air, dmu, inv_re, g;
     const double *phi;
     LevelArrays<double> beta, u, r;
+    double *w;  // 12 arrays of n: C_x, C_y, C_z, T_x, T_y, T_z, F_xy, F_xz, F_yz, S_xy, S_xz, S_yz
 };
 
 __device__ __forceinline__ int clamp_idx(int v, int hi) { return v < 0 ? 0 : (v > hi ? hi : v); }
@@ -1499,54 +1508,106 @@ __device__ __forceinline__ double mom_mu(const MomArgs &m, int i, int j, int k)
     return __dadd_rn(m.mu_air, __dmul_rn(m.dmu, m.phi[((size_t)k * m.ny + j) * m.nx + i]));
 }
 
+// centre flux and stress of axis A at cell (i, j, k) (mu: the cell's viscosity)
+template <int A>
+__device__ __forceinline__ void mom_centre(const MomArgs &m, int i, int j, int k, double mu, double &C, double &T)
+{
+    constexpr int ai = A == 0, aj = A == 1, ak = A == 2;
+    const double u0 = mom_vel<A>(m, i, j, k), u1 = mom_vel<A>(m, i + ai, j + aj, k + ak);
+    const double U = __dmul_rn(0.5, __dadd_rn(u0, u1));
+    C = __dmul_rn(U, U);
+    T = __dmul_rn(__dmul_rn(2.0, mu), __dmul_rn(__dsub_rn(u1, u0), m.ih));
+}
+
+// flux and shear of plane (A, B), A < B, at the low edge of cell (i, j, k); mc, ma, mb, mab: the
+// viscosities of the cell and of its neighbours below along A, along B, along both
 template <int A, int B>
-__device__ __forceinline__ void mom_tangential(const MomArgs &m, int i, int j, int k, double &conv, double &visc)
+__device__ __forceinline__ void mom_edge(const MomArgs &m, int i, int j, int k, double mc, double ma, double mb,
+                                         double mab, double &F, double &S)
 {
     constexpr int ai = A == 0, aj = A == 1, ak = A == 2, bi = B == 0, bj = B == 1, bk = B == 2;
-    double fl[2], tl[2];
-#pragma unroll
-    for (int side = 0; side < 2; side++) {
-        const int si = i + side * bi, sj = j + side * bj, sk = k + side * bk;
-        const double ua0 = mom_vel<A>(m, si - bi, sj - bj, sk - bk);
-        const double ua1 = mom_vel<A>(m, si, sj, sk);
-        const double ub0 = mom_vel<B>(m, si - ai, sj - aj, sk - ak);
-        const double ub1 = mom_vel<B>(m, si, sj, sk);
-        const double vb = __dmul_rn(0.5, __dadd_rn(ub0, ub1)), va = __dmul_rn(0.5, __dadd_rn(ua0, ua1));
-        fl[side] = __dmul_rn(vb, va);
-        const double m00 = mom_mu(m, si - ai - bi, sj - aj - bj, sk - ak - bk);
-        const double m10 = mom_mu(m, si - bi, sj - bj, sk - bk);
-        const double m01 = mom_mu(m, si - ai, sj - aj, sk - ak);
-        const double m11 = mom_mu(m, si, sj, sk);
-        const double me = __dmul_rn(0.25, __dadd_rn(__dadd_rn(__dadd_rn(m00, m10), m01), m11));
-        tl[side] = __dmul_rn(me, __dadd_rn(__dmul_rn(__dsub_rn(ua1, ua0), m.ih), __dmul_rn(__dsub_rn(ub1, ub0), m.ih)));
+    const double ua0 = mom_vel<A>(m, i - bi, j - bj, k - bk), ua1 = mom_vel<A>(m, i, j, k);
+    const double ub0 = mom_vel<B>(m, i - ai, j - aj, k - ak), ub1 = mom_vel<B>(m, i, j, k);
+    F = __dmul_rn(__dmul_rn(0.5, __dadd_rn(ub0, ub1)), __dmul_rn(0.5, __dadd_rn(ua0, ua1)));
+    const double me = __dmul_rn(0.25, __dadd_rn(__dadd_rn(__dadd_rn(mab, mb), ma), mc));
+    S = __dmul_rn(me, __dadd_rn(__dmul_rn(__dsub_rn(ua1, ua0), m.ih), __dmul_rn(__dsub_rn(ub1, ub0), m.ih)));
+}
+
+__global__ void k_mom_parts(MomArgs m)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (i >= m.nx || j >= m.ny) return;
+    const size_t n = (size_t)m.nx * m.ny * m.nz, c = ((size_t)k * m.ny + j) * m.nx + i;
+    if (!MG_CK(c, c, (long long)n, CK_MOMENTUM)) return;
+    const double mc = mom_mu(m, i, j, k), mx = mom_mu(m, i - 1, j, k), my = mom_mu(m, i, j - 1, k),
+                 mz = mom_mu(m, i, j, k - 1), mxy = mom_mu(m, i - 1, j - 1, k), mxz = mom_mu(m, i - 1, j, k - 1),
+                 myz = mom_mu(m, i, j - 1, k - 1);
+    double C, T, F, S;
+    mom_centre<0>(m, i, j, k, mc, C, T);
+    m.w[c] = C;
+    m.w[3 * n + c] = T;
+    mom_centre<1>(m, i, j, k, mc, C, T);
+    m.w[n + c] = C;
+    m.w[4 * n + c] = T;
+    mom_centre<2>(m, i, j, k, mc, C, T);
+    m.w[2 * n + c] = C;
+    m.w[5 * n + c] = T;
+    // in cell-index order: the cell below along both axes, below along the higher axis, below along
+    // the lower axis, the cell itself
+    mom_edge<0, 1>(m, i, j, k, mc, mx, my, mxy, F, S);
+    m.w[6 * n + c] = F;
+    m.w[9 * n + c] = S;
+    mom_edge<0, 2>(m, i, j, k, mc, mx, mz, mxz, F, S);
+    m.w[7 * n + c] = F;
+    m.w[10 * n + c] = S;
+    mom_edge<1, 2>(m, i, j, k, mc, my, mz, myz, F, S);
+    m.w[8 * n + c] = F;
+    m.w[11 * n + c] = S;
+}
+
+// edge value of plane (A, B) (either order) at the low edge of cell (i, j, k), which may lie on the
+// high wall of the other axis (one past the last cell): there the normal velocity of the wall and
+// the mirrored tangential velocity make both the flux and the shear zero
+template <int A, int B>
+__device__ __forceinline__ void mom_edge_at(const MomArgs &m, size_t n, int i, int j, int k, double &F, double &S)
+{
+    constexpr int lo = A < B ? A : B, hi = A < B ? B : A;
+    constexpr int slot = (lo == 0 && hi == 1) ? 0 : ((lo == 0) ? 1 : 2);
+    if (i >= m.nx || j >= m.ny || k >= m.nz) {
+        F = 0.0;
+        S = 0.0;
+        return;
     }
-    conv = __dadd_rn(conv, __dmul_rn(__dsub_rn(fl[1], fl[0]), m.ih));
-    visc = __dadd_rn(visc, __dsub_rn(tl[1], tl[0]));
+    const size_t c = ((size_t)k * m.ny + j) * m.nx + i;
+    F = m.w[(6 + slot) * n + c];
+    S = m.w[(9 + slot) * n + c];
 }
 
 template <int A>
-__device__ __forceinline__ double mom_face(const MomArgs &m, int i, int j, int k, double beta)
+__device__ __forceinline__ double mom_face(const MomArgs &m, size_t n, int i, int j, int k, size_t c, double beta)
 {
     constexpr int ai = A == 0, aj = A == 1, ak = A == 2;
-    const double um = mom_vel<A>(m, i - ai, j - aj, k - ak);
-    const double u0 = mom_vel<A>(m, i, j, k);
-    const double up = mom_vel<A>(m, i + ai, j + aj, k + ak);
-    const double cm = __dmul_rn(0.5, __dadd_rn(um, u0)), cp = __dmul_rn(0.5, __dadd_rn(u0, up));
-    double conv = __dmul_rn(__dsub_rn(__dmul_rn(cp, cp), __dmul_rn(cm, cm)), m.ih);
-    const double mum = mom_mu(m, i - ai, j - aj, k - ak);
-    const double mup = mom_mu(m, i, j, k);
-    const double tp = __dmul_rn(__dmul_rn(2.0, mup), __dmul_rn(__dsub_rn(up, u0), m.ih));
-    const double tm = __dmul_rn(__dmul_rn(2.0, mum), __dmul_rn(__dsub_rn(u0, um), m.ih));
-    double visc = __dsub_rn(tp, tm);
+    const size_t cm = c - (ai ? 1 : (aj ? (size_t)m.nx : (size_t)m.nx * m.ny));
+    double conv = __dmul_rn(__dsub_rn(m.w[A * n + c], m.w[A * n + cm]), m.ih);
+    double visc = __dsub_rn(m.w[(3 + A) * n + c], m.w[(3 + A) * n + cm]);
+    auto tangential = [&](auto bcon) {
+        constexpr int B = decltype(bcon)::value;
+        constexpr int bi = B == 0, bj = B == 1, bk = B == 2;
+        double F0, S0, F1, S1;
+        mom_edge_at<A, B>(m, n, i, j, k, F0, S0);
+        mom_edge_at<A, B>(m, n, i + bi, j + bj, k + bk, F1, S1);
+        conv = __dadd_rn(conv, __dmul_rn(__dsub_rn(F1, F0), m.ih));
+        visc = __dadd_rn(visc, __dsub_rn(S1, S0));
+    };
     if (A == 0) {
-        mom_tangential<0, 1>(m, i, j, k, conv, visc);
-        mom_tangential<0, 2>(m, i, j, k, conv, visc);
+        tangential(std::integral_constant<int, 1>());
+        tangential(std::integral_constant<int, 2>());
     } else if (A == 1) {
-        mom_tangential<1, 0>(m, i, j, k, conv, visc);
-        mom_tangential<1, 2>(m, i, j, k, conv, visc);
+        tangential(std::integral_constant<int, 0>());
+        tangential(std::integral_constant<int, 2>());
     } else {
-        mom_tangential<2, 0>(m, i, j, k, conv, visc);
-        mom_tangential<2, 1>(m, i, j, k, conv, visc);
+        tangential(std::integral_constant<int, 0>());
+        tangential(std::integral_constant<int, 1>());
     }
     double r = m.convect ? -conv : 0.0;
     r = __dadd_rn(r, __dmul_rn(__dmul_rn(m.inv_re, beta), __dmul_rn(visc, m.ih)));
@@ -1555,16 +1616,17 @@ __device__ __forceinline__ double mom_face(const MomArgs &m, int i, int j, int k
 }
 
 // one thread per cell: R on its three low faces
-__global__ void k_momentum_rhs(MomArgs m)
+__global__ void k_mom_combine(MomArgs m)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= m.nx) return;
-    const size_t c = ((size_t)k * m.ny + j) * m.nx + i;
-    if (!MG_CK(c, c, (long long)m.nx * m.ny * m.nz, CK_MOMENTUM)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (i >= m.nx || j >= m.ny) return;
+    const size_t n = (size_t)m.nx * m.ny * m.nz, c = ((size_t)k * m.ny + j) * m.nx + i;
+    if (!MG_CK(c, c, (long long)n, CK_MOMENTUM)) return;
     const double bx = m.beta.bx[c], by = m.beta.by[c], bz = m.beta.bz[c];
-    m.r.bx[c] = pos_bits(bx) ? mom_face<0>(m, i, j, k, bx) : 0.0;
-    m.r.by[c] = pos_bits(by) ? mom_face<1>(m, i, j, k, by) : 0.0;
-    m.r.bz[c] = pos_bits(bz) ? mom_face<2>(m, i, j, k, bz) : 0.0;
+    // an open face is interior (its low neighbour exists), so c - e_a is a cell
+    m.r.bx[c] = (i > 0 && pos_bits(bx)) ? mom_face<0>(m, n, i, j, k, c, bx) : 0.0;
+    m.r.by[c] = (j > 0 && pos_bits(by)) ? mom_face<1>(m, n, i, j, k, c, by) : 0.0;
+    m.r.bz[c] = (k > 0 && pos_bits(bz)) ? mom_face<2>(m, n, i, j, k, c, bz) : 0.0;
 }
 
 // out = 0.5 (a + b)   (b null: 0.5 a)
@@ -2623,7 +2685,7 @@ cudaError_t launch_rk_combine(size_t n, const LevelArrays<double> &a, const Leve
 
 cudaError_t launch_momentum_rhs(Dims d, double h, const double *phi, double mu_air, double mu_water, double inv_re,
                                 double g, int convect, const LevelArrays<double> &beta, const LevelArrays<double> &u,
-                                const LevelArrays<double> &r, cudaStream_t s)
+                                const LevelArrays<double> &r, double *work, cudaStream_t s)
 {
     MomArgs m;
     m.nx = d.nx;
@@ -2639,8 +2701,12 @@ cudaError_t launch_momentum_rhs(Dims d, double h, const double *phi, double mu_a
     m.beta = beta;
     m.u = u;
     m.r = r;
+    m.w = work;
+    const dim3 g2 = row_grid2(d.nx, d.ny, d.nz), blk = row_block2(d.nx);
     note_launch();
-    k_momentum_rhs<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(m);
+    k_mom_parts<<<g2, blk, 0, s>>>(m);
+    note_launch();
+    k_mom_combine<<<g2, blk, 0, s>>>(m);
     return cudaGetLastError();
 }
 

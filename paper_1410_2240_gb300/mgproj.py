@@ -94,7 +94,7 @@ _lib.mg_set_face_areas.argtypes = [_vp, _PP]
 _lib.mg_set_body_velocity.argtypes = [_vp, _PP]
 _lib.mg_rk2_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Forces),
                               ctypes.c_double, _PP, _vp, _vp, ctypes.c_double, ctypes.POINTER(Stats)]
-_lib.mg_momentum_rhs.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _PP, ctypes.POINTER(Forces), _PP, _vp]
+_lib.mg_momentum_rhs.argtypes = [ctypes.POINTER(Grid), _vp, _PP, _PP, ctypes.POINTER(Forces), _PP, _vp, _vp]
 _lib.mg_stretched_metrics.argtypes = [ctypes.POINTER(Grid), _vp, _vp, _vp, _PP, _PP, _PP, _PP, _vp]
 _lib.mg_kernel_launches.restype = ctypes.c_uint64
 _lib.mg_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -231,16 +231,20 @@ def stretched_metrics(hx: torch.Tensor, hy: torch.Tensor, hz: torch.Tensor, beta
 
 
 def momentum_rhs(phi: torch.Tensor, beta: Sequence[torch.Tensor], u: Sequence[torch.Tensor], h: float,
-                 f: Forces, out=None, stream=None):
+                 f: Forces, out=None, work=None, stream=None):
     """mg_momentum_rhs: R_i of Eq. navi without the pressure (body force, viscous, convective) on
-    the faces; beta = 1/rho on open faces (face_coeffs), 0 on closed ones."""
+    the faces; beta = 1/rho on open faces (face_coeffs), 0 on closed ones.  work: scratch of
+    12 * phi.numel() doubles (allocated when None)."""
     shape = phi.shape
     nz, ny, nx = shape
     g = Grid(nx, ny, nz, h)
     if out is None:
         out = tuple(torch.empty_like(phi) for _ in range(3))
+    if work is None:
+        work = torch.empty(12 * phi.numel(), dtype=torch.float64, device=phi.device)
     _check(_lib.mg_momentum_rhs(ctypes.byref(g), _dev(phi, shape, name="phi"), _faces(beta, shape, "beta"),
-                                _faces(u, shape, "u"), ctypes.byref(f), _faces(out, shape, "R"), _stream(stream)))
+                                _faces(u, shape, "u"), ctypes.byref(f), _faces(out, shape, "R"),
+                                _dev(work, (12 * phi.numel(),), name="work"), _stream(stream)))
     return out
 
 

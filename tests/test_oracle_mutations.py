@@ -87,8 +87,8 @@ MUTANTS = [
      "#define UPW(u, lo, hi) ((u) > 0.0 ? (u) * phi[hi] : (u) * phi[lo])", [T5.test_vof_upwind_hand_example]),
     ("normal viscous stress without its factor 2", "const double tp = 2.0 * mup * ((up - u0) * ih);",
      "const double tp = mup * ((up - u0) * ih);", [lambda: T6.test_viscous_term_exact_for_quadratic_velocity(False)]),
-    ("edge viscosity from two cells", "const double me = 0.25 * (((m00 + m10) + m01) + m11);",
-     "const double me = 0.5 * (m01 + m11);", [lambda: T6.test_viscous_term_exact_for_quadratic_velocity(True)]),
+    ("edge viscosity from two cells", "a < b ? 0.25 * (((m00 + m10) + m01) + m11)", "a < b ? 0.5 * (m01 + m11)",
+     [lambda: T6.test_viscous_term_exact_for_quadratic_velocity(True)]),
     ("normal momentum flux sign", "conv = (cp * cp - cm * cm) * ih;", "conv = (cp * cp + cm * cm) * ih;",
      [T6.test_convective_term_exact_for_linear_velocity]),
     ("shear takes the wrong tangential face", "const double ub0 = fvel(U[b], b, si - ea[0], sj - ea[1], sk - ea[2], nx, ny, nz);",
