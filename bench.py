@@ -57,12 +57,12 @@ def iteration_bytes(inner, vcycle_bytes, krylov, resid_bytes):
     """Algorithmic bytes per finest cell of one outer iteration: `inner` V-cycles plus the CG vector
     work (krylov) or the refinement step's residual and accumulation."""
     return inner * vcycle_bytes + (B_CG_ITER if krylov else resid_bytes)
-SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
-                1: "k_smooth_split4 x2 colour passes, colour-split p and b, uniform-row faces",
+SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p, b and faces, uniform-row records",
+                1: "k_smooth_split4 x2 colour passes, colour-split p, b and faces, uniform-row records",
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
 # DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split4 colour
 # passes) from an ncu capture of this workload
-SWEEP_TRAFFIC_256 = 119.533568e6 + 18.985728e6 + 119.533312e6 + 18.476544e6
+SWEEP_TRAFFIC_256 = 118.514176e6 + 18.064384e6 + 118.515200e6 + 18.266112e6
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))
 

@@ -93,6 +93,9 @@ struct mg_ctx {
     // rows than uniform ones: a stretched grid)
     float4 *arow0 = nullptr;
     unsigned *rowcnt = nullptr;
+    // the finest FP32 face arrays in the colour-split layout (with split0 and nx % 8 == 0), read
+    // by the colour passes on rows without a record
+    LevelArrays<float> sf0;
     bool banded = false;
     // connected regions of the live fine cells: their number; for more than one, each live cell's
     // region number (cc_label, the union-find labels otherwise), the cells per region (device
@@ -467,8 +470,9 @@ int vcycle(mg_ctx *c, const std::vector<LevelArrays<T>> &L, int l, const T *b, T
         } else if (sp.half) {
             if constexpr (std::is_same<T, float>::value) {
                 const int r0 = alternate ? (npass + 1) & 1 : 0;
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow, r0, zpass));
-                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow, arow, r0 ^ (alternate ? 1 : 0)));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first, s, urow, arow, r0, zpass, &c->sf0));
+                CK(mg::launch_smooth_split(d, h2, L[l], b, cur, first ^ 1, s, urow, arow, r0 ^ (alternate ? 1 : 0),
+                                           false, &c->sf0));
                 npass += 2;
             }
         } else {
@@ -800,6 +804,11 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
                                           nullptr, 1.0f));
         }
         if (c->rowcnt) CK(cudaMemsetAsync(c->rowcnt, 0, 2 * sizeof(unsigned), s));
+        if (c->sf0.bx) {  // the same FP32 values (narrow of the FP64 face) in the colour-split layout
+            CK(mg::launch_to_f32_layout(c->dims[0].n(), c->L64[0].bx, c->sf0.bx, s, c->split0));
+            CK(mg::launch_to_f32_layout(c->dims[0].n(), c->L64[0].by, c->sf0.by, s, c->split0));
+            CK(mg::launch_to_f32_layout(c->dims[0].n(), c->L64[0].bz, c->sf0.bz, s, c->split0));
+        }
         if (c->urow0)
             CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s, c->arow0,
                                        c->rowcnt));
@@ -1081,6 +1090,9 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
         if (st == MG_OK && c->split0.half && c->dims[0].nx % 8 == 0) {
             st = c->alloc(&c->arow0, (size_t)c->dims[0].ny * c->dims[0].nz);
             if (st == MG_OK) st = c->alloc(&c->rowcnt, 2);
+            if (st == MG_OK) st = c->alloc(&c->sf0.bx, c->dims[0].n());
+            if (st == MG_OK) st = c->alloc(&c->sf0.by, c->dims[0].n());
+            if (st == MG_OK) st = c->alloc(&c->sf0.bz, c->dims[0].n());
         }
         if (st != MG_OK) return bail(st);
     }

@@ -125,11 +125,13 @@ cudaError_t launch_smooth(Dims d, T h2, const LevelArrays<T> &L, const T *b, T *
                           int z0 = 0, int z1 = -1, bool zero = false);
 // one colour of a red-black sweep on the colour-split layout (FP32, all dims even); urow (optional):
 // the level's uniform-row values, arow (optional, nx % 8 == 0, replaces urow in the sweep): its
-// banded-row records (launch_uniform_rows); rev: blocks take the planes in descending order
+// banded-row records (launch_uniform_rows); rev: blocks take the planes in descending order; S
+// (required where nx % 8 == 0): the face arrays of L in the colour-split layout
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
                                 cudaStream_t s, const float *urow = nullptr, const float4 *arow = nullptr,
-                                int rev = 0, bool zero = false);
-// urow[k*ny + j] = v if every face around row (j,k) but its two x-walls equals v, else 0; arow
+                                int rev = 0, bool zero = false, const LevelArrays<float> *S = nullptr);
+// urow[k*ny + j] = v if row (j,k) is interior (0 < j < ny-1, 0 < k < nz-1) and every face around
+// it but its two x-walls equals v, else 0; arow
 // (optional) = {vx, vy, vzl, vzh} if the row's x-, y-, low z- and high z-faces hold one value
 // each, else zeros; count (optional, two counters, incremented): uniform rows, banded rows that
 // are not uniform

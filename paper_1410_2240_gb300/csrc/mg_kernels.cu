@@ -443,8 +443,8 @@ __device__ __forceinline__ int row_parity(unsigned c, const Split &sp)
 }
 
 // Uniform rows.  Away from the interface and the body, every face coefficient around an x-row of
-// cells holds one value (pure air or pure water).  urow[k*ny + j] = that value v when every face
-// of every cell of row (j,k) except the two x-walls (bx at i = 0 and the high face of i = nx-1,
+// cells holds one value (pure air or pure water).  urow[k*ny + j] = that value v when the row is
+// interior (0 < j < ny-1, 0 < k < nz-1) and every face of every cell of row (j,k) except the two x-walls (bx at i = 0 and the high face of i = nx-1,
 // both walls, stored as 0) equals v bitwise, else 0; one warp per row.  A pass that reads urow[r]
 // != 0 takes its face values from it instead of loading them: the same values, so the same results.
 // On a grid stretched in z the metric factors differ per axis, and a row away from the interface
@@ -461,7 +461,7 @@ __global__ void k_uniform_rows(int nx, int ny, int nz, const float *__restrict__
     if (r >= ny * nz) return;
     const int j = r % ny, k = r / ny;
     const size_t sxy = (size_t)nx * ny, c0 = (size_t)r * nx;
-    const bool inner = j < ny - 1 && k < nz - 1;
+    const bool inner = j > 0 && k > 0 && j < ny - 1 && k < nz - 1;
     const float vy = by[c0], vx = nx > 1 ? bx[c0 + 1] : vy, vzl = bz[c0], vzh = inner ? bz[c0 + sxy] : 0.f;
     const int bxv = __float_as_int(vx), byv = __float_as_int(vy), bzl = __float_as_int(vzl),
               bzh = __float_as_int(vzh);
@@ -542,15 +542,20 @@ __global__ void k_smooth_split(int nx, int ny, int nz, float h2, LevelArrays<flo
 
 // The same colour pass, four consecutive cells of the colour per thread (nx % 8 == 0): the cells'
 // slots mb..mb+3 are float4-aligned in the colour-split arrays, so the x-neighbours (one float4
-// and one scalar), the y and z neighbours, b and the results move as float4; on rows that are not
-// uniform the faces come as float4 pairs from which each cell takes its own.  Four independent
+// and one scalar), the y and z neighbours, b and the results move as float4.  Four independent
 // updates per thread keep more loads in flight than one, which the pass needs once uniform rows
 // have removed most of its bytes.  Each cell's arithmetic is k_smooth_split's, in its order.
 // OFF = (j + k + colour) & 1, the x offset of the colour in the row (uniform across a warp).
 // BAND: the row's record is {vx, vy, vzl, vzh} of a banded row (all four equal on a uniform row,
-// zeros elsewhere), else {v, v, v, v} from urow.
+// zeros elsewhere), else {v, v, v, v} from urow.  A row with a record is interior (0 < j < ny-1,
+// 0 < k < nz-1: k_uniform_rows), so its update needs no y or z wall tests, which keeps the
+// record path short; the neighbours are loaded before the record is known, under the wall tests
+// any row needs.  Rows without a record take their faces from S, the colour-split copies of the
+// face arrays: a cell's low faces are the own colour's slots, its high faces the low faces of its
+// +x, +y and +z neighbours, i.e. the other colour's slots of its x-neighbour (as for p), mb + hx
+// and mb + hxy; six float4 and one scalar, each value used.
 template <int OFF, bool BAND, bool ZERO>
-__device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, const LevelArrays<float> &L,
+__device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, const LevelArrays<float> &S,
                                             const float *__restrict__ b, float *__restrict__ p, int colour, float4 rv,
                                             int g, int j, int k)
 {
@@ -561,10 +566,10 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
     const float *__restrict__ o = p + (colour ? 0 : half);
     float *own = p + (colour ? half : 0);
     const float *bo = b + (colour ? half : 0);
+    const size_t so = colour ? half : 0, sn = colour ? 0 : half;  // own and other colour in S
     {
-        const long long n = (long long)sxy * nz, c0 = 2 * (long long)mb, m = (long long)mb;
+        const long long n = (long long)sxy * nz, m = (long long)mb;
         (void)n;
-        (void)c0;
         (void)m;
         if (!(MG_CK(m, m + 3, half, CK_SMOOTH_SPLIT4) &&
               (OFF ? (g >= G - 1 || MG_CK(m + 4, m + 4, half, CK_SMOOTH_SPLIT4))
@@ -573,9 +578,10 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
               (j >= ny - 1 || MG_CK(m + hx, m + hx + 3, half, CK_SMOOTH_SPLIT4)) &&
               (k == 0 || MG_CK(m - (long long)hxy, m - (long long)hxy + 3, half, CK_SMOOTH_SPLIT4)) &&
               (k >= nz - 1 || MG_CK(m + hxy, m + hxy + 3, half, CK_SMOOTH_SPLIT4)) &&
-              (v != 0.f || (MG_CK(c0, c0 + 7 + ((OFF && 8 * g + 7 < nx - 1) ? 1 : 0), n, CK_SMOOTH_SPLIT4) &&
-                            (j >= ny - 1 || MG_CK(c0 + nx, c0 + nx + 7, n, CK_SMOOTH_SPLIT4)) &&
-                            (k >= nz - 1 || MG_CK(c0 + sxy, c0 + sxy + 7, n, CK_SMOOTH_SPLIT4))))))
+              (v != 0.f || (MG_CK(so + m, so + m + 3, n, CK_SMOOTH_SPLIT4) &&
+                            MG_CK(sn + m, sn + m + 3 + ((OFF && g < G - 1) ? 1 : 0), n, CK_SMOOTH_SPLIT4) &&
+                            (j >= ny - 1 || MG_CK(sn + m + hx, sn + m + hx + 3, n, CK_SMOOTH_SPLIT4)) &&
+                            (k >= nz - 1 || MG_CK(sn + m + hxy, sn + m + hxy + 3, n, CK_SMOOTH_SPLIT4))))))
             return;
     }
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -591,60 +597,67 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
     const float oy0[4] = {oym.x, oym.y, oym.z, oym.w}, oy1[4] = {oyp.x, oyp.y, oyp.z, oyp.w};
     const float oz0[4] = {ozm.x, ozm.y, ozm.z, ozm.w}, oz1[4] = {ozp.x, ozp.y, ozp.z, ozp.w};
     const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
-    const size_t c0 = 2 * mb;
-    float fbx[9], fby[8], fbyh[8], fbz[8], fbzh[8];
-    auto ld8 = [](const float *a, float *d) {
-        const float4 u = *reinterpret_cast<const float4 *>(a), w = *reinterpret_cast<const float4 *>(a + 4);
-        d[0] = u.x; d[1] = u.y; d[2] = u.z; d[3] = u.w; d[4] = w.x; d[5] = w.y; d[6] = w.z; d[7] = w.w;
-    };
-    // on a uniform row the diagonal is 6v, or 5v at an x-wall (the sums of inv_diag, in its
-    // order: 0 + v = v + 0 = v), so two divisions serve the thread's four cells; on a banded row
-    // the same with vx, vy, vzl, vzh in their places
-    const float vx = BAND ? rv.x : v, vy = BAND ? rv.y : v, vzl = BAND ? rv.z : v, vzh = BAND ? rv.w : v;
-    float inv6 = 0.f, inv5 = 0.f;
-    if (v == 0.f) {
-        ld8(L.bx + c0, fbx);
-        fbx[8] = (OFF && 8 * g + 7 < nx - 1) ? L.bx[c0 + 8] : 0.f;
-        ld8(L.by + c0, fby);
-        if (j < ny - 1) ld8(L.by + c0 + nx, fbyh); else for (int q = 0; q < 8; q++) fbyh[q] = 0.f;
-        ld8(L.bz + c0, fbz);
-        if (k < nz - 1) ld8(L.bz + c0 + sxy, fbzh); else for (int q = 0; q < 8; q++) fbzh[q] = 0.f;
-    } else if (BAND) {
-        inv6 = 1.f / ((((((vx + vx) + vy) + vy) + vzl) + vzh));
-        inv5 = 1.f / ((((vx + vy) + vy) + vzl) + vzh);
-    } else {
-        const float s5 = (((v + v) + v) + v) + v;
-        inv6 = 1.f / (s5 + v);
-        inv5 = 1.f / s5;
-    }
     float out[4];
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-        const int i = 8 * g + 2 * t + OFF;
-        const int e = 2 * t + OFF;
-        float bxl, bxh, byl, byh, bzl, bzh;
-        if (v != 0.f) {
-            bxl = i > 0 ? vx : 0.f; bxh = i < nx - 1 ? vx : 0.f; byl = byh = vy; bzl = vzl; bzh = vzh;
+    if (v != 0.f) {
+        // a row with a record: the diagonal is 6v, or 5v at an x-wall (the sums of inv_diag, in its
+        // order: 0 + v = v + 0 = v), so two divisions serve the thread's four cells; on a banded
+        // row the same with vx, vy, vzl, vzh in their places
+        const float vx = BAND ? rv.x : v, vy = BAND ? rv.y : v, vzl = BAND ? rv.z : v, vzh = BAND ? rv.w : v;
+        float inv6, inv5;
+        if (BAND) {
+            inv6 = 1.f / ((((((vx + vx) + vy) + vy) + vzl) + vzh));
+            inv5 = 1.f / ((((vx + vy) + vy) + vzl) + vzh);
         } else {
-            bxl = fbx[e]; bxh = i < nx - 1 ? fbx[e + 1] : 0.f;
-            byl = fby[e]; byh = fbyh[e]; bzl = fbz[e]; bzh = fbzh[e];
+            const float s5 = (((v + v) + v) + v) + v;
+            inv6 = 1.f / (s5 + v);
+            inv5 = 1.f / s5;
         }
-        const float pxm = xs[t + OFF], pxp = xs[t + 1 + OFF];  // slots mb+t-1+OFF, mb+t+OFF
-        float s = 0.f;
-        if (i > 0) s = fmaf(bxl, pxm, s);
-        if (i < nx - 1) s = fmaf(bxh, pxp, s);
-        if (j > 0) s = fmaf(byl, oy0[t], s);
-        if (j < ny - 1) s = fmaf(byh, oy1[t], s);
-        if (k > 0) s = fmaf(bzl, oz0[t], s);
-        if (k < nz - 1) s = fmaf(bzh, oz1[t], s);
-        const float dinv = v != 0.f ? ((i > 0 && i < nx - 1) ? inv6 : inv5)
-                                    : inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh);
-        out[t] = dinv * fmaf(-h2, bb[t], s);
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int i = 8 * g + 2 * t + OFF;
+            const float pxm = xs[t + OFF], pxp = xs[t + 1 + OFF];  // slots mb+t-1+OFF, mb+t+OFF
+            float s = 0.f;
+            if (i > 0) s = fmaf(vx, pxm, s);
+            if (i < nx - 1) s = fmaf(vx, pxp, s);
+            s = fmaf(vy, oy0[t], s);
+            s = fmaf(vy, oy1[t], s);
+            s = fmaf(vzl, oz0[t], s);
+            s = fmaf(vzh, oz1[t], s);
+            const float dinv = (i > 0 && i < nx - 1) ? inv6 : inv5;
+            out[t] = dinv * fmaf(-h2, bb[t], s);
+        }
+    } else {
+        const float4 xl = *reinterpret_cast<const float4 *>(S.bx + so + mb);
+        const float4 yl = *reinterpret_cast<const float4 *>(S.by + so + mb);
+        const float4 zl = *reinterpret_cast<const float4 *>(S.bz + so + mb);
+        const float4 xh = *reinterpret_cast<const float4 *>(S.bx + sn + mb);
+        const float xe = (OFF && g < G - 1) ? S.bx[sn + mb + 4] : 0.f;
+        const float4 yh = (j < ny - 1) ? *reinterpret_cast<const float4 *>(S.by + sn + mb + hx) : zero4;
+        const float4 zh = (k < nz - 1) ? *reinterpret_cast<const float4 *>(S.bz + sn + mb + hxy) : zero4;
+        const float fxl[4] = {xl.x, xl.y, xl.z, xl.w}, fxh[5] = {xh.x, xh.y, xh.z, xh.w, xe};
+        const float fyl[4] = {yl.x, yl.y, yl.z, yl.w}, fyh[4] = {yh.x, yh.y, yh.z, yh.w};
+        const float fzl[4] = {zl.x, zl.y, zl.z, zl.w}, fzh[4] = {zh.x, zh.y, zh.z, zh.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int i = 8 * g + 2 * t + OFF;
+            // high x-face: the other colour's slot mb+t+OFF, the x-neighbour's low face
+            const float bxl = fxl[t], bxh = i < nx - 1 ? fxh[t + OFF] : 0.f;
+            const float byl = fyl[t], byh = fyh[t], bzl = fzl[t], bzh = fzh[t];
+            const float pxm = xs[t + OFF], pxp = xs[t + 1 + OFF];
+            float s = 0.f;
+            if (i > 0) s = fmaf(bxl, pxm, s);
+            if (i < nx - 1) s = fmaf(bxh, pxp, s);
+            if (j > 0) s = fmaf(byl, oy0[t], s);
+            if (j < ny - 1) s = fmaf(byh, oy1[t], s);
+            if (k > 0) s = fmaf(bzl, oz0[t], s);
+            if (k < nz - 1) s = fmaf(bzh, oz1[t], s);
+            out[t] = inv_diag<float>(0.f, bxl, bxh, byl, byh, bzl, bzh) * fmaf(-h2, bb[t], s);
+        }
     }
     *reinterpret_cast<float4 *>(own + mb) = make_float4(out[0], out[1], out[2], out[3]);
 }
 template <bool BAND, bool ZERO>
-__global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<float> L, const float *__restrict__ b,
+__global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<float> S, const float *__restrict__ b,
                                 float *__restrict__ p, int colour, const float *__restrict__ urow,
                                 const float4 *__restrict__ arow, int rev)
 {
@@ -661,8 +674,8 @@ __global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<fl
         const float v = urow ? urow[(size_t)k * ny + j] : 0.f;
         rv = make_float4(v, v, v, v);
     }
-    if ((j + k + colour) & 1) split4_body<1, BAND, ZERO>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
-    else split4_body<0, BAND, ZERO>(nx, ny, nz, h2, L, b, p, colour, rv, g, j, k);
+    if ((j + k + colour) & 1) split4_body<1, BAND, ZERO>(nx, ny, nz, h2, S, b, p, colour, rv, g, j, k);
+    else split4_body<0, BAND, ZERO>(nx, ny, nz, h2, S, b, p, colour, rv, g, j, k);
 }
 
 // r = b - h^-2 sum_f beta_f (p_nb - p_c) at one fine cell (sum order x-,x+,y-,y+,z-,z+).
@@ -2355,24 +2368,26 @@ template cudaError_t launch_smooth<float>(Dims, float, const LevelArrays<float> 
                                           cudaStream_t, int, int, bool);
 
 cudaError_t launch_smooth_split(Dims d, float h2, const LevelArrays<float> &L, const float *b, float *p, int colour,
-                                cudaStream_t s, const float *urow, const float4 *arow, int rev, bool zero)
+                                cudaStream_t s, const float *urow, const float4 *arow, int rev, bool zero,
+                                const LevelArrays<float> *S)
 {
     note_launch();
     if (d.nx % 8 == 0) {  // four cells per thread, blocks of 32 threads x 4 rows
+        if (!S || !S->bx || !S->by || !S->bz) return cudaErrorInvalidValue;
         const int G = d.nx / 8;
         const dim3 grid((G + 31) / 32, (d.ny + 3) / 4, d.nz), block(32, 4);
         if (arow) {
             if (zero)
-                k_smooth_split4<true, true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow, rev);
+                k_smooth_split4<true, true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, *S, b, p, colour, urow, arow, rev);
             else
-                k_smooth_split4<true, false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, arow,
+                k_smooth_split4<true, false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, *S, b, p, colour, urow, arow,
                                                                     rev);
         } else {
             if (zero)
-                k_smooth_split4<false, true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow, nullptr,
-                                                                    rev);
+                k_smooth_split4<false, true><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, *S, b, p, colour, urow,
+                                                                    nullptr, rev);
             else
-                k_smooth_split4<false, false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, L, b, p, colour, urow,
+                k_smooth_split4<false, false><<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, h2, *S, b, p, colour, urow,
                                                                      nullptr, rev);
         }
     } else {
