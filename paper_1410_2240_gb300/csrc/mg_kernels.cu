@@ -87,9 +87,19 @@ __device__ bool reduce_finish(double a, double b, double *partials, double *dsca
     if (!last) return false;
     __threadfence();
     double x = 0.0, y = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        x += __ldcg(partials + 2 * i);
-        y += __ldcg(partials + 2 * i + 1);
+    // two strides per iteration, both loads issued before either sum: half the chain of
+    // dependent L2 round trips, the same additions in the same order
+    const int nb = (int)gridDim.x;
+    for (int i = threadIdx.x; i < nb; i += 2 * blockDim.x) {
+        const int i2 = i + (int)blockDim.x;
+        const double x0 = __ldcg(partials + 2 * i), y0 = __ldcg(partials + 2 * i + 1);
+        const double x1 = i2 < nb ? __ldcg(partials + 2 * i2) : 0.0, y1 = i2 < nb ? __ldcg(partials + 2 * i2 + 1) : 0.0;
+        x += x0;
+        y += y0;
+        if (i2 < nb) {
+            x += x1;
+            y += y1;
+        }
     }
     x = block_sum<kRedThreads>(x);
     y = block_sum<kRedThreads>(y);
@@ -99,6 +109,23 @@ __device__ bool reduce_finish(double a, double b, double *partials, double *dsca
         *ctr = 0u;
     }
     return true;
+}
+
+// The last block of a grid to get here (the counter after the partials, reset by that block):
+// true in all its threads.  For kernels that need one block to act after every block has read
+// something, with nothing to sum.
+__device__ bool last_block(double *partials)
+{
+    __shared__ bool last;
+    unsigned *ctr = reinterpret_cast<unsigned *>(partials + 2 * kRedBlocks);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+        if (last) *ctr = 0u;
+    }
+    __syncthreads();
+    return last;
 }
 
 __device__ __forceinline__ void cell_of(unsigned idx, int nx, int ny, int &i, int &j, int &k)
@@ -1832,10 +1859,14 @@ __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const d
 // S_SIGMA <d, A d>, S_RR ||r||^2.
 // ---------------------------------------------------------------------------
 
-// r = b - A p (FP64); optionally r32 = r / scale, scale = RMS of b (first pass) written to scale_slot
+// r = b - A p (FP64), as residual_at forms it: differences of neighbouring p first, so a large
+// smooth offset in p (a hydrostatic pressure) cancels before any product.  Optionally r32 = r /
+// scale, scale = RMS of b (first pass) written to scale_slot.  Cell indices by multiply-shift
+// division (fnx, fny).
 __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<double> L, const double *__restrict__ b,
                             const double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
-                            double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, size_t half)
+                            double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, size_t half,
+                            FastDiv fnx, FastDiv fny)
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
@@ -1848,8 +1879,8 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
     }
     double rr = 0.0, sp = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_of(idx, nx, ny, i, j, k);
+        const unsigned t = fdiv(idx, fnx), kk = fdiv(t, fny);
+        const int i = (int)(idx - t * (unsigned)nx), k = (int)kk, j = (int)(t - kk * (unsigned)ny);
         const double v = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         r[idx] = v;
         if (r32) {
@@ -1895,12 +1926,20 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
     const float4 *r4 = reinterpret_cast<const float4 *>(r32);
     const float4 *z4 = reinterpret_cast<const float4 *>(z);
     const float4 *o4 = reinterpret_cast<const float4 *>(zo);
-    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += stride) {
-        const float4 rv = r4[v], zv = z4[v];
-        a += (double)fmaf(rv.w, zv.w, fmaf(rv.z, zv.z, fmaf(rv.y, zv.y, rv.x * zv.x)));
-        if (zo) {
-            const float4 ov = o4[v];
-            c += (double)fmaf(rv.w, ov.w, fmaf(rv.z, ov.z, fmaf(rv.y, ov.y, rv.x * ov.x)));
+    auto dot4 = [](float4 x, float4 y) { return (double)fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x))); };
+    // float4 groups v and v + stride per iteration, all loads issued first; the sums in the same
+    // order as one group per iteration
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += 2 * stride) {
+        const unsigned w = v + stride;
+        const bool has_w = w < n4;
+        const float4 rv = r4[v], zv = z4[v], rw = has_w ? r4[w] : zero4, zw = has_w ? z4[w] : zero4;
+        const float4 ov = zo ? o4[v] : zero4, ow = (zo && has_w) ? o4[w] : zero4;
+        a += dot4(rv, zv);
+        if (zo) c += dot4(rv, ov);
+        if (has_w) {
+            a += dot4(rw, zw);
+            if (zo) c += dot4(rw, ow);
         }
     }
     for (unsigned idx = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -1926,24 +1965,43 @@ __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restric
                                     (so_slot >= 0 ? dscal[so_slot] / dscal[sz_slot] : 1.0);
     const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
     double2 *d2 = reinterpret_cast<double2 *>(d);
-    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
-        size_t i0 = 2 * v, i1 = 2 * v + 1;
-        if (sp.half) {  // colour-split Z: the pair's colours sit at slot v of each half
+    // the two Z indices of pair v (colour-split Z: the pair's colours sit at slot v of each half)
+    auto zidx = [&](unsigned v, size_t &i0, size_t &i1) {
+        i0 = 2 * (size_t)v;
+        i1 = 2 * (size_t)v + 1;
+        if (sp.half) {
             const int q = row_parity(2 * v, sp);
             i0 = (q ? sp.half : 0) + v;
             i1 = (q ? 0 : sp.half) + v;
-            if (!(MG_CK(i0, i0, (long long)n, CK_SPLIT_SLOT) && MG_CK(i1, i1, (long long)n, CK_SPLIT_SLOT))) continue;
+            return MG_CK(i0, i0, (long long)n, CK_SPLIT_SLOT) && MG_CK(i1, i1, (long long)n, CK_SPLIT_SLOT);
         }
-        const double z0 = widen(z[i0]), z1 = widen(z[i1]);
-        double2 dv = first ? make_double2(0.0, 0.0) : d2[v];
-        dv.x = fma(beta, dv.x, z0);
-        dv.y = fma(beta, dv.y, z1);
-        d2[v] = dv;
+        return true;
+    };
+    // pairs v and v + stride per iteration, both pairs' loads issued before either update
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += 2 * stride) {
+        const unsigned w = v + stride;
+        const bool has_w = w < n2;
+        size_t a0, a1, b0 = 0, b1 = 0;
+        const bool ok_v = zidx(v, a0, a1), ok_w = has_w && zidx(w, b0, b1);
+        const Z za0 = ok_v ? z[a0] : Z(0), za1 = ok_v ? z[a1] : Z(0);
+        const Z zb0 = ok_w ? z[b0] : Z(0), zb1 = ok_w ? z[b1] : Z(0);
+        double2 dv = (first || !ok_v) ? make_double2(0.0, 0.0) : d2[v];
+        double2 dw = (first || !ok_w) ? make_double2(0.0, 0.0) : d2[w];
+        if (ok_v) {
+            dv.x = fma(beta, dv.x, widen(za0));
+            dv.y = fma(beta, dv.y, widen(za1));
+            d2[v] = dv;
+        }
+        if (ok_w) {
+            dw.x = fma(beta, dw.x, widen(zb0));
+            dw.y = fma(beta, dw.y, widen(zb1));
+            d2[w] = dw;
+        }
     }
     for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride)
         d[idx] = fma(beta, first ? 0.0 : d[idx], widen(z[idx]));
     // every block has read <r, z> above: the last one moves the new <r, z> into its place
-    if (reduce_finish(0.0, 0.0, partials, dscal, -1, -1) && threadIdx.x == 0) dscal[S_RZ] = dscal[S_RZN];
+    if (last_block(partials) && threadIdx.x == 0) dscal[S_RZ] = dscal[S_RZN];
 }
 
 // Jacobi preconditioner: z = (scale * dinv) * r, dead cells 0
@@ -2797,7 +2855,8 @@ cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, c
 {
     const unsigned g = red_grid(d.n());
     note_launch();
-    k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials, sp.half);
+    k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials, sp.half,
+                                          make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny));
     return cudaGetLastError();
 }
 
