@@ -27,6 +27,7 @@ from __future__ import annotations
 import argparse
 import gc
 import json
+import resource
 import os
 import statistics
 import subprocess
@@ -405,8 +406,9 @@ def e2e_leg(case, K, W):
     for i in range(W):
         step(i, last=False)
     torch.cuda.synchronize()
-    steps_ms = []
+    steps_ms, nivcsw = [], []
     mem0 = torch.cuda.memory_stats()
+    load0 = os.getloadavg()
     gc.collect()
     gc.disable()  # no collector pause inside the timed steps (as timeit does)
     try:
@@ -414,8 +416,10 @@ def e2e_leg(case, K, W):
         upload(0)  # the first timed step's inputs: inside the timed region, hidden by nothing
         for i in range(K):
             ts = time.perf_counter()
+            cs = resource.getrusage(resource.RUSAGE_SELF).ru_nivcsw
             step(i, last=(i == K - 1))
             steps_ms.append(1e3 * (time.perf_counter() - ts))
+            nivcsw.append(resource.getrusage(resource.RUSAGE_SELF).ru_nivcsw - cs)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
     finally:
@@ -427,6 +431,12 @@ def e2e_leg(case, K, W):
     d2h = 7 * 8 * n
     return {"value": 2 * K / sec, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": 1e3 * sec / K, "host_step_ms": [round(t, 2) for t in steps_ms],
+            # involuntary context switches of this process per step (the host thread preempted)
+            # and the host's load average before and after: a stalled step with many switches
+            # and a high load points at other work on the host's cores
+            "involuntary_ctx_switches_per_step": nivcsw,
+            "host_loadavg_1min": [round(load0[0], 2), round(os.getloadavg()[0], 2)],
+            "host_cores": os.cpu_count(),
             "allocator_during_timing": grew,
             "api": "paper_1410_2240_gb300.autograd.project (mixed) + backward, inputs of step i+1 uploaded "
                    "during step i's backward, results read back on a second stream"}

@@ -51,6 +51,19 @@ __device__ double block_sum(double v)
     return r;
 }
 
+// A scalar every thread of a block needs, computed by thread 0 and shared: FP64 divisions and
+// square roots of the CG's scalars would otherwise run in every thread, on the FP64 unit these
+// passes are bound by (tens of operations per thread, one to two per cell).  f() is called in
+// thread 0 only; the value is the one each thread would have computed.
+template <typename F>
+__device__ __forceinline__ double block_scalar(F f)
+{
+    __shared__ double v;
+    if (threadIdx.x == 0) v = f();
+    __syncthreads();
+    return v;
+}
+
 // Sums the per-block partial pairs in a fixed order (deterministic) into dscal.
 __global__ void k_finish2(const double *__restrict__ partials, int nblocks, double *__restrict__ dscal, int slot0,
                           int slot1)
@@ -1268,7 +1281,7 @@ __global__ void k_sum_live(unsigned n, const double *__restrict__ v, const doubl
 __global__ void k_rhs_center(unsigned n, const double *__restrict__ rhs, const double *__restrict__ dinv,
                              double *__restrict__ b0, double *dscal, double *__restrict__ partials)
 {
-    const double mean = dscal[S_SUM_B] / dscal[S_NLIVE];
+    const double mean = block_scalar([&] { return dscal[S_SUM_B] / dscal[S_NLIVE]; });
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const double v = pos_bits(dinv[idx]) ? rhs[idx] - mean : 0.0;
@@ -1302,7 +1315,7 @@ __global__ void k_resid_norm(int nx, int ny, int nz, double ih2, LevelArrays<dou
 __global__ void k_sub_mean_p(unsigned n, const double *__restrict__ dinv, double *__restrict__ p,
                              const double *__restrict__ dscal)
 {
-    const double mean = dscal[S_SUM_P] / dscal[S_NLIVE];
+    const double mean = block_scalar([&] { return dscal[S_SUM_P] / dscal[S_NLIVE]; });
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
         p[idx] = pos_bits(dinv[idx]) ? p[idx] - mean : 0.0;
 }
@@ -1314,7 +1327,7 @@ __global__ void k_resid_cast(int nx, int ny, int nz, double ih2, LevelArrays<dou
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
-    const double inv_scale = 1.0 / dscal[scale_in];
+    const double inv_scale = block_scalar([&] { return 1.0 / dscal[scale_in]; });
     double rr = 0.0, sp = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int i, j, k;
@@ -1870,13 +1883,13 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
 {
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
-    double inv_scale = 1.0;
-    if (r32) {
+    const double inv_scale = block_scalar([&] {
+        if (!r32) return 1.0;
         const double rms = sqrt(dscal[S_NB2] / dscal[S_NLIVE]);
         const double sc = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
-        inv_scale = 1.0 / sc;
-        if (blockIdx.x == 0 && threadIdx.x == 0) dscal[scale_slot] = sc;
-    }
+        if (blockIdx.x == 0) dscal[scale_slot] = sc;
+        return 1.0 / sc;
+    });
     double rr = 0.0, sp = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const unsigned t = fdiv(idx, fnx), kk = fdiv(t, fny);
@@ -1926,7 +1939,8 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
     const float4 *r4 = reinterpret_cast<const float4 *>(r32);
     const float4 *z4 = reinterpret_cast<const float4 *>(z);
     const float4 *o4 = reinterpret_cast<const float4 *>(zo);
-    auto dot4 = [](float4 x, float4 y) { return (double)fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x))); };
+    // widened on the integer pipe (exact, as the conversion instruction, which runs on the FP64 unit)
+    auto dot4 = [](float4 x, float4 y) { return widen(fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)))); };
     // float4 groups v and v + stride per iteration, all loads issued first; the sums in the same
     // order as one group per iteration
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1943,8 +1957,8 @@ __global__ void k_pcg_dots32(unsigned n, const float *__restrict__ r32, const fl
         }
     }
     for (unsigned idx = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        a += (double)(r32[idx] * z[idx]);
-        if (zo) c += (double)(r32[idx] * zo[idx]);
+        a += widen(r32[idx] * z[idx]);
+        if (zo) c += widen(r32[idx] * zo[idx]);
     }
     a = block_sum<kRedThreads>(a) * sr * dscal[sz_slot];
     c = block_sum<kRedThreads>(c) * (so_slot >= 0 ? sr * dscal[so_slot] : 0.0);
@@ -1960,9 +1974,11 @@ template <typename Z>
 __global__ void k_pcg_dir(unsigned n, const Z *__restrict__ z, double *__restrict__ d, double *dscal,
                           int sz_slot, int so_slot, int first, Split sp, double *__restrict__ partials)
 {
-    const double beta = first ? 0.0
-                              : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ] *
-                                    (so_slot >= 0 ? dscal[so_slot] / dscal[sz_slot] : 1.0);
+    const double beta = block_scalar([&] {
+        return first ? 0.0
+                     : (dscal[S_RZN] - dscal[S_RZO]) / dscal[S_RZ] *
+                           (so_slot >= 0 ? dscal[so_slot] / dscal[sz_slot] : 1.0);
+    });
     const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
     double2 *d2 = reinterpret_cast<double2 *>(d);
     // the two Z indices of pair v (colour-split Z: the pair's colours sit at slot v of each half)
@@ -2051,14 +2067,15 @@ __global__ void k_pcg_update(unsigned n, const double *__restrict__ d, const dou
                              Split sp)
 {
     // d holds D = (direction) / sd (k_pcg_dir): alpha = <r,z> / <d, A d> times sd
-    const double alpha = dscal[S_RZ] / (dscal[S_SIGMA] * (sd_slot >= 0 ? dscal[sd_slot] : 1.0));
-    double inv_scale = 1.0;
-    if (r32) {
+    const double alpha =
+        block_scalar([&] { return dscal[S_RZ] / (dscal[S_SIGMA] * (sd_slot >= 0 ? dscal[sd_slot] : 1.0)); });
+    const double inv_scale = block_scalar([&] {
+        if (!r32) return 1.0;
         const double rms = sqrt(dscal[S_RR] / dscal[S_NLIVE]);
         const double sc = (rms > 0.0 && isfinite(rms)) ? rms : 1.0;
-        inv_scale = 1.0 / sc;
-        if (blockIdx.x == 0 && threadIdx.x == 0) dscal[scale_slot] = sc;
-    }
+        if (blockIdx.x == 0) dscal[scale_slot] = sc;
+        return 1.0 / sc;
+    });
     const float inv_scale32 = (float)inv_scale;
     double rr = 0.0;
     const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
