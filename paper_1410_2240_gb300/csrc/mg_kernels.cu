@@ -705,7 +705,13 @@ __global__ void k_smooth_split4(int nx, int ny, int nz, float h2, LevelArrays<fl
     // an ascending one starts on the data that pass touched last (still in L2)
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int by = rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
-    const int j = by * blockDim.y + threadIdx.y, k = rev ? nz - 1 - (int)blockIdx.z : (int)blockIdx.z;
+    // the planes of the four quarters interleaved in the block order (0, nz/4, nz/2, 3nz/4, 1, ...):
+    // the rows without a record gather in a band of planes (an interface), and interleaving runs
+    // their face-loading blocks alongside blocks of record rows instead of all together
+    const int zb = rev ? (int)gridDim.z - 1 - (int)blockIdx.z : (int)blockIdx.z;
+    const int qz = nz / 4;
+    const int k = (nz & 3) ? zb : (zb & 3) * qz + (zb >> 2);
+    const int j = by * blockDim.y + threadIdx.y;
     if (g >= nx / 8 || j >= ny) return;
     float4 rv;
     if (BAND) {
@@ -807,7 +813,9 @@ __global__ void k_resid_restrict_pairs(int nx, int ny, int nz, float ih2, LevelA
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int Jb = blockIdx.y * blockDim.y + threadIdx.y;
     const int J = rev ? NY - 1 - Jb : Jb;
-    const int K = rev ? nz / 2 - 1 - (int)blockIdx.z : (int)blockIdx.z;
+    // coarse planes of the four quarters interleaved in the block order, as in the colour passes
+    const int NZ = nz / 2, zb = rev ? NZ - 1 - (int)blockIdx.z : (int)blockIdx.z;
+    const int K = (NZ & 3) ? zb : (zb & 3) * (NZ / 4) + (zb >> 2);
     if (I >= NX || Jb >= NY) return;
     const size_t sxy = (size_t)nx * ny;
     const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
@@ -972,7 +980,11 @@ __global__ void k_prolong(int nx, int ny, int nz, const T *__restrict__ ec, cons
 {
     using P2 = typename Pair<T>::type;
     const int NX = nx / 2, NY = ny / 2, NZ = nz / 2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y, K = blockIdx.z;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+    // on the colour-split finest level, coarse planes of the four quarters interleaved in the block
+    // order, as in its colour passes and restriction
+    const int zb = blockIdx.z;
+    const int K = (SPLIT && (NZ & 3) == 0) ? (zb & 3) * (NZ / 4) + (zb >> 2) : zb;
     if (I >= NX || J >= NY) return;
     {
         const long long n = (long long)nx * ny * nz;
