@@ -104,6 +104,7 @@ struct mg_ctx {
     int *cc_label = nullptr, *cc_roots = nullptr;
     uint8_t *open_bits = nullptr;  // open low faces of each fine cell at the last labelling
     unsigned *cc_ctr = nullptr;
+    unsigned *pnz = nullptr;  // the zero test of a solve's initial guess
     double *cc_sum = nullptr, *cc_cnt = nullptr, *cc_part = nullptr;
     std::vector<double> hcnt, hsum;
     bool incompat = false;      // the current solve's rhs failed the compatibility test
@@ -871,8 +872,9 @@ int pcg_impl(mg_ctx *c, const double *rhs, double *p, double tol_user, mg_stats 
         // (re)start: true residual
         {
             ProfScope ps(c, MG_PROF_RESID64, true);
+            // the first residual of a solve tests p for zero (a zero guess needs no stencil)
             CK(mg::launch_pcg_resid(d, ih2, c->L64[0], c->b0, p, c->kr, mixed ? c->L32[0].b : nullptr, c->partials,
-                                    c->dscal, sc_cur, s, c->split0));
+                                    c->dscal, sc_cur, s, c->split0, first_check ? c->pnz : nullptr));
         }
         CKS(read_scalars(c));
         if (first_check) check_compatible(c);
@@ -1073,6 +1075,7 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (st == MG_OK && cudaMemsetAsync(c->open_bits, 0xff, c->dims[0].n(), c->s) != cudaSuccess)
         st = fail(MG_ERR_CUDA, "mg_setup: memset failed");
     if (st == MG_OK) st = c->alloc(&c->cc_ctr, 4);
+    if (st == MG_OK) st = c->alloc(&c->pnz, 1);
     if (st == MG_OK) st = c->alloc(&c->cc_roots, kMaxRegions);
     if (st == MG_OK) st = c->alloc(&c->cc_sum, kMaxRegions);
     if (st == MG_OK) st = c->alloc(&c->cc_cnt, kMaxRegions);

@@ -207,9 +207,11 @@ cudaError_t launch_to_f32_layout(size_t n, const double *src, float *dst, cudaSt
 cudaError_t launch_from_f32_layout(size_t n, const float *src, double *dst, cudaStream_t s, Split sp = {});
 
 // multigrid-preconditioned CG (FP64 Krylov vectors)
+// pnz (optional): a device word; with it, the pass first tests whether p is zero everywhere and,
+// if so, takes r = b without loading p's stencil (the same values)
 cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
                              double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s,
-                             Split sp = {});
+                             Split sp = {}, unsigned *pnz = nullptr);
 template <typename Z>
 cudaError_t launch_pcg_dots(size_t n, const double *r, const Z *z, const Z *zo, double *partials, double *dscal,
                             int sz_slot, int so_slot, cudaStream_t s);

@@ -1888,11 +1888,30 @@ __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const d
 // smooth offset in p (a hydrostatic pressure) cancels before any product.  Optionally r32 = r /
 // scale, scale = RMS of b (first pass) written to scale_slot.  Cell indices by multiply-shift
 // division (fnx, fny).
+// *flag |= 1 if any p[i] is nonzero (either sign of zero counts as zero); the caller clears it
+__global__ void k_nonzero(unsigned n, const double *__restrict__ p, unsigned *__restrict__ flag)
+{
+    bool any = false;
+    const unsigned n2 = n / 2, stride = gridDim.x * blockDim.x;
+    const double2 *p2 = reinterpret_cast<const double2 *>(p);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < n2; v += stride) {
+        const double2 x = p2[v];
+        any |= ((__double_as_longlong(x.x) | __double_as_longlong(x.y)) << 1) != 0;
+    }
+    for (unsigned idx = 2 * n2 + blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride)
+        any |= (__double_as_longlong(p[idx]) << 1) != 0;
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+// pnz (optional): the k_nonzero flag of p; 0 means p is zero everywhere, and each cell's
+// residual is then b exactly (residual64_at's zero case) with no stencil loaded: the same values
+// for a fraction of the loads (the first residual of a solve from a zero guess)
 __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<double> L, const double *__restrict__ b,
                             const double *__restrict__ p, double *__restrict__ r, float *__restrict__ r32,
                             double *__restrict__ dscal, int scale_slot, double *__restrict__ partials, size_t half,
-                            FastDiv fnx, FastDiv fny)
+                            FastDiv fnx, FastDiv fny, const unsigned *__restrict__ pnz)
 {
+    const bool pzero = pnz && *pnz == 0u;
     const unsigned n = (unsigned)nx * ny * nz;
     const size_t sxy = (size_t)nx * ny;
     const double inv_scale = block_scalar([&] {
@@ -1906,14 +1925,14 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const unsigned t = fdiv(idx, fnx), kk = fdiv(t, fny);
         const int i = (int)(idx - t * (unsigned)nx), k = (int)kk, j = (int)(t - kk * (unsigned)ny);
-        const double v = residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+        const double v = pzero ? b[idx] : residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
         r[idx] = v;
         if (r32) {
             const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
             if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = narrow(v * inv_scale);
         }
         rr += v * v;
-        if (pos_bits(L.dinv[idx])) sp += p[idx];
+        if (!pzero && pos_bits(L.dinv[idx])) sp += p[idx];
     }
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
@@ -2880,12 +2899,18 @@ cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, cons
 
 cudaError_t launch_pcg_resid(Dims d, double ih2, const LevelArrays<double> &L, const double *b, const double *p,
                              double *r, float *r32, double *partials, double *dscal, int scale_slot, cudaStream_t s,
-                             Split sp)
+                             Split sp, unsigned *pnz)
 {
     const unsigned g = red_grid(d.n());
+    if (pnz) {  // is p zero everywhere?
+        cudaError_t e = cudaMemsetAsync(pnz, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        note_launch();
+        k_nonzero<<<g, kRedThreads, 0, s>>>((unsigned)d.n(), p, pnz);
+    }
     note_launch();
     k_pcg_resid<<<g, kRedThreads, 0, s>>>(d.nx, d.ny, d.nz, ih2, L, b, p, r, r32, dscal, scale_slot, partials, sp.half,
-                                          make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny));
+                                          make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny), pnz);
     return cudaGetLastError();
 }
 
