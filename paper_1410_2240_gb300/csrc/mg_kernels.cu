@@ -1651,7 +1651,7 @@ __device__ __forceinline__ void mom_edge_at(const MomArgs &m, size_t n, int i, i
 template <int A>
 __device__ __forceinline__ double mom_face(const MomArgs &m, size_t n, int i, int j, int k, size_t c, double beta)
 {
-    constexpr int ai = A == 0, aj = A == 1, ak = A == 2;
+    constexpr int ai = A == 0, aj = A == 1;
     const size_t cm = c - (ai ? 1 : (aj ? (size_t)m.nx : (size_t)m.nx * m.ny));
     double conv = __dmul_rn(__dsub_rn(m.w[A * n + c], m.w[A * n + cm]), m.ih);
     double visc = __dsub_rn(m.w[(3 + A) * n + c], m.w[(3 + A) * n + cm]);
