@@ -608,11 +608,11 @@ def run_ours(args):
     out["smoother_cell_updates_per_s"] = n / (sweep_ms / 1e3) if sweep_ms else None
     out["kernel_gbs"] = kernel_gbs(out["kernel_ms"], n)
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e_leg(case, max(4, K // 2), 5)
+        out["e2e"] = e2e_leg(case, max(4, K), 5)
         # the same with the projected velocity and all four gradients read back (940 MB a step):
         # the copies engines' reads of device memory slow the overlapped solves (reported, not the
         # headline: the result the contract reads back is the loss)
-        full = e2e_leg(case, max(4, K // 2), 5, readback="all")
+        full = e2e_leg(case, max(4, K), 5, readback="all")
         out["e2e"]["all_results_read_back"] = {k: full[k] for k in ("value", "ms_per_step", "d2h_bytes_per_step",
                                                                      "device_step_ms")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "c5":

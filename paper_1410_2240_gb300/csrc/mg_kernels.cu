@@ -632,7 +632,9 @@ __device__ __forceinline__ void split4_body(int nx, int ny, int nz, float h2, co
     const float4 oyp = (!ZERO && j < ny - 1) ? *reinterpret_cast<const float4 *>(o + mb + hx) : zero4;
     const float4 ozm = (!ZERO && k > 0) ? *reinterpret_cast<const float4 *>(o + mb - hxy) : zero4;
     const float4 ozp = (!ZERO && k < nz - 1) ? *reinterpret_cast<const float4 *>(o + mb + hxy) : zero4;
-    const float4 bv = *reinterpret_cast<const float4 *>(bo + mb);
+    // b of this colour is read next a sweep later: loaded evict-first, so that it leaves L2 to the
+    // iterate the next pass reads
+    const float4 bv = __ldcs(reinterpret_cast<const float4 *>(bo + mb));
     const float xs[6] = {OFF ? 0.f : oxe, ox.x, ox.y, ox.z, ox.w, OFF ? oxe : 0.f};  // slots mb-1 .. mb+4
     const float oy0[4] = {oym.x, oym.y, oym.z, oym.w}, oy1[4] = {oyp.x, oyp.y, oyp.z, oyp.w};
     const float oz0[4] = {ozm.x, ozm.y, ozm.z, ozm.w}, oz1[4] = {ozp.x, ozp.y, ozp.z, ozp.w};
