@@ -63,7 +63,7 @@ SWEEP_KERNEL = {0: "k_smooth_split4 x2 colour passes, colour-split p, b and face
                 2: "k_rb_sweep<float,32,8> fused", 3: "k_rb_sweep_tma fused, TMA-staged planes"}
 # DRAM bytes of one finest-grid FP32 sweep of the default smoother (two k_smooth_split4 colour
 # passes) from an ncu capture of this workload
-SWEEP_TRAFFIC_256 = 119.294720e6 + 16.830208e6 + 119.297792e6 + 18.639360e6
+SWEEP_TRAFFIC_256 = 119.288064e6 + 11.910400e6 + 119.242240e6 + 13.071104e6
 PROF_GROUPS = (("smooth", 0), ("restrict", 1), ("prolong", 2), ("resid64", 3), ("cg_apply", 4), ("cg_vectors", 5),
                ("coarse_levels", 6), ("hierarchy_update", 7))
 
