@@ -117,7 +117,11 @@ struct mg_ctx {
     double *partials = nullptr; // reduction partials
     double *dscal = nullptr;    // device scalars (mg::Scal)
     double *hscal = nullptr;    // pinned host mirror of dscal
+    // pinned staging of the coarsest grid's inverse: its three face arrays (3 ncoarse), the
+    // inverse (ncoarse^2), then the two row counters of the finest uniform / banded rows
+    double *hcoarse = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_h = nullptr;  // the coarsest faces and the scalars reached the host
     // the coarse-grid correction of one V-cycle (everything below the finest level) as a
     // CUDA graph per precision, captured on first use on a private stream
     cudaStream_t cap_stream = nullptr;
@@ -149,6 +153,8 @@ struct mg_ctx {
     {
         for (void *q : allocs) cudaFree(q);
         if (hscal) cudaFreeHost(hscal);
+        if (hcoarse) cudaFreeHost(hcoarse);
+        if (ev_h) cudaEventDestroy(ev_h);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
@@ -204,8 +210,7 @@ inline double dot4(const double *a, const double *b, int n)
     return (s0 + s1) + (s2 + s3);
 }
 
-int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &bx, const std::vector<double> &by,
-                   const std::vector<double> &bz, std::vector<double> &M)
+int coarse_inverse(int nx, int ny, int nz, double h, const double *bx, const double *by, const double *bz, double *M)
 {
     const int n = nx * ny * nz;
     const double ih2 = 1.0 / (h * h);
@@ -247,7 +252,7 @@ int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &
                 }
         }
     }
-    M.assign((size_t)n * n, 0.0);
+    std::fill(M, M + (size_t)n * n, 0.0);
     for (auto &mem : members) {
         const int m = (int)mem.size();
         if (m < 2) continue;
@@ -292,7 +297,7 @@ int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &
         if (bad) return fail(MG_ERR_ARG, "coarsest-grid operator is not semi-definite");
         // W = C^-1 (lower), stored by columns as rows of WT (upper): column j solves C w = e_j
         std::vector<double> WT((size_t)m * m, 0.0);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) if (m > 128)
         for (int j = 0; j < m; j++) {
             double *w = &WT[(size_t)j * m];
             for (int i = j; i < m; i++) {
@@ -302,7 +307,7 @@ int coarse_inverse(int nx, int ny, int nz, double h, const std::vector<double> &
         }
         // X = S^-1 = W^T W: X[x][y] = sum_{q >= max(x,y)} WT[x][q] WT[y][q]
         std::vector<double> X((size_t)m * m);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) if (m > 128)
         for (int x = 0; x < m; x++) {
             const double *wx = &WT[(size_t)x * m];
             for (int y = 0; y <= x; y++) {
@@ -553,10 +558,17 @@ int coarse_correction_graph(mg_ctx *c, const std::vector<LevelArrays<T>> &L)
 
 // read the device scalars into the pinned mirror (one stream sync); report a kernel whose
 // bounded wait expired
+int check_scalars(mg_ctx *c);
 int read_scalars(mg_ctx *c)
 {
     CK(cudaMemcpyAsync(c->hscal, c->dscal, mg::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
+    return check_scalars(c);
+}
+
+// the scalars just read: report a kernel whose bounded wait expired (and clear its flag)
+int check_scalars(mg_ctx *c)
+{
     if (c->hscal[mg::S_ERR] != 0.0) {
         CK(cudaMemsetAsync(c->dscal + mg::S_ERR, 0, sizeof(double), c->s));
         return fail(MG_ERR_CUDA, "a pipelined smoothing kernel's bounded wait expired (data not delivered)");
@@ -751,15 +763,30 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
                                        l == 0 ? c->open_bits : nullptr, c->dscal + mg::S_TOPO));
     }
     CK(mg::launch_count_live(c->dims[0], c->L64[0].dinv, c->partials, c->dscal, s));
-    // coarsest operator to the host
+    // the coarsest operator and the scalars to the pinned host mirrors; the host waits for them
+    // alone (event), while the FP32 copies queued next still run: the host's inverse of the
+    // coarsest operator overlaps them
     const int nc = c->ncoarse;
-    std::vector<double> cb[3];
-    double *src[3] = {c->L64.back().bx, c->L64.back().by, c->L64.back().bz};
-    for (int a = 0; a < 3; a++) {
-        cb[a].resize(nc);
-        CK(cudaMemcpyAsync(cb[a].data(), src[a], nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double *hcb = c->hcoarse, *hM = c->hcoarse + 3 * (size_t)nc;
+    unsigned *hrow = reinterpret_cast<unsigned *>(hM + (size_t)nc * nc);
+    const double *src[3] = {c->L64.back().bx, c->L64.back().by, c->L64.back().bz};
+    for (int a = 0; a < 3; a++)
+        CK(cudaMemcpyAsync(hcb + (size_t)a * nc, src[a], nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->hscal, c->dscal, mg::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev_h, s));
+    if (c->o.prec == MG_MIXED) {
+        // narrowed faces and 1/sum of them (the value the FP32 smoothers form on the fly); the
+        // finest level's faces also in the colour-split layout
+        for (int l = 0; l < c->nlev; l++)
+            CK(mg::launch_level_f32(c->dims[l], c->L64[l], c->L32[l], s, l == 0 ? &c->sf0 : nullptr, c->split0));
+        if (c->rowcnt) CK(cudaMemsetAsync(c->rowcnt, 0, 2 * sizeof(unsigned), s));
+        if (c->urow0)
+            CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s, c->arow0,
+                                       c->rowcnt));
+        if (c->rowcnt) CK(cudaMemcpyAsync(hrow, c->rowcnt, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     }
-    CKS(read_scalars(c));
+    CK(cudaEventSynchronize(c->ev_h));
+    CKS(check_scalars(c));
     c->nlive = c->hscal[mg::S_NLIVE];
     // connected regions of the live fine cells, labelled again where the open faces changed
     // (first build included: the stored bits start as 0xff)
@@ -791,35 +818,11 @@ int compute_hierarchy(mg_ctx *c, const double *const face_coeffs[3])
         CK(cudaMemcpyAsync(c->hcnt.data(), c->cc_cnt, c->ncomp * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
-    std::vector<double> M;
-    CKS(coarse_inverse(dc.nx, dc.ny, dc.nz, c->hs.back(), cb[0], cb[1], cb[2], M));
-    CK(cudaMemcpyAsync(c->M, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    if (c->o.prec == MG_MIXED) {
-        for (int l = 0; l < c->nlev; l++) {
-            const size_t n = c->dims[l].n();
-            CK(mg::launch_cast_f32(n, c->L64[l].bx, c->L32[l].bx, s));
-            CK(mg::launch_cast_f32(n, c->L64[l].by, c->L32[l].by, s));
-            CK(mg::launch_cast_f32(n, c->L64[l].bz, c->L32[l].bz, s));
-            // 1/sum of the FP32 coefficients, the value the FP32 smoothers form on the fly
-            CK(mg::launch_diag_inv<float>(c->dims[l], c->L32[l].bx, c->L32[l].by, c->L32[l].bz, c->L32[l].dinv, s,
-                                          nullptr, 1.0f));
-        }
-        if (c->rowcnt) CK(cudaMemsetAsync(c->rowcnt, 0, 2 * sizeof(unsigned), s));
-        if (c->sf0.bx) {  // the same FP32 values (narrow of the FP64 face) in the colour-split layout
-            CK(mg::launch_to_f32_layout(c->dims[0].n(), c->L64[0].bx, c->sf0.bx, s, c->split0));
-            CK(mg::launch_to_f32_layout(c->dims[0].n(), c->L64[0].by, c->sf0.by, s, c->split0));
-            CK(mg::launch_to_f32_layout(c->dims[0].n(), c->L64[0].bz, c->sf0.bz, s, c->split0));
-        }
-        if (c->urow0)
-            CK(mg::launch_uniform_rows(c->dims[0], c->L32[0].bx, c->L32[0].by, c->L32[0].bz, c->urow0, s, c->arow0,
-                                       c->rowcnt));
-    }
-    CK(cudaStreamSynchronize(s));  // M's host staging buffer must outlive the copy
-    if (c->rowcnt) {
-        unsigned cnt[2] = {0, 0};
-        CK(cudaMemcpy(cnt, c->rowcnt, sizeof cnt, cudaMemcpyDeviceToHost));
-        c->banded = cnt[1] > cnt[0];
-    }
+    CKS(coarse_inverse(dc.nx, dc.ny, dc.nz, c->hs.back(), hcb, hcb + nc, hcb + 2 * (size_t)nc, hM));
+    CK(cudaMemcpyAsync(c->M, hM, (size_t)nc * nc * sizeof(double), cudaMemcpyHostToDevice, s));
+    // the pinned staging must outlive the copy; the row counters have arrived
+    CK(cudaStreamSynchronize(s));
+    if (c->o.prec == MG_MIXED && c->rowcnt) c->banded = hrow[1] > hrow[0];
     return MG_OK;
 }
 
@@ -1082,7 +1085,10 @@ int mg_setup(mg_ctx **out, const mg_grid *g, const double *const face_coeffs[3],
     if (st == MG_OK) st = c->alloc(&c->cc_part, 8 * mg::kRedBlocks);
     if (st != MG_OK) return bail(st);
     if (cudaMallocHost(&c->hscal, mg::S_COUNT * sizeof(double)) != cudaSuccess ||
-        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaMallocHost(&c->hcoarse, (3 * (size_t)c->ncoarse + (size_t)c->ncoarse * c->ncoarse + 1) * sizeof(double)) !=
+            cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_h, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(MG_ERR_CUDA, "mg_setup: pinned buffer / event creation failed"));
     }

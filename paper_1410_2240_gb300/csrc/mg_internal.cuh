@@ -117,7 +117,11 @@ cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *di
                             double *changed = nullptr);
 cudaError_t launch_restrict_coeffs(Dims fine, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s);
-cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s);
+// the FP32 copy of a level (faces and 1/sum of the narrowed faces) from its FP64 faces; with sf,
+// the faces also in the colour-split layout sp
+cudaError_t launch_level_f32(Dims d, const LevelArrays<double> &L, LevelArrays<float> &out, cudaStream_t s,
+                             LevelArrays<float> *sf = nullptr, Split sp = {});
+
 // one colour of a red-black sweep on planes [z0, z1) (z1 < 0: to the last plane); zero: the
 // iterate is zero and is not read (the first pass of a cycle from a zero guess)
 template <typename T>

@@ -405,12 +405,6 @@ __global__ void k_restrict_coeffs(int nx, int ny, int nz, const double *__restri
     cbz[C] = 0.25 * (((bz[f] + bz[f + 1]) + bz[f + nx]) + bz[f + nx + 1]);
 }
 
-__global__ void k_cast_f32(size_t n, const double *__restrict__ src, float *__restrict__ dst)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = narrow(src[i]);
-}
-
 // Inverse diagonal of a smoothing update: FP64 levels use the stored 1/sum(beta); FP32 levels
 // form 1/sum from the six face coefficients already loaded (sum in the order of k_diag_inv),
 // which saves reading dinv.
@@ -1382,6 +1376,52 @@ __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *
 
 // FP64 natural-order field <-> the finest FP32 field in the layout sp (one FP32 V-cycle on a
 // caller's FP64 rhs and iterate)
+// The FP32 copy of one level: the narrowed faces (natural layout; on the finest level with a
+// colour-split layout, also in that layout, sf != null) and 1/sum of the narrowed faces, summed
+// in k_diag_inv's order with its divisor memo (so the value k_diag_inv gives on the narrowed
+// faces), from one read of the FP64 faces.  Grid and runs as k_diag_inv.
+__global__ void k_level_f32(int nx, int ny, int nz, const double *__restrict__ bx, const double *__restrict__ by,
+                            const double *__restrict__ bz, LevelArrays<float> out, LevelArrays<float> sf,
+                            size_t half)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    const int k0 = blockIdx.z * kRun, k1 = min(k0 + kRun, nz);
+    const size_t sxy = (size_t)nx * ny;
+    float s_last = 1.0f, q_last = 1.0f;
+    size_t c = (size_t)k0 * sxy + (size_t)j * nx + i;
+    float bz_lo = narrow(bz[c]);
+    for (int k = k0; k < k1; k++, c += sxy) {
+        const float bz_hi = (k < nz - 1) ? narrow(bz[c + sxy]) : 0.0f;
+        const float x = narrow(bx[c]), y = narrow(by[c]);
+        out.bx[c] = x;
+        out.by[c] = y;
+        out.bz[c] = bz_lo;
+        if (sf.bx) {
+            const size_t e = split_slot(c, (j + k) & 1, half);
+            sf.bx[e] = x;
+            sf.by[e] = y;
+            sf.bz[e] = bz_lo;
+        }
+        float t = x;
+        t += (i < nx - 1) ? narrow(bx[c + 1]) : 0.0f;
+        t += y;
+        t += (j < ny - 1) ? narrow(by[c + nx]) : 0.0f;
+        t += bz_lo;
+        t += bz_hi;
+        bz_lo = bz_hi;
+        float q = 0.0f;
+        if (t > 0.0f) {
+            if (!same_bits(t, s_last)) {
+                s_last = t;
+                q_last = div_call(1.0f, t);
+            }
+            q = q_last;
+        }
+        out.dinv[c] = q;
+    }
+}
+
 __global__ void k_to_f32_layout(unsigned n, const double *__restrict__ src, float *__restrict__ dst, Split sp)
 {
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
@@ -2437,8 +2477,17 @@ cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *di
 }
 template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *,
                                              cudaStream_t, const LevelArrays<double> *, double, uint8_t *, double *);
-template cudaError_t launch_diag_inv<float>(Dims, const float *, const float *, const float *, float *, cudaStream_t,
-                                            const LevelArrays<float> *, float, uint8_t *, double *);
+
+cudaError_t launch_level_f32(Dims d, const LevelArrays<double> &L, LevelArrays<float> &out, cudaStream_t s,
+                             LevelArrays<float> *sf, Split sp)
+{
+    note_launch();
+    const bool split = sf && sf->bx && sp.half;
+    k_level_f32<<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, L.bx, L.by, L.bz, out,
+                                                                     split ? *sf : LevelArrays<float>{},
+                                                                     split ? sp.half : 0);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_restrict_coeffs(Dims f, const double *bx, const double *by, const double *bz, double *cbx,
                                    double *cby, double *cbz, cudaStream_t s)
@@ -2446,13 +2495,6 @@ cudaError_t launch_restrict_coeffs(Dims f, const double *bx, const double *by, c
     note_launch();
     k_restrict_coeffs<<<row_grid(f.nx / 2, f.ny / 2, f.nz / 2), kRowThreads, 0, s>>>(f.nx, f.ny, f.nz, bx, by, bz, cbx,
                                                                                       cby, cbz);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cast_f32(size_t n, const double *src, float *dst, cudaStream_t s)
-{
-    note_launch();
-    k_cast_f32<<<red_grid(n), kRedThreads, 0, s>>>(n, src, dst);
     return cudaGetLastError();
 }
 
