@@ -213,7 +213,7 @@ __device__ __forceinline__ bool zero_bits(float x) { return (__float_as_int(x) <
 enum CheckKernel : unsigned {
     CK_SMOOTH = 1, CK_SMOOTH_SPLIT, CK_SMOOTH_SPLIT4, CK_RESTRICT, CK_RESTRICT_PAIRS, CK_PROLONG, CK_COARSE_SOLVE,
     CK_TAIL, CK_RESID, CK_SPLIT_SLOT, CK_PCG_APPLY, CK_DIVERGENCE, CK_CORRECT, CK_ADJOINT, CK_PHI_GRAD,
-    CK_FACE_COEFFS, CK_DIAG_INV, CK_MOMENTUM, CK_LABEL, CK_VOF, CK_NARROW
+    CK_FACE_COEFFS, CK_DIAG_INV, CK_MOMENTUM, CK_LABEL, CK_VOF, CK_NARROW, CK_POW2
 };
 #ifdef MGP_CHECK
 __device__ unsigned long long g_check_first = 0;  // kernel id << 48 | (index & (2^48 - 1)); 0: none
@@ -266,6 +266,33 @@ __device__ __forceinline__ float narrow(double x)
 #endif
     return f;
 }
+
+// x * f for f = 2^e, bit for bit the product __dmul_rn(x, f), on the integer pipe where x and the
+// product are normal numbers: e added to the exponent field (the FP64 unit is the limiting
+// resource of the FP64 set-up and projection passes).  Zeros, subnormals, infinities, NaNs and
+// products outside the normal range take the multiply.  The check build compares every result
+// with the multiply.
+__device__ __forceinline__ double mul_pow2(double x, double f, int e)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int ex = (hi >> 20) & 0x7ff;
+    double y;
+    if ((unsigned)(ex - 1) < 2046u && (unsigned)(ex + e - 1) < 2046u)
+        y = __hiloint2double(hi + e * (1 << 20), lo);
+    else
+        y = __dmul_rn(x, f);
+#ifdef MGP_CHECK
+    if (__double_as_longlong(y) != __double_as_longlong(__dmul_rn(x, f)) && !isnan(x))
+        ck_record(CK_POW2, (long long)((unsigned long long)__double_as_longlong(x) >> 16));
+#endif
+    return y;
+}
+// a power-of-two factor (ok: f = 2^e) or any other (ok = 0: a multiply)
+struct Scale2 {
+    double f;
+    int e, ok;
+};
+__device__ __forceinline__ double mul_s2(double x, const Scale2 &s) { return s.ok ? mul_pow2(x, s.f, s.e) : __dmul_rn(x, s.f); }
 
 // cell c = (i, j, k) and the neighbours its guards admit (i > 0: c - 1, i < nx - 1: c + 1, ...)
 // inside the nx*ny*nz cells
@@ -340,12 +367,13 @@ __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__
 
 // dinv = 1 / (sum of the six face coefficients), summed x-, x+, y-, y+, z-, z+; 0 if none is
 // open.  Optionally (op != null) the CG operator's arrays scaled by `scale` = h^-2: op->dinv =
-// scale * sum, op->bx/by/bz = scale * the faces.  kRun cells per thread with the divisor memo above.
+// scale * sum, op->bx/by/bz = scale * the faces (mul_s2: the products, on the integer pipe when
+// h^-2 is a power of two).  kRun cells per thread with the divisor memo above.
 template <typename T>
 // open (optional): per cell the open bits of its three low faces (x 1, y 2, z 4), kept from the
 // last call; where they change, *changed = 1 (the fluid regions must be labelled again)
 __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, const T *__restrict__ by,
-                           const T *__restrict__ bz, T *__restrict__ dinv, LevelArrays<T> op, T scale,
+                           const T *__restrict__ bz, T *__restrict__ dinv, LevelArrays<T> op, Scale2 scale,
                            uint8_t *__restrict__ open, double *__restrict__ changed)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -364,10 +392,10 @@ __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, con
         s += bz_lo;
         s += bz_hi;
         if (op.dinv) {
-            op.dinv[c] = s * scale;
-            op.bx[c] = bx[c] * scale;
-            op.by[c] = by[c] * scale;
-            op.bz[c] = bz_lo * scale;
+            op.dinv[c] = mul_s2(s, scale);
+            op.bx[c] = mul_s2(bx[c], scale);
+            op.by[c] = mul_s2(by[c], scale);
+            op.bz[c] = mul_s2(bz_lo, scale);
         }
         if (open) {
             const uint8_t bits = (uint8_t)((pos_bits(bx[c]) ? 1 : 0) | (pos_bits(by[c]) ? 2 : 0) | (pos_bits(bz_lo) ? 4 : 0));
@@ -1442,7 +1470,7 @@ __global__ void k_from_f32_layout(unsigned n, const float *__restrict__ src, dou
 // ---------------------------------------------------------------------------
 // Projection (Eq. poisson1 right-hand side; Eq. runge1 correction) and adjoint
 // ---------------------------------------------------------------------------
-__global__ void k_divergence(int nx, int ny, int nz, double scale, const double *__restrict__ bx,
+__global__ void k_divergence(int nx, int ny, int nz, Scale2 scale, const double *__restrict__ bx,
                              const double *__restrict__ by, const double *__restrict__ bz,
                              const double *__restrict__ ux, const double *__restrict__ uy,
                              const double *__restrict__ uz, double *__restrict__ rhs)
@@ -1452,14 +1480,20 @@ __global__ void k_divergence(int nx, int ny, int nz, double scale, const double 
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_DIVERGENCE)) return;
+    // every load first (a velocity's load does not wait for its face's coefficient)
+    const bool xh = i < nx - 1, yh = j < ny - 1, zh = k < nz - 1;
+    const double bx0 = bx[c], bx1 = xh ? bx[c + 1] : 0.0, by0 = by[c], by1 = yh ? by[c + nx] : 0.0;
+    const double bz0 = bz[c], bz1 = zh ? bz[c + sxy] : 0.0;
+    const double ux0 = ux[c], ux1 = xh ? ux[c + 1] : 0.0, uy0 = uy[c], uy1 = yh ? uy[c + nx] : 0.0;
+    const double uz0 = uz[c], uz1 = zh ? uz[c + sxy] : 0.0;
     double d = 0.0;
-    if (i < nx - 1 && pos_bits(bx[c + 1])) d += ux[c + 1];
-    if (pos_bits(bx[c])) d -= ux[c];
-    if (j < ny - 1 && pos_bits(by[c + nx])) d += uy[c + nx];
-    if (pos_bits(by[c])) d -= uy[c];
-    if (k < nz - 1 && pos_bits(bz[c + sxy])) d += uz[c + sxy];
-    if (pos_bits(bz[c])) d -= uz[c];
-    rhs[c] = scale * d;
+    if (pos_bits(bx1)) d += ux1;
+    if (pos_bits(bx0)) d -= ux0;
+    if (pos_bits(by1)) d += uy1;
+    if (pos_bits(by0)) d -= uy0;
+    if (pos_bits(bz1)) d += uz1;
+    if (pos_bits(bz0)) d -= uz0;
+    rhs[c] = mul_s2(d, scale);  // scale * d
 }
 
 // ---------------------------------------------------------------------------
@@ -1802,16 +1836,16 @@ __global__ void k_divergence_area(int nx, int ny, int nz, double scale, LevelArr
 }
 
 // u_f = u*_f - dt beta_f (p_c - p_nb) / h on open low faces; closed faces copy u*.
-// x / h, rounded once: a multiply by 1/h when h is a power of two (then x * (1/h) is exact and
-// equal to the quotient), an IEEE division otherwise
-__device__ __forceinline__ double div_h(double x, double h, double inv_h, bool pow2)
+// x / h, rounded once: a multiply by ih = 1/h when h is a power of two (then x * (1/h) is exact
+// and equal to the quotient; mul_pow2), an IEEE division otherwise
+__device__ __forceinline__ double div_h(double x, double h, const Scale2 &ih)
 {
-    return pow2 ? __dmul_rn(x, inv_h) : div_call(x, h);
+    return ih.ok ? mul_pow2(x, ih.f, ih.e) : div_call(x, h);
 }
 
 // The face is open where b > 0; its coefficient is val (1/rho when b holds area * 1/rho), or b
 // itself when val is null.
-__global__ void k_correct(int nx, int ny, int nz, double dt, double h, double inv_h, int pow2,
+__global__ void k_correct(int nx, int ny, int nz, double dt, double h, Scale2 ih,
                           const double *__restrict__ bx, const double *__restrict__ by, const double *__restrict__ bz,
                           const double *__restrict__ p, const double *ux0, const double *uy0, const double *uz0,
                           double *ux, double *uy, double *uz, LevelArrays<double> val)
@@ -1821,20 +1855,19 @@ __global__ void k_correct(int nx, int ny, int nz, double dt, double h, double in
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_CORRECT)) return;
-    const double pc = p[c];
-    double b = bx[c], u = ux0[c], bv = val.bx ? val.bx[c] : b;
-    if (i > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - 1])), h, inv_h, pow2));
-    ux[c] = u;
-    b = by[c];
-    u = uy0[c];
-    bv = val.by ? val.by[c] : b;
-    if (j > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - nx])), h, inv_h, pow2));
-    uy[c] = u;
-    b = bz[c];
-    u = uz0[c];
-    bv = val.bz ? val.bz[c] : b;
-    if (k > 0 && pos_bits(b)) u = __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, p[c - sxy])), h, inv_h, pow2));
-    uz[c] = u;
+    // every load first; each face's update formed and kept where the face is open (the same
+    // operations as forming it there alone)
+    const double pc = p[c], pxl = i > 0 ? p[c - 1] : 0.0, pyl = j > 0 ? p[c - nx] : 0.0;
+    const double pzl = k > 0 ? p[c - sxy] : 0.0;
+    const double b0 = bx[c], b1 = by[c], b2 = bz[c];
+    const double u0 = ux0[c], u1 = uy0[c], u2 = uz0[c];
+    const double v0 = val.bx ? val.bx[c] : b0, v1 = val.by ? val.by[c] : b1, v2 = val.bz ? val.bz[c] : b2;
+    auto upd = [&](double u, double bv, double pn) {
+        return __dsub_rn(u, div_h(__dmul_rn(__dmul_rn(dt, bv), __dsub_rn(pc, pn)), h, ih));
+    };
+    ux[c] = (i > 0 && pos_bits(b0)) ? upd(u0, v0, pxl) : u0;
+    uy[c] = (j > 0 && pos_bits(b1)) ? upd(u1, v1, pyl) : u1;
+    uz[c] = (k > 0 && pos_bits(b2)) ? upd(u2, v2, pzl) : u2;
 }
 
 __global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double *__restrict__ by,
@@ -1851,24 +1884,22 @@ __global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double
 
 // grad_u = w - G q (open faces) / w (closed);  grad_beta = dt (G p)((G q) - w) (open) / 0 (closed)
 // a: the face's open area (fractional areas), or null
+// has_a: the face's open area a multiplies G q (fractional areas)
 __device__ __forceinline__ void adj_face(double b, double pc, double pn, double qc, double qn, double w, double h,
-                                         double inv_h, bool pow2, double dt, const double *a, size_t c, double &gu,
-                                         double &gb)
+                                         const Scale2 &ih, double dt, bool has_a, double a, double &gu, double &gb)
 {
-    if (pos_bits(b)) {
-        double gq = div_h(__dsub_rn(qc, qn), h, inv_h, pow2);
-        const double gp = div_h(__dsub_rn(pc, pn), h, inv_h, pow2);
-        if (a) gq = __dmul_rn(a[c], gq);
-        gu = __dsub_rn(w, gq);
-        // (Gq - w) is -gu exactly: a rounded difference changes sign with its operands' order
-        gb = __dmul_rn(__dmul_rn(dt, gp), -gu);
-    } else {
-        gu = w;
-        gb = 0.0;
-    }
+    double gq = div_h(__dsub_rn(qc, qn), h, ih);
+    const double gp = div_h(__dsub_rn(pc, pn), h, ih);
+    if (has_a) gq = __dmul_rn(a, gq);
+    const double go = __dsub_rn(w, gq);
+    // (Gq - w) is -gu exactly: a rounded difference changes sign with its operands' order
+    const double bo = __dmul_rn(__dmul_rn(dt, gp), -go);
+    const bool open = pos_bits(b);
+    gu = open ? go : w;
+    gb = open ? bo : 0.0;
 }
 
-__global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double inv_h, int pow2, double dt,
+__global__ void k_adjoint_faces(int nx, int ny, int nz, double h, Scale2 ih, double dt,
                                 const double *__restrict__ bx,
                                 const double *__restrict__ by, const double *__restrict__ bz,
                                 const double *__restrict__ p, const double *__restrict__ q,
@@ -1881,41 +1912,76 @@ __global__ void k_adjoint_faces(int nx, int ny, int nz, double h, double inv_h, 
     const size_t sxy = (size_t)nx * ny;
     const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
     if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_ADJOINT)) return;
+    // every load first
     const double pc = p[c], qc = q[c];
+    const double pxl = i > 0 ? p[c - 1] : 0.0, qxl = i > 0 ? q[c - 1] : 0.0;
+    const double pyl = j > 0 ? p[c - nx] : 0.0, qyl = j > 0 ? q[c - nx] : 0.0;
+    const double pzl = k > 0 ? p[c - sxy] : 0.0, qzl = k > 0 ? q[c - sxy] : 0.0;
+    const double b0 = bx[c], b1 = by[c], b2 = bz[c], w0 = wx[c], w1 = wy[c], w2 = wz[c];
+    const double a0 = area.bx ? area.bx[c] : 1.0, a1 = area.by ? area.by[c] : 1.0, a2 = area.bz ? area.bz[c] : 1.0;
     double gu, gb;
-    adj_face(bx[c], pc, i > 0 ? p[c - 1] : 0.0, qc, i > 0 ? q[c - 1] : 0.0, wx[c], h, inv_h, pow2, dt, area.bx, c, gu,
-             gb);
+    adj_face(b0, pc, pxl, qc, qxl, w0, h, ih, dt, area.bx != nullptr, a0, gu, gb);
     gux[c] = gu;
     if (gbx) gbx[c] = gb;
-    adj_face(by[c], pc, j > 0 ? p[c - nx] : 0.0, qc, j > 0 ? q[c - nx] : 0.0, wy[c], h, inv_h, pow2, dt, area.by, c,
-             gu, gb);
+    adj_face(b1, pc, pyl, qc, qyl, w1, h, ih, dt, area.by != nullptr, a1, gu, gb);
     guy[c] = gu;
     if (gby) gby[c] = gb;
-    adj_face(bz[c], pc, k > 0 ? p[c - sxy] : 0.0, qc, k > 0 ? q[c - sxy] : 0.0, wz[c], h, inv_h, pow2, dt, area.bz,
-             c, gu, gb);
+    adj_face(b2, pc, pzl, qc, qzl, w2, h, ih, dt, area.bz != nullptr, a2, gu, gb);
     guz[c] = gu;
     if (gbz) gbz[c] = gb;
 }
 
-// grad_phi_c = -(drho/2) sum over the six faces of beta_f^2 grad_beta_f (order x-,x+,y-,y+,z-,z+)
+// grad_phi_c = -(drho/2) sum over the six faces of beta_f^2 grad_beta_f (order x-,x+,y-,y+,z-,z+).
+// A block of W x R threads covers R rows of W cells (W: nx rounded up to a warp multiple, at most
+// kPhiW) and walks kPhiRun planes up z.  Each face's product (beta_f beta_f) grad_beta_f is formed
+// once: every cell forms those of its x- and y- faces and of the z- face of the cell above; the
+// x+ and y+ products are the neighbours' (shared memory, two buffers by plane parity), formed again
+// only at the block's right edge and top row, and the z+ product is carried up as the next cell's
+// z- product.  The same products summed in the same order as forming all six per cell (0 + t is
+// t but for -0; NaN payloads aside).
+constexpr int kPhiW = 512, kPhiThreads = 512, kPhiRun = 8;
 __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const double *__restrict__ bx,
                            const double *__restrict__ by, const double *__restrict__ bz,
                            const double *__restrict__ gbx, const double *__restrict__ gby,
                            const double *__restrict__ gbz, double *__restrict__ gphi)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= nx) return;
+    __shared__ double sh[2][2][kPhiThreads];  // [plane parity][x- / y- product][thread]
+    const int W = blockDim.x, R = blockDim.y;
+    const int i = blockIdx.x * W + threadIdx.x, j = blockIdx.y * R + threadIdx.y;
+    const int t = threadIdx.y * W + threadIdx.x;
+    const bool in = i < nx && j < ny;
+    const int k0 = blockIdx.z * kPhiRun, k1 = min(k0 + kPhiRun, nz);
     const size_t sxy = (size_t)nx * ny;
-    const size_t c = (size_t)k * sxy + (size_t)j * nx + i;
-    if (!ck_cell((long long)c, i, j, k, nx, ny, nz, CK_PHI_GRAD)) return;
-    double s = 0.0;
-    s = __dadd_rn(s, __dmul_rn(__dmul_rn(bx[c], bx[c]), gbx[c]));
-    if (i < nx - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(bx[c + 1], bx[c + 1]), gbx[c + 1]));
-    s = __dadd_rn(s, __dmul_rn(__dmul_rn(by[c], by[c]), gby[c]));
-    if (j < ny - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(by[c + nx], by[c + nx]), gby[c + nx]));
-    s = __dadd_rn(s, __dmul_rn(__dmul_rn(bz[c], bz[c]), gbz[c]));
-    if (k < nz - 1) s = __dadd_rn(s, __dmul_rn(__dmul_rn(bz[c + sxy], bz[c + sxy]), gbz[c + sxy]));
-    gphi[c] = __dmul_rn(neg_half_drho, s);
+    auto prod = [](double b, double g) { return __dmul_rn(__dmul_rn(b, b), g); };
+    size_t c = in ? (size_t)k0 * sxy + (size_t)j * nx + i : 0;
+    const bool ok0 = in && ck_cell((long long)c, i, j, k0, nx, ny, nz, CK_PHI_GRAD);
+    double tz_lo = ok0 ? prod(bz[c], gbz[c]) : 0.0;
+    for (int k = k0; k < k1; k++, c += sxy) {
+        const bool ok = in && ck_cell((long long)c, i, j, k, nx, ny, nz, CK_PHI_GRAD);
+        double tx = 0.0, ty = 0.0, tz_hi = 0.0;
+        if (ok) {
+            tx = prod(bx[c], gbx[c]);
+            ty = prod(by[c], gby[c]);
+            if (k < nz - 1) tz_hi = prod(bz[c + sxy], gbz[c + sxy]);
+        }
+        double(*buf)[kPhiThreads] = sh[k & 1];
+        buf[0][t] = tx;
+        buf[1][t] = ty;
+        __syncthreads();  // one barrier per plane: a buffer is written again two planes later
+        if (ok) {
+            double tx_hi = 0.0, ty_hi = 0.0;
+            if (i < nx - 1) tx_hi = threadIdx.x < W - 1 ? buf[0][t + 1] : prod(bx[c + 1], gbx[c + 1]);
+            if (j < ny - 1) ty_hi = threadIdx.y < R - 1 ? buf[1][t + W] : prod(by[c + nx], gby[c + nx]);
+            double s = (__double_as_longlong(tx) << 1) == 0 ? 0.0 : tx;  // 0 + tx
+            if (i < nx - 1) s = __dadd_rn(s, tx_hi);
+            s = __dadd_rn(s, ty);
+            if (j < ny - 1) s = __dadd_rn(s, ty_hi);
+            s = __dadd_rn(s, tz_lo);
+            if (k < nz - 1) s = __dadd_rn(s, tz_hi);
+            gphi[c] = __dmul_rn(neg_half_drho, s);
+        }
+        tz_lo = tz_hi;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2417,6 +2483,21 @@ __global__ void k_comp_center(unsigned n, const double *__restrict__ v, const in
     }
 }
 
+// f as a Scale2 (ok when f = 2^e)
+inline Scale2 scale2(double f)
+{
+    int ex;
+    const bool ok = std::frexp(f, &ex) == 0.5;
+    return Scale2{f, ex - 1, ok ? 1 : 0};
+}
+// 1/h as a Scale2 for div_h: ok when h is a power of two (h = 2^(ex-1), 1/h = 2^(1-ex) exactly)
+inline Scale2 inv_scale2(double h)
+{
+    int ex;
+    const bool ok = std::frexp(h, &ex) == 0.5;
+    return Scale2{1.0 / h, 1 - ex, ok ? 1 : 0};
+}
+
 inline dim3 row_grid(int threads_x, int ny, int nz)
 {
     return dim3((unsigned)((threads_x + kRowThreads - 1) / kRowThreads), (unsigned)ny, (unsigned)nz);
@@ -2471,8 +2552,8 @@ cudaError_t launch_diag_inv(Dims d, const T *bx, const T *by, const T *bz, T *di
 {
     note_launch();
     k_diag_inv<T><<<run_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, bx, by, bz, dinv,
-                                                                      op ? *op : LevelArrays<T>{}, scale, open,
-                                                                      changed);
+                                                                      op ? *op : LevelArrays<T>{},
+                                                                      scale2((double)scale), open, changed);
     return cudaGetLastError();
 }
 template cudaError_t launch_diag_inv<double>(Dims, const double *, const double *, const double *, double *,
@@ -2805,7 +2886,7 @@ cudaError_t launch_divergence(Dims d, double scale, const double *bx, const doub
                               const double *ux, const double *uy, const double *uz, double *rhs, cudaStream_t s)
 {
     note_launch();
-    k_divergence<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, scale, bx, by, bz, ux, uy, uz,
+    k_divergence<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, scale2(scale), bx, by, bz, ux, uy, uz,
                                                                      rhs);
     return cudaGetLastError();
 }
@@ -2815,9 +2896,7 @@ cudaError_t launch_correct(Dims d, double dt, double h, const double *bx, const 
                            double *uy, double *uz, cudaStream_t s, const LevelArrays<double> *val)
 {
     note_launch();
-    int ex;
-    const bool pow2 = std::frexp(h, &ex) == 0.5;
-    k_correct<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, dt, h, 1.0 / h, pow2, bx, by, bz, p,
+    k_correct<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, dt, h, inv_scale2(h), bx, by, bz, p,
                                                                   ux0, uy0, uz0, ux, uy, uz,
                                                                   val ? *val : LevelArrays<double>{});
     return cudaGetLastError();
@@ -2923,9 +3002,7 @@ cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, 
                                  double *gbz, cudaStream_t s, const LevelArrays<double> *area)
 {
     note_launch();
-    int ex;
-    const bool pow2 = std::frexp(h, &ex) == 0.5;
-    k_adjoint_faces<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h, 1.0 / h, pow2, dt, bx, by,
+    k_adjoint_faces<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, h, inv_scale2(h), dt, bx, by,
                                                                         bz, p, q, wx, wy, wz, gux, guy, guz, gbx, gby,
                                                                         gbz, area ? *area : LevelArrays<double>{});
     return cudaGetLastError();
@@ -2935,8 +3012,11 @@ cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, cons
                             const double *gbx, const double *gby, const double *gbz, double *gphi, cudaStream_t s)
 {
     note_launch();
-    k_phi_grad<<<row_grid(d.nx, d.ny, d.nz), kRowThreads, 0, s>>>(d.nx, d.ny, d.nz, neg_half_drho, bx, by, bz, gbx,
-                                                                   gby, gbz, gphi);
+    // W x R threads: a row (rounded up to whole warps, at most kPhiW cells) by as many rows as fit
+    const int W = std::min((d.nx + 31) / 32 * 32, kPhiW), R = std::max(1, std::min(kPhiThreads / W, d.ny));
+    const dim3 grid((unsigned)((d.nx + W - 1) / W), (unsigned)((d.ny + R - 1) / R), (unsigned)((d.nz + kPhiRun - 1) / kPhiRun));
+    k_phi_grad<<<grid, dim3((unsigned)W, (unsigned)R), 0, s>>>(d.nx, d.ny, d.nz, neg_half_drho, bx, by, bz, gbx, gby,
+                                                               gbz, gphi);
     return cudaGetLastError();
 }
 
