@@ -327,12 +327,30 @@ __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__
     size_t c = (size_t)k0 * sxy + (size_t)j * nx + i;
     bool s_below = k0 > 0 && solid && solid[c - sxy];
     double r_below = k0 > 0 ? __dadd_rn(rho_a, __dmul_rn(drho, phi[c - sxy])) : 0.0;
+    // a cell's inputs (phi and the solid flags of the cell and its x- and y- neighbours), all
+    // loaded at once; the next cell's are loaded before this one's faces are formed and stored
+    struct In {
+        double pc, px, py;
+        bool sc, sx, sy;
+    };
+    auto load = [&](size_t cc) {
+        In v;
+        v.pc = phi[cc];
+        v.px = i > 0 ? phi[cc - 1] : 0.0;
+        v.py = j > 0 ? phi[cc - nx] : 0.0;
+        v.sc = solid && solid[cc];
+        v.sx = solid && i > 0 && solid[cc - 1];
+        v.sy = solid && j > 0 && solid[cc - nx];
+        return v;
+    };
+    In cur = load(c);
     for (int k = k0; k < k1; k++, c += sxy) {
-        const bool sc = solid && solid[c];
-        const double rc = __dadd_rn(rho_a, __dmul_rn(drho, phi[c]));
+        const In nxt = k + 1 < k1 ? load(c + sxy) : cur;
+        const bool sc = cur.sc;
+        const double rc = __dadd_rn(rho_a, __dmul_rn(drho, cur.pc));
         double v = 0.0;
-        if (i > 0 && !sc && !(solid && solid[c - 1])) {
-            const double den = __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - 1])), rc);
+        if (i > 0 && !sc && !cur.sx) {
+            const double den = __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, cur.px)), rc);
             if (!same_bits(den, dx_last)) {
                 dx_last = den;
                 qx_last = div_call(2.0, den);
@@ -341,8 +359,8 @@ __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__
         }
         bx[c] = v;
         v = 0.0;
-        if (j > 0 && !sc && !(solid && solid[c - nx])) {
-            const double den = __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, phi[c - nx])), rc);
+        if (j > 0 && !sc && !cur.sy) {
+            const double den = __dadd_rn(__dadd_rn(rho_a, __dmul_rn(drho, cur.py)), rc);
             if (!same_bits(den, dy_last)) {
                 dy_last = den;
                 qy_last = div_call(2.0, den);
@@ -362,6 +380,7 @@ __global__ void k_face_coeffs(int nx, int ny, int nz, const double *__restrict__
         bz[c] = v;
         s_below = sc;
         r_below = rc;
+        cur = nxt;
     }
 }
 
@@ -383,27 +402,45 @@ __global__ void k_diag_inv(int nx, int ny, int nz, const T *__restrict__ bx, con
     T s_last = T(1), q_last = T(1);
     size_t c = (size_t)k0 * sxy + (size_t)j * nx + i;
     T bz_lo = bz[c];
+    // a cell's loads at once; the next cell's issued before this one's stores
+    struct In {
+        T x0, x1, y0, y1, zh;
+        uint8_t ob;
+    };
+    auto load = [&](size_t cc, int kk) {
+        In v;
+        v.x0 = bx[cc];
+        v.x1 = (i < nx - 1) ? bx[cc + 1] : T(0);
+        v.y0 = by[cc];
+        v.y1 = (j < ny - 1) ? by[cc + nx] : T(0);
+        v.zh = (kk < nz - 1) ? bz[cc + sxy] : T(0);
+        v.ob = open ? open[cc] : 0;
+        return v;
+    };
+    In cur = load(c, k0);
     for (int k = k0; k < k1; k++, c += sxy) {
-        const T bz_hi = (k < nz - 1) ? bz[c + sxy] : T(0);
-        T s = bx[c];
-        s += (i < nx - 1) ? bx[c + 1] : T(0);
-        s += by[c];
-        s += (j < ny - 1) ? by[c + nx] : T(0);
+        const In nxt = k + 1 < k1 ? load(c + sxy, k + 1) : cur;
+        const T bz_hi = cur.zh;
+        T s = cur.x0;
+        s += cur.x1;
+        s += cur.y0;
+        s += cur.y1;
         s += bz_lo;
         s += bz_hi;
         if (op.dinv) {
             op.dinv[c] = mul_s2(s, scale);
-            op.bx[c] = mul_s2(bx[c], scale);
-            op.by[c] = mul_s2(by[c], scale);
+            op.bx[c] = mul_s2(cur.x0, scale);
+            op.by[c] = mul_s2(cur.y0, scale);
             op.bz[c] = mul_s2(bz_lo, scale);
         }
         if (open) {
-            const uint8_t bits = (uint8_t)((pos_bits(bx[c]) ? 1 : 0) | (pos_bits(by[c]) ? 2 : 0) | (pos_bits(bz_lo) ? 4 : 0));
-            if (open[c] != bits) {
+            const uint8_t bits = (uint8_t)((pos_bits(cur.x0) ? 1 : 0) | (pos_bits(cur.y0) ? 2 : 0) | (pos_bits(bz_lo) ? 4 : 0));
+            if (cur.ob != bits) {
                 open[c] = bits;
                 *changed = 1.0;
             }
         }
+        cur = nxt;
         bz_lo = bz_hi;
         T q = T(0);
         if (s > T(0)) {
@@ -1419,9 +1456,24 @@ __global__ void k_level_f32(int nx, int ny, int nz, const double *__restrict__ b
     float s_last = 1.0f, q_last = 1.0f;
     size_t c = (size_t)k0 * sxy + (size_t)j * nx + i;
     float bz_lo = narrow(bz[c]);
+    // a cell's loads at once; the next cell's issued before this one's stores
+    struct In {
+        double x0, x1, y0, y1, zh;
+    };
+    auto load = [&](size_t cc, int kk) {
+        In v;
+        v.x0 = bx[cc];
+        v.x1 = (i < nx - 1) ? bx[cc + 1] : 0.0;
+        v.y0 = by[cc];
+        v.y1 = (j < ny - 1) ? by[cc + nx] : 0.0;
+        v.zh = (kk < nz - 1) ? bz[cc + sxy] : 0.0;
+        return v;
+    };
+    In cur = load(c, k0);
     for (int k = k0; k < k1; k++, c += sxy) {
-        const float bz_hi = (k < nz - 1) ? narrow(bz[c + sxy]) : 0.0f;
-        const float x = narrow(bx[c]), y = narrow(by[c]);
+        const In nxt = k + 1 < k1 ? load(c + sxy, k + 1) : cur;
+        const float bz_hi = narrow(cur.zh);
+        const float x = narrow(cur.x0), y = narrow(cur.y0);
         out.bx[c] = x;
         out.by[c] = y;
         out.bz[c] = bz_lo;
@@ -1432,12 +1484,13 @@ __global__ void k_level_f32(int nx, int ny, int nz, const double *__restrict__ b
             sf.bz[e] = bz_lo;
         }
         float t = x;
-        t += (i < nx - 1) ? narrow(bx[c + 1]) : 0.0f;
+        t += narrow(cur.x1);
         t += y;
-        t += (j < ny - 1) ? narrow(by[c + nx]) : 0.0f;
+        t += narrow(cur.y1);
         t += bz_lo;
         t += bz_hi;
         bz_lo = bz_hi;
+        cur = nxt;
         float q = 0.0f;
         if (t > 0.0f) {
             if (!same_bits(t, s_last)) {
