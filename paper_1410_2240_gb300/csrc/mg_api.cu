@@ -1478,12 +1478,10 @@ int mg_project_adjoint(mg_ctx *c, const double *const w[3], const double *p, dou
         CK(cudaMemsetAsync(q, 0, n * sizeof(double), c->s));
     }
     const LevelArrays<double> &L = c->L64[0];
-    // beta * w into grad_u (used as scratch), then c = D(beta w); beta = 1/rho (with fractional areas
-    // the operator's coefficient is area * 1/rho, and D sums the open faces without their areas)
+    // c = D(beta w), the products beta * w rounded once; beta = 1/rho (with fractional areas the
+    // operator's coefficient is area * 1/rho, and D sums the open faces without their areas)
     const LevelArrays<double> &B = c->has_area ? c->kbeta : L;
-    CK(mg::launch_face_mul(n, B.bx, B.by, B.bz, w[0], w[1], w[2], grad_u[0], grad_u[1], grad_u[2], c->s));
-    CK(mg::launch_divergence(c->dims[0], 1.0 / c->g.h, L.bx, L.by, L.bz, grad_u[0], grad_u[1], grad_u[2], c->rhs_tmp,
-                             c->s));
+    CK(mg::launch_divergence_mul(c->dims[0], 1.0 / c->g.h, L, B, w[0], w[1], w[2], c->rhs_tmp, c->s));
     const int st = c->o.krylov ? pcg_impl(c, c->rhs_tmp, q, tol, stats) : solve_impl(c, c->rhs_tmp, q, tol, stats);
     if (st != MG_OK && st != MG_ERR_NOT_CONVERGED && st != MG_ERR_INCOMPATIBLE) return st;
     const std::string keep = g_err;

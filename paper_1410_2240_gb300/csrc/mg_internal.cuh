@@ -271,9 +271,9 @@ cudaError_t launch_area_coeffs(size_t n, const LevelArrays<double> &area, const 
 cudaError_t launch_divergence_area(Dims d, double scale, const LevelArrays<double> &mask,
                                    const LevelArrays<double> &area, const LevelArrays<double> &u,
                                    const LevelArrays<double> &v, double *rhs, cudaStream_t s);
-cudaError_t launch_face_mul(size_t n, const double *bx, const double *by, const double *bz, const double *wx,
-                            const double *wy, const double *wz, double *ox, double *oy, double *oz,
-                            cudaStream_t s);
+// rhs = scale * sum over the open faces (L > 0) of +-(B w): the divergence of the face products
+cudaError_t launch_divergence_mul(Dims d, double scale, const LevelArrays<double> &L, const LevelArrays<double> &B,
+                                  const double *wx, const double *wy, const double *wz, double *rhs, cudaStream_t s);
 cudaError_t launch_adjoint_faces(Dims d, double h, double dt, const double *bx, const double *by,
                                  const double *bz, const double *p, const double *q, const double *wx,
                                  const double *wy, const double *wz, double *gux, double *guy, double *guz,

@@ -159,6 +159,9 @@ __device__ __forceinline__ void cell_of(unsigned idx, int nx, int ny, int &i, in
 // bits change: in a uniform region (pure air, pure water, constant coefficients) that is once
 // per run instead of once per cell, and the results are those of dividing every time.
 constexpr int kRun = 16;
+// Kernels that share face products along rows (k_phi_grad, k_divergence_mul): blocks of at most
+// kPhiThreads threads over rows of at most kPhiW cells, kPhiRun planes per block.
+constexpr int kPhiW = 512, kPhiThreads = 512, kPhiRun = 8;
 
 __device__ __forceinline__ bool same_bits(double a, double b)
 {
@@ -1923,20 +1926,65 @@ __global__ void k_correct(int nx, int ny, int nz, double dt, double h, Scale2 ih
     uz[c] = (k > 0 && pos_bits(b2)) ? upd(u2, v2, pzl) : u2;
 }
 
-__global__ void k_face_mul(size_t n, const double *__restrict__ bx, const double *__restrict__ by,
-                           const double *__restrict__ bz, const double *__restrict__ wx, const double *__restrict__ wy,
-                           const double *__restrict__ wz, double *__restrict__ ox, double *__restrict__ oy,
-                           double *__restrict__ oz)
+// rhs_c = scale * the sum over the open faces of c (L's coefficient > 0) of +-(B_f w_f), x+ added
+// and x- subtracted, then y, then z: the divergence (as k_divergence) of the face products B w,
+// each rounded once (the adjoint's right-hand side D(beta w)).  Blocks as k_phi_grad: each face's
+// product formed once, the x+ and y+ ones taken from the neighbours through shared memory (formed
+// again only at the block's right edge and top row), the z+ one carried up the column.
+__global__ void k_divergence_mul(int nx, int ny, int nz, Scale2 scale, LevelArrays<double> L, LevelArrays<double> B,
+                                 const double *__restrict__ wx, const double *__restrict__ wy,
+                                 const double *__restrict__ wz, double *__restrict__ rhs)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        ox[i] = __dmul_rn(bx[i], wx[i]);
-        oy[i] = __dmul_rn(by[i], wy[i]);
-        oz[i] = __dmul_rn(bz[i], wz[i]);
+    __shared__ double sh[2][2][kPhiThreads];  // [plane parity][x- / y- product][thread]
+    const int W = blockDim.x, R = blockDim.y;
+    const int i = blockIdx.x * W + threadIdx.x, j = blockIdx.y * R + threadIdx.y;
+    const int t = threadIdx.y * W + threadIdx.x;
+    const bool in = i < nx && j < ny;
+    const int k0 = blockIdx.z * kPhiRun, k1 = min(k0 + kPhiRun, nz);
+    const size_t sxy = (size_t)nx * ny;
+    size_t c = in ? (size_t)k0 * sxy + (size_t)j * nx + i : 0;
+    const bool ok0 = in && ck_cell((long long)c, i, j, k0, nx, ny, nz, CK_DIVERGENCE);
+    double tz_lo = ok0 ? __dmul_rn(B.bz[c], wz[c]) : 0.0;
+    bool oz_lo = ok0 && pos_bits(L.bz[c]);
+    for (int k = k0; k < k1; k++, c += sxy) {
+        const bool ok = in && ck_cell((long long)c, i, j, k, nx, ny, nz, CK_DIVERGENCE);
+        double tx = 0.0, ty = 0.0, tz_hi = 0.0;
+        bool ox0 = false, ox1 = false, oy0 = false, oy1 = false, oz1 = false;
+        if (ok) {
+            tx = __dmul_rn(B.bx[c], wx[c]);
+            ty = __dmul_rn(B.by[c], wy[c]);
+            ox0 = pos_bits(L.bx[c]);
+            oy0 = pos_bits(L.by[c]);
+            ox1 = i < nx - 1 && pos_bits(L.bx[c + 1]);
+            oy1 = j < ny - 1 && pos_bits(L.by[c + nx]);
+            if (k < nz - 1) {
+                tz_hi = __dmul_rn(B.bz[c + sxy], wz[c + sxy]);
+                oz1 = pos_bits(L.bz[c + sxy]);
+            }
+        }
+        double(*buf)[kPhiThreads] = sh[k & 1];
+        buf[0][t] = tx;
+        buf[1][t] = ty;
+        __syncthreads();  // one barrier per plane: a buffer is written again two planes later
+        if (ok) {
+            double tx_hi = 0.0, ty_hi = 0.0;
+            if (i < nx - 1) tx_hi = threadIdx.x < W - 1 ? buf[0][t + 1] : __dmul_rn(B.bx[c + 1], wx[c + 1]);
+            if (j < ny - 1) ty_hi = threadIdx.y < R - 1 ? buf[1][t + W] : __dmul_rn(B.by[c + nx], wy[c + nx]);
+            double d = 0.0;
+            if (ox1) d = __dadd_rn(d, tx_hi);
+            if (ox0) d = __dsub_rn(d, tx);
+            if (oy1) d = __dadd_rn(d, ty_hi);
+            if (oy0) d = __dsub_rn(d, ty);
+            if (oz1) d = __dadd_rn(d, tz_hi);
+            if (oz_lo) d = __dsub_rn(d, tz_lo);
+            rhs[c] = mul_s2(d, scale);  // scale * d
+        }
+        tz_lo = tz_hi;
+        oz_lo = oz1;
     }
 }
 
 // grad_u = w - G q (open faces) / w (closed);  grad_beta = dt (G p)((G q) - w) (open) / 0 (closed)
-// a: the face's open area (fractional areas), or null
 // has_a: the face's open area a multiplies G q (fractional areas)
 __device__ __forceinline__ void adj_face(double b, double pc, double pn, double qc, double qn, double w, double h,
                                          const Scale2 &ih, double dt, bool has_a, double a, double &gu, double &gb)
@@ -1992,7 +2040,6 @@ __global__ void k_adjoint_faces(int nx, int ny, int nz, double h, Scale2 ih, dou
 // only at the block's right edge and top row, and the z+ product is carried up as the next cell's
 // z- product.  The same products summed in the same order as forming all six per cell (0 + t is
 // t but for -0; NaN payloads aside).
-constexpr int kPhiW = 512, kPhiThreads = 512, kPhiRun = 8;
 __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const double *__restrict__ bx,
                            const double *__restrict__ by, const double *__restrict__ bz,
                            const double *__restrict__ gbx, const double *__restrict__ gby,
@@ -3041,11 +3088,22 @@ cudaError_t launch_divergence_area(Dims d, double scale, const LevelArrays<doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_face_mul(size_t n, const double *bx, const double *by, const double *bz, const double *wx,
-                            const double *wy, const double *wz, double *ox, double *oy, double *oz, cudaStream_t s)
+// blocks of the kernels that share face products along rows (k_phi_grad, k_divergence_mul): W x R
+// threads, a row rounded up to whole warps (at most kPhiW cells) by as many rows as fit
+inline void row_share_grid(Dims d, dim3 &grid, dim3 &block)
+{
+    const int W = std::min((d.nx + 31) / 32 * 32, kPhiW), R = std::max(1, std::min(kPhiThreads / W, d.ny));
+    grid = dim3((unsigned)((d.nx + W - 1) / W), (unsigned)((d.ny + R - 1) / R), (unsigned)((d.nz + kPhiRun - 1) / kPhiRun));
+    block = dim3((unsigned)W, (unsigned)R);
+}
+
+cudaError_t launch_divergence_mul(Dims d, double scale, const LevelArrays<double> &L, const LevelArrays<double> &B,
+                                  const double *wx, const double *wy, const double *wz, double *rhs, cudaStream_t s)
 {
     note_launch();
-    k_face_mul<<<red_grid(n), kRedThreads, 0, s>>>(n, bx, by, bz, wx, wy, wz, ox, oy, oz);
+    dim3 grid, block;
+    row_share_grid(d, grid, block);
+    k_divergence_mul<<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, scale2(scale), L, B, wx, wy, wz, rhs);
     return cudaGetLastError();
 }
 
@@ -3065,11 +3123,9 @@ cudaError_t launch_phi_grad(Dims d, double neg_half_drho, const double *bx, cons
                             const double *gbx, const double *gby, const double *gbz, double *gphi, cudaStream_t s)
 {
     note_launch();
-    // W x R threads: a row (rounded up to whole warps, at most kPhiW cells) by as many rows as fit
-    const int W = std::min((d.nx + 31) / 32 * 32, kPhiW), R = std::max(1, std::min(kPhiThreads / W, d.ny));
-    const dim3 grid((unsigned)((d.nx + W - 1) / W), (unsigned)((d.ny + R - 1) / R), (unsigned)((d.nz + kPhiRun - 1) / kPhiRun));
-    k_phi_grad<<<grid, dim3((unsigned)W, (unsigned)R), 0, s>>>(d.nx, d.ny, d.nz, neg_half_drho, bx, by, bz, gbx, gby,
-                                                               gbz, gphi);
+    dim3 grid, block;
+    row_share_grid(d, grid, block);
+    k_phi_grad<<<grid, block, 0, s>>>(d.nx, d.ny, d.nz, neg_half_drho, bx, by, bz, gbx, gby, gbz, gphi);
     return cudaGetLastError();
 }
 
