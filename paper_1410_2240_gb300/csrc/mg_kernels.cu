@@ -275,6 +275,12 @@ __device__ __forceinline__ float narrow(double x)
 // resource of the FP64 set-up and projection passes).  Zeros, subnormals, infinities, NaNs and
 // products outside the normal range take the multiply.  The check build compares every result
 // with the multiply.
+// Products that only some lanes or launches need, as calls: the compiler cannot run a call
+// speculatively, so a branch around one is not if-converted into an FP64 instruction that every
+// warp issues (predicated off, it still occupies the FP64 unit).
+__device__ __noinline__ double dmul_call(double x, double f) { return __dmul_rn(x, f); }
+__device__ __noinline__ double sq_mul_call(double b, double g) { return __dmul_rn(__dmul_rn(b, b), g); }
+
 __device__ __forceinline__ double mul_pow2(double x, double f, int e)
 {
     const int hi = __double2hiint(x), lo = __double2loint(x);
@@ -283,7 +289,7 @@ __device__ __forceinline__ double mul_pow2(double x, double f, int e)
     if ((unsigned)(ex - 1) < 2046u && (unsigned)(ex + e - 1) < 2046u)
         y = __hiloint2double(hi + e * (1 << 20), lo);
     else
-        y = __dmul_rn(x, f);
+        y = dmul_call(x, f);
 #ifdef MGP_CHECK
     if (__double_as_longlong(y) != __double_as_longlong(__dmul_rn(x, f)) && !isnan(x))
         ck_record(CK_POW2, (long long)((unsigned long long)__double_as_longlong(x) >> 16));
@@ -295,7 +301,7 @@ struct Scale2 {
     double f;
     int e, ok;
 };
-__device__ __forceinline__ double mul_s2(double x, const Scale2 &s) { return s.ok ? mul_pow2(x, s.f, s.e) : __dmul_rn(x, s.f); }
+__device__ __forceinline__ double mul_s2(double x, const Scale2 &s) { return s.ok ? mul_pow2(x, s.f, s.e) : dmul_call(x, s.f); }
 
 // cell c = (i, j, k) and the neighbours its guards admit (i > 0: c - 1, i < nx - 1: c + 1, ...)
 // inside the nx*ny*nz cells
@@ -1968,8 +1974,8 @@ __global__ void k_divergence_mul(int nx, int ny, int nz, Scale2 scale, LevelArra
         __syncthreads();  // one barrier per plane: a buffer is written again two planes later
         if (ok) {
             double tx_hi = 0.0, ty_hi = 0.0;
-            if (i < nx - 1) tx_hi = threadIdx.x < W - 1 ? buf[0][t + 1] : __dmul_rn(B.bx[c + 1], wx[c + 1]);
-            if (j < ny - 1) ty_hi = threadIdx.y < R - 1 ? buf[1][t + W] : __dmul_rn(B.by[c + nx], wy[c + nx]);
+            if (i < nx - 1) tx_hi = threadIdx.x < W - 1 ? buf[0][t + 1] : dmul_call(B.bx[c + 1], wx[c + 1]);
+            if (j < ny - 1) ty_hi = threadIdx.y < R - 1 ? buf[1][t + W] : dmul_call(B.by[c + nx], wy[c + nx]);
             double d = 0.0;
             if (ox1) d = __dadd_rn(d, tx_hi);
             if (ox0) d = __dsub_rn(d, tx);
@@ -1991,7 +1997,7 @@ __device__ __forceinline__ void adj_face(double b, double pc, double pn, double 
 {
     double gq = div_h(__dsub_rn(qc, qn), h, ih);
     const double gp = div_h(__dsub_rn(pc, pn), h, ih);
-    if (has_a) gq = __dmul_rn(a, gq);
+    if (has_a) gq = dmul_call(a, gq);
     const double go = __dsub_rn(w, gq);
     // (Gq - w) is -gu exactly: a rounded difference changes sign with its operands' order
     const double bo = __dmul_rn(__dmul_rn(dt, gp), -go);
@@ -2070,8 +2076,8 @@ __global__ void k_phi_grad(int nx, int ny, int nz, double neg_half_drho, const d
         __syncthreads();  // one barrier per plane: a buffer is written again two planes later
         if (ok) {
             double tx_hi = 0.0, ty_hi = 0.0;
-            if (i < nx - 1) tx_hi = threadIdx.x < W - 1 ? buf[0][t + 1] : prod(bx[c + 1], gbx[c + 1]);
-            if (j < ny - 1) ty_hi = threadIdx.y < R - 1 ? buf[1][t + W] : prod(by[c + nx], gby[c + nx]);
+            if (i < nx - 1) tx_hi = threadIdx.x < W - 1 ? buf[0][t + 1] : sq_mul_call(bx[c + 1], gbx[c + 1]);
+            if (j < ny - 1) ty_hi = threadIdx.y < R - 1 ? buf[1][t + W] : sq_mul_call(by[c + nx], gby[c + nx]);
             double s = (__double_as_longlong(tx) << 1) == 0 ? 0.0 : tx;  // 0 + tx
             if (i < nx - 1) s = __dadd_rn(s, tx_hi);
             s = __dadd_rn(s, ty);
