@@ -159,6 +159,11 @@ __device__ __forceinline__ void cell_of(unsigned idx, int nx, int ny, int &i, in
 // bits change: in a uniform region (pure air, pure water, constant coefficients) that is once
 // per run instead of once per cell, and the results are those of dividing every time.
 constexpr int kRun = 16;
+// a compile-time bool as a value (a generic lambda's case)
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
 // Kernels that share face products along rows (k_phi_grad, k_divergence_mul): blocks of at most
 // kPhiThreads threads over rows of at most kPhiW cells, kPhiRun planes per block.
 constexpr int kPhiW = 512, kPhiThreads = 512, kPhiRun = 8;
@@ -2136,18 +2141,27 @@ __global__ void k_pcg_resid(int nx, int ny, int nz, double ih2, LevelArrays<doub
         return 1.0 / sc;
     });
     double rr = 0.0, sp = 0.0;
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const unsigned t = fdiv(idx, fnx), kk = fdiv(t, fny);
-        const int i = (int)(idx - t * (unsigned)nx), k = (int)kk, j = (int)(t - kk * (unsigned)ny);
-        const double v = pzero ? b[idx] : residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
-        r[idx] = v;
-        if (r32) {
-            const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
-            if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = narrow(v * inv_scale);
+    // one loop per case of the (grid-uniform) zero test: the zero case's loop holds no stencil
+    // arithmetic at all (a select inside one loop would still issue it)
+    auto run = [&](auto zero_tag) {
+        constexpr bool PZ = decltype(zero_tag)::value;
+        for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+            const unsigned t = fdiv(idx, fnx), kk = fdiv(t, fny);
+            const int i = (int)(idx - t * (unsigned)nx), k = (int)kk, j = (int)(t - kk * (unsigned)ny);
+            const double v = PZ ? b[idx] : residual64_at(i, j, k, idx, nx, ny, nz, sxy, ih2, L, b, p);
+            r[idx] = v;
+            if (r32) {
+                const size_t slot = half ? split_slot(idx, (j + k) & 1, half) : idx;
+                if (MG_CK(slot, slot, (long long)n, CK_SPLIT_SLOT)) r32[slot] = narrow(v * inv_scale);
+            }
+            rr += v * v;
+            if (!PZ && pos_bits(L.dinv[idx])) sp += p[idx];
         }
-        rr += v * v;
-        if (!pzero && pos_bits(L.dinv[idx])) sp += p[idx];
-    }
+    };
+    if (pzero)
+        run(BoolTag<true>{});
+    else
+        run(BoolTag<false>{});
     rr = block_sum<kRedThreads>(rr);
     sp = block_sum<kRedThreads>(sp);
     reduce_finish(rr, sp, partials, dscal, S_RR, S_SUM_P);
