@@ -1359,8 +1359,12 @@ __global__ void k_sum_live(unsigned n, const double *__restrict__ v, const doubl
                            double *__restrict__ partials, double *dscal)
 {
     double a = 0.0;
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        if (pos_bits(dinv[idx])) a += v[idx];
+    // the value loaded whatever the test (no wait on dinv); a starts at +0 and stays off -0, so
+    // adding +0 for a dead cell leaves it unchanged
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const double x = v[idx];
+        a += pos_bits(dinv[idx]) ? x : 0.0;
+    }
     reduce_finish(block_sum<kRedThreads>(a), 0.0, partials, dscal, S_SUM_B, -1);
 }
 
@@ -1371,7 +1375,8 @@ __global__ void k_rhs_center(unsigned n, const double *__restrict__ rhs, const d
     const double mean = block_scalar([&] { return dscal[S_SUM_B] / dscal[S_NLIVE]; });
     double a = 0.0;
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const double v = pos_bits(dinv[idx]) ? rhs[idx] - mean : 0.0;
+        const double x = rhs[idx];  // loaded whatever the test
+        const double v = pos_bits(dinv[idx]) ? x - mean : 0.0;
         b0[idx] = v;
         a += v * v;
     }
@@ -1403,8 +1408,10 @@ __global__ void k_sub_mean_p(unsigned n, const double *__restrict__ dinv, double
                              const double *__restrict__ dscal)
 {
     const double mean = block_scalar([&] { return dscal[S_SUM_P] / dscal[S_NLIVE]; });
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-        p[idx] = pos_bits(dinv[idx]) ? p[idx] - mean : 0.0;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const double x = p[idx];  // loaded whatever the test
+        p[idx] = pos_bits(dinv[idx]) ? x - mean : 0.0;
+    }
 }
 
 // Mixed refinement: r = b - A p in FP64, stored as FP32 r / scale_in; partial ||r||^2.
