@@ -415,7 +415,7 @@ def e2e_leg(case, K, W, readback="loss"):
     for i in range(W):
         step(i, last=False, slot=K + i)
     torch.cuda.synchronize()
-    steps_ms, nivcsw = [], []
+    steps_ms, nivcsw, nvcsw, minflt, majflt = [], [], [], [], []
     # main-stream events around each step: its span on the device, against its host time
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     mem0 = torch.cuda.memory_stats()
@@ -427,12 +427,16 @@ def e2e_leg(case, K, W, readback="loss"):
         upload(0)  # the first timed step's inputs: inside the timed region, hidden by nothing
         for i in range(K):
             ts = time.perf_counter()
-            cs = resource.getrusage(resource.RUSAGE_SELF).ru_nivcsw
+            ru0 = resource.getrusage(resource.RUSAGE_SELF)
             ev[i][0].record()
             step(i, last=(i == K - 1))
             ev[i][1].record()
             steps_ms.append(1e3 * (time.perf_counter() - ts))
-            nivcsw.append(resource.getrusage(resource.RUSAGE_SELF).ru_nivcsw - cs)
+            ru1 = resource.getrusage(resource.RUSAGE_SELF)
+            nivcsw.append(ru1.ru_nivcsw - ru0.ru_nivcsw)
+            nvcsw.append(ru1.ru_nvcsw - ru0.ru_nvcsw)
+            minflt.append(ru1.ru_minflt - ru0.ru_minflt)
+            majflt.append(ru1.ru_majflt - ru0.ru_majflt)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
     finally:
@@ -450,6 +454,10 @@ def e2e_leg(case, K, W, readback="loss"):
             # and the host's load average before and after: a stalled step with many switches
             # and a high load points at other work on the host's cores
             "involuntary_ctx_switches_per_step": nivcsw,
+            # voluntary switches (the thread blocked: a synchronisation, a lock, I/O) and page
+            # faults per step: a stalled step with many of either points inside the process
+            "voluntary_ctx_switches_per_step": nvcsw,
+            "page_faults_per_step": {"minor": minflt, "major": majflt},
             "device_step_ms": [round(a.elapsed_time(b), 2) for a, b in ev],
             "host_loadavg_1min": [round(load0[0], 2), round(os.getloadavg()[0], 2)],
             "host_cores": os.cpu_count(),
