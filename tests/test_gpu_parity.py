@@ -163,8 +163,8 @@ def test_projection_matches_oracle(mgp, name):
 
 @pytest.mark.parametrize("name", ["c2_64", "ell16"])
 def test_adjoint_faces_and_phi_grad_bit_exact_given_p_q(mgp, name):
-    """Given the same p and w, the adjoint's face gradients and the phi chain rule are bit-exact;
-    the adjoint solve itself matches the oracle to the solve tolerance."""
+    """Given the same p and w, the adjoint (its own solve for q) matches the oracle's to the solve
+    tolerance, and the phi chain rule on the oracle's grad_beta is bit-exact."""
     case = SMALL[name]
     beta_g, ctx = _ctx(mgp, case)
     uo, po, beta_o, _ = O.project(case.phi, case.solid, case.u_star, case.h, lam=case.lam, tol=1e-12)
@@ -177,6 +177,32 @@ def test_adjoint_faces_and_phi_grad_bit_exact_given_p_q(mgp, name):
     # phi chain rule bit-exact on the oracle's grad_beta
     gphi_g = host(mgp.phi_grad(beta_g, faces_dev(gb_o), case.h, rho_air=case.lam))
     assert np.array_equal(gphi_g, O.phi_grad(beta_o, gb_o, case.lam))
+
+
+@pytest.mark.parametrize("name", ["c2_64", "ell16"])
+def test_adjoint_faces_bit_exact_given_q(mgp, name):
+    """The adjoint's face gradients from the library's own q (read back through q_out) equal the
+    oracle's formulas on the same p, q and w bit for bit: grad_u* = w - G q and grad_beta =
+    dt (G p)(G q - w) on open faces, w and 0 on closed ones.  The right-hand side D(beta w) of
+    that solve has the oracle's norm once its region means are removed (a dropped beta, sign or
+    face would change it at O(1))."""
+    case = SMALL[name]
+    beta_g, ctx = _ctx(mgp, case)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    p = np.random.default_rng(5).standard_normal(case.shape)
+    dt = 2.5e-4
+    q = torch.zeros(case.shape, dtype=torch.float64, device="cuda")
+    gu_g, gb_g, st = ctx.project_adjoint(faces_dev(case.w), dev(p), dt=dt, tol=1e-10, q=q)
+    qg = host(q)
+    assert np.abs(qg).max() > 0
+    gq = O.gradient(beta_o, qg, case.h)
+    gp = O.gradient(beta_o, p, case.h)
+    for b, x, g, a, ug, bg in zip(beta_o, case.w, gq, gp, faces_host(gu_g), faces_host(gb_g)):
+        assert np.array_equal(ug, np.where(b > 0, x - g, x))
+        assert np.array_equal(bg, np.where(b > 0, dt * a * (g - x), 0.0))
+    c = O.divergence(beta_o, tuple(b * x for b, x in zip(beta_o, case.w)), case.h, 1.0)
+    lab, nc = O.components(beta_o)
+    assert st.rhs_norm == pytest.approx(np.linalg.norm(O.remove_mean(c, lab, nc)), rel=1e-12)
 
 
 FUSED_CASES = {
