@@ -166,7 +166,7 @@ struct BoolTag {
 };
 // Kernels that share face products along rows (k_phi_grad, k_divergence_mul): blocks of at most
 // kPhiThreads threads over rows of at most kPhiW cells, kPhiRun planes per block.
-constexpr int kPhiW = 512, kPhiThreads = 512, kPhiRun = 8;
+constexpr int kPhiW = 256, kPhiThreads = 512, kPhiRun = 8;
 
 __device__ __forceinline__ bool same_bits(double a, double b)
 {

@@ -179,14 +179,25 @@ def test_adjoint_faces_and_phi_grad_bit_exact_given_p_q(mgp, name):
     assert np.array_equal(gphi_g, O.phi_grad(beta_o, gb_o, case.lam))
 
 
-@pytest.mark.parametrize("name", ["c2_64", "ell16"])
+# rows longer than one block of the row-sharing kernels (k_phi_grad, k_divergence_mul): the x+
+# products at the blocks' right edges are formed again there; h = 1/520 (division by h)
+WIDE = "wide_520x32x32"
+
+
+def _adjoint_case(name):
+    if name == WIDE:
+        return synth.small_case(520, 32, 32, seed=11, solid="ellipsoid")
+    return SMALL[name]
+
+
+@pytest.mark.parametrize("name", ["c2_64", "ell16", WIDE])
 def test_adjoint_faces_bit_exact_given_q(mgp, name):
     """The adjoint's face gradients from the library's own q (read back through q_out) equal the
     oracle's formulas on the same p, q and w bit for bit: grad_u* = w - G q and grad_beta =
     dt (G p)(G q - w) on open faces, w and 0 on closed ones.  The right-hand side D(beta w) of
     that solve has the oracle's norm once its region means are removed (a dropped beta, sign or
     face would change it at O(1))."""
-    case = SMALL[name]
+    case = _adjoint_case(name)
     beta_g, ctx = _ctx(mgp, case)
     beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
     p = np.random.default_rng(5).standard_normal(case.shape)
@@ -380,3 +391,14 @@ def test_jacobi_pcg_grows_with_n_multigrid_does_not(mgp):
     assert its["jacobi", 64] >= 1.5 * its["jacobi", 32], its
     assert abs(its["mg", 64] - its["mg", 32]) <= 2, its
     assert its["jacobi", 32] > 3 * its["mg", 32], its
+
+
+def test_phi_grad_wide_rows_bit_exact(mgp):
+    """The phi chain rule on rows longer than one block (520 cells) and on random grad_beta:
+    bit-exact, the block-edge products included."""
+    case = _adjoint_case(WIDE)
+    beta_g, _ = _ctx(mgp, case)
+    beta_o = O.face_coeffs(case.phi, case.solid, case.lam)
+    gb = tuple(np.random.default_rng(6).standard_normal(case.shape) for _ in range(3))
+    gphi_g = host(mgp.phi_grad(beta_g, faces_dev(gb), case.h, rho_air=case.lam))
+    assert np.array_equal(gphi_g, O.phi_grad(beta_o, gb, case.lam))
