@@ -275,17 +275,17 @@ __device__ __forceinline__ float narrow(double x)
     return f;
 }
 
-// x * f for f = 2^e, bit for bit the product __dmul_rn(x, f), on the integer pipe where x and the
-// product are normal numbers: e added to the exponent field (the FP64 unit is the limiting
-// resource of the FP64 set-up and projection passes).  Zeros, subnormals, infinities, NaNs and
-// products outside the normal range take the multiply.  The check build compares every result
-// with the multiply.
 // Products that only some lanes or launches need, as calls: the compiler cannot run a call
 // speculatively, so a branch around one is not if-converted into an FP64 instruction that every
 // warp issues (predicated off, it still occupies the FP64 unit).
 __device__ __noinline__ double dmul_call(double x, double f) { return __dmul_rn(x, f); }
 __device__ __noinline__ double sq_mul_call(double b, double g) { return __dmul_rn(__dmul_rn(b, b), g); }
 
+// x * f for f = 2^e, bit for bit the product __dmul_rn(x, f), on the integer pipe where x and the
+// product are normal numbers: e added to the exponent field (the FP64 unit is the limiting
+// resource of the FP64 set-up and projection passes).  Zeros, subnormals, infinities, NaNs and
+// products outside the normal range take the multiply (a call).  The check build compares every
+// result with the multiply.
 __device__ __forceinline__ double mul_pow2(double x, double f, int e)
 {
     const int hi = __double2hiint(x), lo = __double2loint(x);
@@ -1460,8 +1460,6 @@ __global__ void k_accumulate(unsigned n, const float *__restrict__ e32, double *
     }
 }
 
-// FP64 natural-order field <-> the finest FP32 field in the layout sp (one FP32 V-cycle on a
-// caller's FP64 rhs and iterate)
 // The FP32 copy of one level: the narrowed faces (natural layout; on the finest level with a
 // colour-split layout, also in that layout, sf != null) and 1/sum of the narrowed faces, summed
 // in k_diag_inv's order with its divisor memo (so the value k_diag_inv gives on the narrowed
@@ -1524,6 +1522,8 @@ __global__ void k_level_f32(int nx, int ny, int nz, const double *__restrict__ b
     }
 }
 
+// FP64 natural-order field <-> the finest FP32 field in the layout sp (one FP32 V-cycle on a
+// caller's FP64 rhs and iterate)
 __global__ void k_to_f32_layout(unsigned n, const double *__restrict__ src, float *__restrict__ dst, Split sp)
 {
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
